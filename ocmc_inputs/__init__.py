@@ -1,0 +1,192 @@
+"""Seeded synthetic inputs shared by the CUDA engine's tests/bench and the oracle.
+
+This module holds none of the transport method's arithmetic: it only builds
+phantoms (density + material grids) and beam descriptions (energy bin edges
+and weights, field, SSD, direction) shaped like the workloads of Tian et al.
+(oclMC), Sec. 2.2 "Materials": a homogeneous water phantom, a water/bone/lung
+slab phantom and a half-slab phantom irradiated by a 15 MeV electron beam or
+a 6 MV photon beam from a point source at SSD 100 cm.
+
+Material indices: 0 water, 1 cortical bone (ICRP, 1.85 g/cm^3),
+2 lung (ICRP, 0.26 g/cm^3). Arrays are x-fastest: index = x + nx*(y + ny*z),
+stored as numpy arrays of shape (nz, ny, nx).
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+WATER, BONE, LUNG = 0, 1, 2
+RHO = {WATER: 1.0, BONE: 1.85, LUNG: 0.26}
+
+
+@dataclasses.dataclass
+class Phantom:
+    density: np.ndarray   # float32 (nz, ny, nx), g/cm^3
+    material: np.ndarray  # uint8 (nz, ny, nx)
+    voxel: tuple          # (dx, dy, dz) cm
+
+    @property
+    def shape_xyz(self):
+        nz, ny, nx = self.density.shape
+        return nx, ny, nz
+
+    @property
+    def size_cm(self):
+        nx, ny, nz = self.shape_xyz
+        return nx * self.voxel[0], ny * self.voxel[1], nz * self.voxel[2]
+
+
+@dataclasses.dataclass
+class Beam:
+    particle: int            # 0 photon, 1 electron
+    edges: np.ndarray        # float32 (n_bins+1,) MeV
+    weights: np.ndarray      # float32 (n_bins,)
+    field: tuple             # (fx, fy) cm, in the plane through iso normal to dir
+    ssd: float               # cm; <= 0 means a parallel beam
+    iso: tuple               # field centre (cm)
+    direction: tuple         # beam axis (unit vector)
+
+
+def homogeneous(n, voxel, material=WATER, density=None):
+    nx, ny, nz = n
+    rho = RHO[material] if density is None else density
+    d = np.full((nz, ny, nx), rho, dtype=np.float32)
+    m = np.full((nz, ny, nx), material, dtype=np.uint8)
+    return Phantom(d, m, tuple(float(v) for v in voxel))
+
+
+def _layered(n, voxel, layers, half=False):
+    """layers: list of (z0, z1, material) in cm from the entrance surface z=0.
+    With half=True the layers cover only x < Lx/2 for bone and x >= Lx/2 for
+    lung (the half-slab phantom); elsewhere water."""
+    nx, ny, nz = n
+    ph = homogeneous(n, voxel, WATER)
+    zc = (np.arange(nz) + 0.5) * voxel[2]
+    xc = (np.arange(nx) + 0.5) * voxel[0]
+    lx = nx * voxel[0]
+    for z0, z1, mat in layers:
+        zsel = (zc >= z0) & (zc < z1)
+        if not half:
+            ph.material[zsel] = mat
+            ph.density[zsel] = RHO[mat]
+        else:
+            xsel = xc < lx / 2 if mat == BONE else xc >= lx / 2
+            sel = zsel[:, None, None] & np.ones((1, ny, 1), bool) & xsel[None, None, :]
+            ph.material[sel] = mat
+            ph.density[sel] = RHO[mat]
+    return ph
+
+
+def slab(n=(120, 120, 120), voxel=(0.25, 0.25, 0.25), layers=((3.0, 5.0, BONE), (5.0, 12.0, LUNG))):
+    """Water with a bone layer and a lung layer along z (water beyond)."""
+    return _layered(n, voxel, layers)
+
+
+def half_slab(n=(120, 120, 120), voxel=(0.25, 0.25, 0.25)):
+    """Bone for x < Lx/2 and lung for x >= Lx/2 over depths 3-10 cm; water elsewhere."""
+    return _layered(n, voxel, ((3.0, 10.0, BONE), (3.0, 10.0, LUNG)), half=True)
+
+
+def ct_like(n=(256, 256, 128), voxel=(0.2, 0.2, 0.2), seed=1):
+    """Synthetic CT-like phantom: water-body ellipsoid with 3-8 random inserts,
+    densities uniform in [0.2, 1.9]; density thresholds pick the material
+    (< 0.6 lung, 0.6-1.3 water, > 1.3 bone). Outside the body: air-like 0.0012 water."""
+    rng = np.random.default_rng(seed)
+    nx, ny, nz = n
+    lx, ly, lz = nx * voxel[0], ny * voxel[1], nz * voxel[2]
+    z, y, x = np.meshgrid((np.arange(nz) + 0.5) * voxel[2], (np.arange(ny) + 0.5) * voxel[1],
+                          (np.arange(nx) + 0.5) * voxel[0], indexing="ij")
+    dens = np.full((nz, ny, nx), 0.0012, np.float32)
+    body = ((x - lx / 2) / (0.45 * lx)) ** 2 + ((y - ly / 2) / (0.35 * ly)) ** 2 + ((z - lz / 2) / (0.48 * lz)) ** 2 <= 1
+    dens[body] = 1.0
+    for _ in range(int(rng.integers(3, 9))):
+        c = rng.uniform([0.3 * lx, 0.35 * ly, 0.2 * lz], [0.7 * lx, 0.65 * ly, 0.8 * lz])
+        r = rng.uniform([1.0, 1.0, 1.0], [0.12 * lx, 0.1 * ly, 0.2 * lz])
+        sel = (((x - c[0]) / r[0]) ** 2 + ((y - c[1]) / r[1]) ** 2 + ((z - c[2]) / r[2]) ** 2 <= 1) & body
+        dens[sel] = np.float32(rng.uniform(0.2, 1.9))
+    mat = np.full(dens.shape, WATER, np.uint8)
+    mat[dens < 0.6] = LUNG
+    mat[dens > 1.3] = BONE
+    mat[~body] = WATER
+    return Phantom(dens, mat, tuple(float(v) for v in voxel))
+
+
+def spectrum_6mv(n_bins=24, lo=0.25, hi=6.0):
+    """Closed-form stand-in for a 6 MV bremsstrahlung spectrum,
+    phi(E) ~ ((6 - E)/E) (1 - exp(-(E/1.3)^2)) on [0.25, 6] MeV (mean ~2.0 MeV),
+    integrated over n_bins equal-width bins (Simpson, 64 panels per bin)."""
+    edges = np.linspace(lo, hi, n_bins + 1)
+    w = np.empty(n_bins)
+    for i in range(n_bins):
+        e = np.linspace(edges[i], edges[i + 1], 129)
+        f = ((6.0 - e) / e) * (1.0 - np.exp(-(e / 1.3) ** 2))
+        h = (e[-1] - e[0]) / 128
+        w[i] = h / 3 * (f[0] + f[-1] + 4 * f[1:-1:2].sum() + 2 * f[2:-1:2].sum())
+    w = np.maximum(w, 0)
+    return edges.astype(np.float32), (w / w.sum()).astype(np.float32)
+
+
+def mono(E):
+    return np.array([E, E], np.float32), np.array([1.0], np.float32)
+
+
+def beam_on(ph: Phantom, particle, spectrum, field=(10.0, 10.0), ssd=100.0):
+    """Beam normal to the entrance surface z=0, centred on the phantom's x-y centre."""
+    lx, ly, _ = ph.size_cm
+    edges, w = spectrum
+    return Beam(particle, edges, w, tuple(field), float(ssd), (lx / 2, ly / 2, 0.0), (0.0, 0.0, 1.0))
+
+
+# ---- named workloads ---------------------------------------------------------------
+def electron_water_61():
+    """15 MeV e-, 10x10 parallel field, water 30.5x30.5x30 cm at 0.5 cm (61x61x60)."""
+    ph = homogeneous((61, 61, 60), (0.5, 0.5, 0.5))
+    return ph, beam_on(ph, 1, mono(15.0), (10.0, 10.0), ssd=0.0)
+
+
+def photon_slab_120():
+    """6 MV photons, 10x10 at SSD 100 cm, slab phantom 120^3 at 0.25 cm."""
+    ph = slab()
+    return ph, beam_on(ph, 0, spectrum_6mv(), (10.0, 10.0), ssd=100.0)
+
+
+def photon_half_slab_120():
+    ph = half_slab()
+    return ph, beam_on(ph, 0, spectrum_6mv(), (10.0, 10.0), ssd=100.0)
+
+
+def electron_half_slab_120():
+    ph = half_slab()
+    return ph, beam_on(ph, 1, mono(15.0), (10.0, 10.0), ssd=100.0)
+
+
+def scaled(ph: Phantom, factor):
+    """Coarsen a phantom by an integer factor (nearest sample) for oracle-sized cases."""
+    f = int(factor)
+    d = ph.density[f // 2::f, f // 2::f, f // 2::f].copy()
+    m = ph.material[f // 2::f, f // 2::f, f // 2::f].copy()
+    return Phantom(d, m, tuple(v * f for v in ph.voxel))
+
+
+def random_phantom(n=(24, 20, 28), voxel=(0.5, 0.5, 0.5), seed=0):
+    """Small random heterogeneous phantom for parity tests: random materials with
+    nominal densities, scaled by a random factor in [0.7, 1.3], ~5% vacuum-free."""
+    rng = np.random.default_rng(seed)
+    nx, ny, nz = n
+    mat = rng.integers(0, 3, size=(nz, ny, nx)).astype(np.uint8)
+    base = np.vectorize(RHO.get)(mat).astype(np.float32)
+    dens = (base * rng.uniform(0.7, 1.3, size=base.shape)).astype(np.float32)
+    return Phantom(dens, mat, tuple(float(v) for v in voxel))
+
+
+def pencil(ph: Phantom, particle, E, direction=(0.0, 0.0, 1.0)):
+    """Infinitely thin parallel beam along +z through the x-y centre."""
+    lx, ly, _ = ph.size_cm
+    edges, w = mono(E)
+    return Beam(particle, edges, w, (0.0, 0.0), 0.0, (lx / 2 + 1e-3, ly / 2 + 1e-3, 0.0), direction)
+
+
+__all__ = [n for n in dir() if not n.startswith("_") and n not in ("annotations", "dataclasses", "math", "np")]
