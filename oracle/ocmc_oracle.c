@@ -323,7 +323,8 @@ void orc_philox(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
     out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
 }
 
-/* A particle's random stream: counter = (draw block, history lo, history hi, sub). */
+/* A particle's random stream: counter = (draw block, history lo, history hi, sub).
+   Draw n is word n mod 4 of block n/4; a word x maps to ((x >> 8) + 1) 2^-24. */
 typedef struct { uint32_t key[2]; uint64_t hist; uint32_t sub; uint32_t n; } stream;
 
 static double rnd(stream* s)
@@ -333,7 +334,7 @@ static double rnd(stream* s)
     orc_philox(ctr, s->key, out);
     uint32_t x = out[s->n & 3u];
     s->n++;
-    return ((double)x + 1.0) * (1.0 / 4294967296.0);   /* (0, 1] */
+    return (double)((x >> 8) + 1u) * (1.0 / 16777216.0);   /* (0, 1] on a 2^-24 grid */
 }
 
 static uint32_t child_sub(uint32_t parent, uint32_t n, uint32_t slot)
@@ -389,7 +390,7 @@ static double sample_ms_mu(double G1, stream* s)
 {
     if (G1 < MS_G1_NONE) { (void)rnd(s); return 1.0; }
     if (G1 >= MS_G1_ISO) return 2.0 * rnd(s) - 1.0;
-    double A = orc_ms_solve_A(G1), xi = rnd(s);
+    double A = orc_ms_solve_A(G1), xi = 1.0 - rnd(s);          /* xi in [0, 1) */
     double u = 2.0 * A * xi / (1.0 + A - xi);
     double mu = 1.0 - u;
     return mu < -1.0 ? -1.0 : (mu > 1.0 ? 1.0 : mu);
