@@ -1,0 +1,225 @@
+/*
+ * ocmc.h -- C ABI of the GB300 coupled photon-electron Monte Carlo dose engine.
+ *
+ * The engine computes the method of Tian et al., "An OpenCL-based Monte Carlo
+ * dose calculation engine (oclMC) for coupled photon-electron transport":
+ * analogue photon transport with Woodcock tracking (Compton, photoelectric,
+ * pair production) and Class II condensed-history electron/positron transport
+ * (continuous restricted energy loss, random-hinge multiple scattering,
+ * discrete Moller and bremsstrahlung events) through a voxel phantom, with
+ * the deposited energy tallied per voxel (Sec. 2.1). Results are reported in
+ * MeV/g per source particle (Sec. 2.2 "Materials").
+ *
+ * Conventions for every call:
+ *  - Each call returns an ocmc_status; on failure a message is kept per
+ *    context and returned by ocmc_last_error().
+ *  - The library owns the context and all device memory it allocates.
+ *    Input arrays are copied; the caller keeps ownership of its buffers.
+ *  - A context is not thread-safe; one host thread drives it at a time.
+ *  - All pointers named *_host are host memory; where a call takes an
+ *    `on_device` flag, 1 means the pointer is CUDA device memory on the
+ *    context's device and 0 means host memory.
+ *  - Arrays over the voxel grid are x-fastest: v = ix + nx*(iy + ny*iz).
+ */
+#ifndef OCMC_H
+#define OCMC_H
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ocmc_ctx ocmc_ctx;
+
+typedef enum {
+    OCMC_OK = 0,
+    OCMC_ERR_ARG = 1,       /* invalid argument; nothing changed                  */
+    OCMC_ERR_CUDA = 2,      /* a CUDA runtime call failed (no device, launch...)  */
+    OCMC_ERR_OOM = 3,       /* device allocation failed                           */
+    OCMC_ERR_OVERFLOW = 4,  /* a secondary-particle stack overflowed; the run's   */
+                            /* tally misses the dropped particles                 */
+    OCMC_ERR_TIMEOUT = 5,   /* a particle exceeded the step limit or a sampling   */
+                            /* loop its iteration limit; that particle was dropped*/
+    OCMC_ERR_STATE = 6      /* call out of order (no phantom, no source, ...)     */
+} ocmc_status;
+
+/* Test modes of ocmc_params.flags (used by the physics tests, 0 in production). */
+#define OCMC_FLAG_NO_HARD          1  /* no discrete Moller/bremsstrahlung events   */
+#define OCMC_FLAG_NO_MS            2  /* no multiple-scattering deflection          */
+#define OCMC_FLAG_KILL_FIRST_REAL  4  /* photons removed at first real interaction  */
+#define OCMC_FLAG_KERMA            8  /* e-/e+ deposit their energy where created   */
+
+/* Transport and execution parameters (Sec. 2.1: absorption energies, hard-event
+ * cutoffs and the user-defined step limits d_maxs, d_maxe; Sec. 2.2.1: the
+ * number of concurrently transported particles). Execution fields change speed
+ * only: the dose is bit-identical for any value of them. */
+typedef struct {
+    float e_abs_e;          /* MeV, electron/positron absorption energy (0.2)      */
+    float e_abs_g;          /* MeV, photon absorption energy (0.01)                */
+    float w_cc;             /* MeV, Moller hard-collision threshold (= e_abs_e)    */
+    float w_cb;             /* MeV, bremsstrahlung hard threshold (= e_abs_g)      */
+    float d_maxs;           /* cm, maximum electron step (0.5)                     */
+    float f_maxe;           /* maximum fractional CSDA loss per step (0.05)        */
+    float s_min;            /* cm, boundaries closer than this are crossed without */
+                            /* physics (1e-4)                                      */
+    int32_t n_batches;      /* statistical batches B; batch = history id mod B (10)*/
+    int32_t flags;          /* OCMC_FLAG_* test modes (0)                          */
+    /* execution (tuning) parameters, 0 = automatic */
+    int32_t block_threads;  /* threads per block of the transport kernel           */
+    int32_t blocks_per_sm;  /* resident transport blocks per SM                    */
+    int32_t stack_capacity; /* per-warp capacity of each secondary stack          */
+    int32_t switch_high;    /* other-type stack size that makes a warp switch type */
+    int32_t switch_low;     /* active lanes at or below which a warp switches type */
+} ocmc_params;
+
+/* Run statistics accumulated since the last ocmc_reset_tally(). */
+typedef struct {
+    uint64_t histories;        /* histories transported                           */
+    uint64_t photon_flights;   /* Woodcock flights (real + fictitious)            */
+    uint64_t fictitious;       /* fictitious photon events                         */
+    uint64_t compton, photo, pair;
+    uint64_t electron_steps;   /* condensed-history steps of e-/e+                 */
+    uint64_t moller, brems;    /* accepted hard events                              */
+    uint64_t hard_fictitious;  /* rejected hard-event candidates (energy Woodcock)  */
+    uint64_t annihilations;
+    uint64_t escaped;          /* particles leaving the phantom                     */
+    uint64_t missed;           /* source particles that miss the phantom            */
+    uint64_t geo_crossings;    /* boundary crossings without physics                */
+    uint64_t majorant_violations; /* must stay 0                                     */
+    uint64_t dropped;          /* particles dropped (overflow/limits); must stay 0  */
+    uint64_t transmitted;      /* KILL_FIRST_REAL mode: photons out at z = Lz       */
+    uint64_t warp_iterations;  /* warp-level scheduler iterations                   */
+    uint64_t lane_steps;       /* lane-steps executed (active lanes summed)         */
+    double e_in, e_dep, e_esc, e_miss, pair_mass, annih_mass, e_killed, e_trans, e_dropped; /* MeV */
+    double last_run_ms;        /* device time of the last ocmc_run (CUDA events)   */
+} ocmc_stats;
+
+/* Fill p with the defaults listed above. */
+void ocmc_default_params(ocmc_params* p);
+
+/* Create a context on CUDA device `device` (Sec. 2.2.1 "Initialize"). p may be
+ * NULL for defaults. Errors: OCMC_ERR_ARG (bad parameter values),
+ * OCMC_ERR_CUDA (no such device / no driver), OCMC_ERR_OOM. On failure *out is
+ * set to NULL. */
+ocmc_status ocmc_init(ocmc_ctx** out, int device, const ocmc_params* p);
+
+/* Replace the transport parameters (the tally is kept). Same errors as init. */
+ocmc_status ocmc_set_params(ocmc_ctx* ctx, const ocmc_params* p);
+
+/* The voxel phantom (Sec. 2.1: each voxel has a density and a material type).
+ * density_host: nx*ny*nz float, g/cm^3, finite and in [0, 30];
+ * material_host: nx*ny*nz uint8, 0 water, 1 cortical bone (ICRP), 2 lung (ICRP);
+ * dx, dy, dz: voxel size in cm. The phantom occupies [0,nx*dx] x [0,ny*dy] x
+ * [0,nz*dz]. 1 <= nx, ny, nz <= 1024. Copies the data (host pointers) and
+ * resets the tally. Errors: OCMC_ERR_ARG for bad sizes or values. */
+ocmc_status ocmc_create_phantom(ocmc_ctx* ctx, int nx, int ny, int nz,
+                                const float* density_host, const uint8_t* material_host,
+                                float dx, float dy, float dz);
+
+/* The beam (Sec. 2.2 "Materials": point source at an SSD with a field defined
+ * at the surface, 15 MeV mono-energetic electrons or a 6 MV photon spectrum;
+ * Sec. 2.2.1: source particles are simulated bin by bin in energy).
+ * particle: 0 photon, 1 electron. bin_edges_host: n_bins+1 floats in MeV
+ * (ascending per bin; a mono-energetic beam is n_bins=1 with equal edges);
+ * weights_host: n_bins non-negative floats, not all zero; 1 <= n_bins <= 256.
+ * Histories are stratified over the bins: of N histories, bin order q (bins by
+ * decreasing energy) receives ids [floor(N c_q / W), floor(N c_{q+1} / W)),
+ * c_q the partial weight sums, W the total. Energies are uniform in the bin.
+ * field_x, field_y: cm, rectangle in the plane through iso normal to dir,
+ * with in-plane axes e1 = normalize(y_hat x dir), e2 = dir x e1.
+ * ssd > 0: point source at iso - ssd*dir; ssd <= 0: parallel beam along dir.
+ * Particles travel in vacuum to the phantom surface. */
+ocmc_status ocmc_set_source(ocmc_ctx* ctx, int particle, int n_bins,
+                            const float* bin_edges_host, const float* weights_host,
+                            float field_x, float field_y, float ssd,
+                            const float iso[3], const float dir[3]);
+
+/* Transport histories 0..n_histories-1 with the Philox key `seed` and add the
+ * deposited energy to the tally (Sec. 2.2.1, Table 1 loop). Asynchronous on
+ * cuda_stream (a cudaStream_t, NULL = the legacy default stream); the call
+ * returns after the launch. Repeated calls accumulate; use different seeds.
+ * Errors: OCMC_ERR_STATE without phantom or source, OCMC_ERR_ARG if n is 0. */
+ocmc_status ocmc_run(ocmc_ctx* ctx, uint64_t n_histories, uint64_t seed, void* cuda_stream);
+
+/* Transport histories [first, first+count) of a run of n_total histories
+ * (sharding over GPUs or resuming a run). The union of disjoint ranges with
+ * the same n_total and seed gives the tally of one ocmc_run(n_total, seed),
+ * bit for bit. */
+ocmc_status ocmc_run_range(ocmc_ctx* ctx, uint64_t first, uint64_t count, uint64_t n_total,
+                           uint64_t seed, void* cuda_stream);
+
+/* Dose in MeV/g per source particle, D_v = sum_b E_bv / (rho_v V N), and its
+ * batch standard error sigma_v = sqrt(sum_b (D_bv - D_v)^2 / (B (B-1)))
+ * (Sec. 3.1). dose_out: nx*ny*nz floats; sigma_out may be NULL. Voxels of
+ * zero density report 0. Synchronises with the last run. Errors:
+ * OCMC_ERR_STATE before any run; OCMC_ERR_OVERFLOW / OCMC_ERR_TIMEOUT if the
+ * runs dropped particles (the dose is still written). */
+ocmc_status ocmc_get_dose(ocmc_ctx* ctx, float* dose_out, float* sigma_out, int on_device);
+
+/* Raw int64 tally, B x nvox, in units of 2^-28 MeV (round to nearest even per
+ * deposit). Integer sums make it bit-identical for any scheduling. */
+ocmc_status ocmc_get_raw_tally(ocmc_ctx* ctx, int64_t* out, int on_device);
+
+/* Add a raw tally (same layout) from another context or rank, together with
+ * the number of histories it represents; used after a cross-GPU sum. */
+ocmc_status ocmc_add_raw_tally(ocmc_ctx* ctx, const int64_t* in, int on_device,
+                               uint64_t first, uint64_t count);
+
+/* Zero the tally, the history count and the statistics. */
+ocmc_status ocmc_reset_tally(ocmc_ctx* ctx);
+
+/* Statistics of the runs since the last reset (synchronises). */
+ocmc_status ocmc_get_stats(ocmc_ctx* ctx, ocmc_stats* out);
+
+/* Number of voxels and batches of the current phantom/parameters. */
+ocmc_status ocmc_get_shape(ocmc_ctx* ctx, int64_t* nvox, int32_t* n_batches);
+
+/* Message of the last failed call on ctx ("" if none; valid until the next
+ * call). ctx may be NULL for failures of ocmc_init. */
+const char* ocmc_last_error(ocmc_ctx* ctx);
+
+/* Release the context and its device memory. NULL is ignored. */
+void ocmc_destroy(ocmc_ctx* ctx);
+
+/* ---- test access to the engine's building blocks ---------------------------
+ * These run the same device functions the transport kernel uses, so the
+ * tests can compare each building block with the CPU oracle. */
+
+/* Philox4x32-10 (Salmon et al. 2011) on the device: for block j in
+ * [0, n_blocks), out_host[4j..4j+3] = Philox(counter = (first_block + j,
+ * c1, c2, c3), key = (key0, key1)). */
+ocmc_status ocmc_test_philox(int device, uint32_t key0, uint32_t key1, uint32_t c1, uint32_t c2,
+                             uint32_t c3, uint32_t first_block, uint32_t n_blocks,
+                             uint32_t* out_host);
+
+/* Source particles of histories [first, first+count) of a run of n_total:
+ * out_host[8j..8j+7] = x, y, z, u, v, w, E, entered (1/0). */
+ocmc_status ocmc_test_source(ocmc_ctx* ctx, uint64_t n_total, uint64_t first, uint64_t count,
+                             uint64_t seed, float* out_host);
+
+/* Samples of one interaction model at energy E (MeV) in material m:
+ * kind 0: Compton cos(theta); 1: Moller W/T; 2: bremsstrahlung photon energy
+ * (MeV); 3: multiple-scattering cos(theta) for G1 = aux (path / lambda_1).
+ * Sample j uses the Philox stream (history j, sub-stream 0x5A5A + kind). */
+ocmc_status ocmc_test_sample(ocmc_ctx* ctx, int kind, int material, float E, float aux,
+                             uint64_t n, uint64_t seed, float* out_host);
+
+/* Engine tables interpolated at energies E_host[0..n) for material m:
+ * out_host[8j..8j+7] = mu_total, mu_compton, mu_photo (cm^2/g), restricted
+ * CSDA range R (g/cm^2, offset: R at the table's lowest energy is the
+ * first-interval estimate), 1/lambda_1 (cm^2/g), sigma_moller, sigma_brems
+ * (cm^2/g), hard-event majorant (cm^2/g). Builds the tables if needed (a
+ * phantom must be set). */
+ocmc_status ocmc_test_tables(ocmc_ctx* ctx, int material, const float* E_host, int n,
+                             float* out_host);
+
+/* End energy of a CSDA step of mass thickness X (g/cm^2) from energy T in
+ * material m, as the transport kernel computes it (range-table inversion). */
+ocmc_status ocmc_test_csda(ocmc_ctx* ctx, int material, const float* T_host, const float* X_host,
+                           int n, float* out_host);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,212 @@
+// ocmc_aux.cu -- dose finalisation and the test kernels that expose the transport
+// kernel's building blocks (RNG, source, samplers, tables) to the test suite.
+#include "ocmc_device.cuh"
+
+#include <algorithm>
+
+namespace ocmc {
+
+namespace {
+
+// D_v = sum_b E_bv / (rho_v V N); sigma_v^2 = sum_b (D_bv - D_v)^2 / (B (B - 1)),
+// D_bv = E_bv / (rho_v V N_b)  (Sec. 2.2 "Materials": MeV/g per source particle;
+// Sec. 3.1: sigma_D, here by the batch method). Grid-stride over voxels.
+__global__ void k_finalize(const long long* __restrict__ tally, const float* __restrict__ density, int B, long long nvox,
+                           double voxel_volume, const double* __restrict__ inv_nb, double inv_n, float* dose,
+                           float* sigma)
+{
+    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < nvox;
+         v += (long long)gridDim.x * blockDim.x) {
+        float rho = density[v];
+        if (!(rho > 0.f)) {
+            dose[v] = 0.f;
+            if (sigma) sigma[v] = 0.f;
+            continue;
+        }
+        double inv_mass = 1.0 / ((double)rho * voxel_volume) / 268435456.0;
+        long long tot = 0;
+        for (int b = 0; b < B; ++b) tot += tally[(long long)b * nvox + v];
+        double D = (double)tot * inv_mass * inv_n;
+        dose[v] = (float)D;
+        if (sigma) {
+            double ss = 0.0;
+            if (B > 1) {
+                for (int b = 0; b < B; ++b) {
+                    double Db = (double)tally[(long long)b * nvox + v] * inv_mass * inv_nb[b] - D;
+                    ss += Db * Db;
+                }
+                ss /= (double)B * (B - 1);
+            }
+            sigma[v] = (float)sqrt(ss);
+        }
+    }
+}
+
+__global__ void k_test_philox(uint32_t k0, uint32_t k1, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t first,
+                              uint32_t n, uint32_t* out)
+{
+    uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    uint4 r = philox4x32_10(make_uint4(first + j, c1, c2, c3), k0, k1);
+    out[4 * j] = r.x;
+    out[4 * j + 1] = r.y;
+    out[4 * j + 2] = r.z;
+    out[4 * j + 3] = r.w;
+}
+
+__global__ void k_test_source(const TransportArgs a, unsigned long long first, unsigned long long count, float* out)
+{
+    unsigned long long j = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x;
+    if (j >= count) return;
+    Lane p;
+    bool in = init_primary(a, first + j, p);
+    float* o = out + 8 * j;
+    o[0] = in ? p.x : 0.f; o[1] = in ? p.y : 0.f; o[2] = in ? p.z : 0.f;
+    o[3] = in ? p.u : 0.f; o[4] = in ? p.v : 0.f; o[5] = in ? p.w : 0.f;
+    o[6] = p.E;
+    o[7] = in ? 1.f : 0.f;
+}
+
+__global__ void k_test_sample(const TransportArgs a, int kind, int m, float E, float aux, unsigned long long n,
+                              float* out)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    SmemTables T = stage_tables(a.t, smem);
+    for (unsigned long long j = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; j < n;
+         j += (unsigned long long)gridDim.x * blockDim.x) {
+        Rng r;
+        r.h0 = (uint32_t)j; r.h1 = (uint32_t)(j >> 32); r.sub = 0x5A5Au + (uint32_t)kind; r.n = 0; r.blk = 0xFFFFFFFFu;
+        bool ok = true;
+        float v = 0.f, eps;
+        if (kind == 0) v = sample_compton(E, r, a.key0, a.key1, &eps, &ok);
+        else if (kind == 1) v = sample_moller(E, a.pp.w_cc, r, a.key0, a.key1, &ok);
+        else if (kind == 2) v = sample_brems(E, a.pp.w_cb, T.msc[2 * m], T.msc[2 * m + 1], r, a.key0, a.key1, &ok);
+        else if (kind == 3) v = sample_ms(T, aux, r, a.key0, a.key1);
+        out[j] = ok ? v : __int_as_float(0x7FC00000);
+    }
+}
+
+__global__ void k_test_tables(const TransportArgs a, int m, const float* E, int n, float* out)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    SmemTables T = stage_tables(a.t, smem);
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    EIdx ei = e_index(E[j]);
+    const int mb = m * NE;
+    float4 pa = T.ph[mb + ei.i], pb = T.ph[mb + ei.i + 1];
+    float mt = __expf(lerp1(pa.x, pb.x, ei.f));
+    float4 A = T.el[mb + ei.i], B = T.el[mb + ei.i + 1];
+    float* o = out + 8 * j;
+    o[0] = mt;
+    o[1] = mt * lerp1(pa.y, pb.y, ei.f);
+    o[2] = mt * lerp1(pa.z, pb.z, ei.f);
+    o[3] = __expf(lerp1(A.x, B.x, ei.f));
+    o[4] = lerp1(A.y, B.y, ei.f);
+    o[5] = lerp1(A.z, B.z, ei.f);
+    o[6] = lerp1(A.w, B.w, ei.f);
+    o[7] = T.el2[mb + ei.i].y;
+}
+
+__global__ void k_test_csda(const TransportArgs a, int m, const float* Tk, const float* X, int n, float* out)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    SmemTables T = stage_tables(a.t, smem);
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    EIdx ei = e_index(Tk[j]);
+    float lnR = lerp1(T.el[m * NE + ei.i].x, T.el[m * NE + ei.i + 1].x, ei.f);
+    out[j] = csda_end(T, m, Tk[j], lnR, X[j]);
+}
+
+__global__ void k_add_tally(long long* t, const long long* in, long long n)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        t[i] += in[i];
+}
+
+__global__ void k_sum_tally(const long long* t, long long n, unsigned long long* out)
+{
+    __shared__ long long red[32];
+    long long s = 0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        s += t[i];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xFFFFFFFFu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        s = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0;
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xFFFFFFFFu, s, o);
+        if (threadIdx.x == 0) atomicAdd(out, (unsigned long long)s);
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_add_tally(long long* tally, const long long* in, long long n, cudaStream_t s)
+{
+    k_add_tally<<<1024, 256, 0, s>>>(tally, in, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sum_tally(const long long* tally, long long n, unsigned long long* out, cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(out, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return e;
+    k_sum_tally<<<1024, 256, 0, s>>>(tally, n, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finalize(const long long* tally, const float* density, int B, long long nvox, double voxel_volume,
+                            const double* inv_nb, double inv_n, float* dose, float* sigma, cudaStream_t s)
+{
+    int blocks = (int)std::min<long long>((nvox + 255) / 256, 152 * 16);
+    k_finalize<<<blocks > 0 ? blocks : 1, 256, 0, s>>>(tally, density, B, nvox, voxel_volume, inv_nb, inv_n, dose, sigma);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_test_philox(uint32_t key0, uint32_t key1, uint32_t c1, uint32_t c2, uint32_t c3,
+                               uint32_t first_block, uint32_t n_blocks, uint32_t* out, cudaStream_t s)
+{
+    k_test_philox<<<(n_blocks + 255) / 256, 256, 0, s>>>(key0, key1, c1, c2, c3, first_block, n_blocks, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_test_source(const TransportArgs& a, unsigned long long n_total, unsigned long long first,
+                               unsigned long long count, float* out, cudaStream_t s)
+{
+    (void)n_total;
+    k_test_source<<<(unsigned)((count + 255) / 256), 256, 0, s>>>(a, first, count, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_test_sample(const TransportArgs& a, int kind, int m, float E, float aux, unsigned long long n,
+                               float* out, cudaStream_t s)
+{
+    cudaError_t e = cudaFuncSetAttribute(k_test_sample, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)SMEM_TABLE_BYTES);
+    if (e != cudaSuccess) return e;
+    k_test_sample<<<152 * 2, 256, SMEM_TABLE_BYTES, s>>>(a, kind, m, E, aux, n, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_test_tables(const TransportArgs& a, int m, const float* E, int n, float* out, cudaStream_t s)
+{
+    cudaError_t e = cudaFuncSetAttribute(k_test_tables, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)SMEM_TABLE_BYTES);
+    if (e != cudaSuccess) return e;
+    k_test_tables<<<(n + 255) / 256, 256, SMEM_TABLE_BYTES, s>>>(a, m, E, n, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_test_csda(const TransportArgs& a, int m, const float* T, const float* X, int n, float* out,
+                             cudaStream_t s)
+{
+    cudaError_t e = cudaFuncSetAttribute(k_test_csda, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)SMEM_TABLE_BYTES);
+    if (e != cudaSuccess) return e;
+    k_test_csda<<<(n + 255) / 256, 256, SMEM_TABLE_BYTES, s>>>(a, m, T, X, n, out);
+    return cudaGetLastError();
+}
+
+}  // namespace ocmc

@@ -1,0 +1,367 @@
+// ocmc_device.cuh -- device building blocks of the transport kernel: the
+// counter-based RNG, table lookups from shared memory, interaction samplers
+// and voxel geometry. The test kernels use the same functions.
+#pragma once
+#include "ocmc_internal.h"
+
+namespace ocmc {
+
+// ---- Philox4x32-10 (Salmon et al. 2011) -----------------------------------------------
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+        uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return c;
+}
+
+// A particle's random stream: counter (n/4, history lo, history hi, sub-stream),
+// key = the run's seed. Draw n is word n mod 4 of that block, mapped to
+// ((x >> 8) + 1) 2^-24 in (0, 1]. The stream depends only on the particle, never
+// on the thread that transports it, so the dose is independent of scheduling.
+struct Rng {
+    uint32_t h0, h1, sub, n, blk;
+    uint4 buf;
+};
+
+__device__ __forceinline__ float rng_u(Rng& r, uint32_t k0, uint32_t k1)
+{
+    uint32_t b = r.n >> 2;
+    if (b != r.blk) {
+        r.buf = philox4x32_10(make_uint4(b, r.h0, r.h1, r.sub), k0, k1);
+        r.blk = b;
+    }
+    uint32_t i = r.n & 3u;
+    r.n++;
+    uint32_t x = i == 0 ? r.buf.x : (i == 1 ? r.buf.y : (i == 2 ? r.buf.z : r.buf.w));
+    return (float)((x >> 8) + 1u) * 5.9604644775390625e-08f;
+}
+
+__device__ __forceinline__ uint32_t child_sub(uint32_t parent, uint32_t n, uint32_t slot)
+{
+    uint32_t h = parent * 0x9E3779B1u ^ (n + 0x7F4A7C15u) * 0x85EBCA77u ^ (slot + 1u) * 0xC2B2AE3Du;
+    h ^= h >> 16; h *= 0x85EBCA6Bu; h ^= h >> 13; h *= 0xC2B2AE35u; h ^= h >> 16;
+    return h == 0u ? 1u : h;
+}
+
+// ---- tables in shared memory ---------------------------------------------------------------
+struct SmemTables {
+    float4* ph;     // NMAT*NE
+    float4* el;     // NMAT*NE
+    float2* el2;    // NMAT*NE
+    float* phmaj;   // NE
+    float* rinv;    // NMAT*NR
+    float* msA;     // NG
+    float* rmeta;   // NMAT*2
+    float* msc;     // NMAT*2
+};
+
+constexpr float LN_E_LO = -6.907755278982137f;              // ln(1e-3)
+constexpr float INV_DLNE = (float)((NE - 1) / 10.373491181781864);   // (NE-1) / ln(E_HI/E_LO)
+constexpr float LN_G_LO = -27.631021115928547f;             // ln(1e-12)
+constexpr float INV_DLNG = (float)((NG - 1) / (2.70805020110221 + 27.631021115928547));
+
+struct EIdx {
+    int i;
+    float f;
+};
+
+__device__ __forceinline__ EIdx e_index(float E)
+{
+    float x = (__logf(E) - LN_E_LO) * INV_DLNE;
+    x = fminf(fmaxf(x, 0.f), (float)(NE - 1) - 1e-3f);
+    EIdx r;
+    r.i = (int)x;
+    r.f = x - (float)r.i;
+    return r;
+}
+
+__device__ __forceinline__ float lerp1(float a, float b, float f) { return fmaf(f, b - a, a); }
+
+// ln E at ln R for material m (range-table inversion)
+__device__ __forceinline__ float range_to_lnE(const SmemTables& T, int m, float lnR)
+{
+    float x = (lnR - T.rmeta[2 * m]) * T.rmeta[2 * m + 1];
+    x = fminf(fmaxf(x, 0.f), (float)(NR - 1) - 1e-3f);
+    int j = (int)x;
+    float f = x - (float)j;
+    const float* r = T.rinv + m * NR;
+    return lerp1(r[j], r[j + 1], f);
+}
+
+// Energy after CSDA slowing over mass thickness X (g/cm^2) from energy E with
+// ln R(E) = lnR: E_end = E exp(g(ln(R - X)) - g(ln R)), g the inverse range
+// table; exact at X = 0 and monotone in X.
+__device__ __forceinline__ float csda_end(const SmemTables& T, int m, float E, float lnR, float X)
+{
+    float R = __expf(lnR);
+    float R1 = R - X;
+    if (!(R1 > 0.f)) return 0.f;
+    float g0 = range_to_lnE(T, m, lnR);
+    float g1 = range_to_lnE(T, m, __logf(R1));
+    return fminf(E, E * __expf(g1 - g0));
+}
+
+// ---- interaction samplers -------------------------------------------------------------------
+constexpr int SAMPLE_LIMIT = 10000;
+constexpr float MC2F = 0.51099895f;
+
+// Compton scattering: eps = E'/E from the Klein-Nishina cross section by the
+// Butcher-Messel decomposition (1/eps and eps envelopes with the rejection
+// factor 1 - eps sin^2 / (1 + eps^2)). Returns cos(theta); *eps_out = E'/E.
+__device__ __forceinline__ float sample_compton(float E, Rng& r, uint32_t k0, uint32_t k1, float* eps_out, bool* ok)
+{
+    float k = E / MC2F;
+    float e0 = 1.f / (1.f + 2.f * k);
+    float a1 = __logf(1.f + 2.f * k);
+    float a2 = 0.5f * (1.f - e0 * e0);
+    float eps = 1.f, t = 0.f;
+    for (int it = 0; it < SAMPLE_LIMIT; ++it) {
+        float r1 = rng_u(r, k0, k1), r2 = rng_u(r, k0, k1), r3 = rng_u(r, k0, k1);
+        if (r1 * (a1 + a2) < a1) eps = __expf(-a1 * r2);
+        else eps = sqrtf(e0 * e0 + (1.f - e0 * e0) * r2);
+        eps = fminf(fmaxf(eps, e0), 1.f);
+        t = (1.f - eps) / (k * eps);
+        float s2 = t * (2.f - t);
+        float g = 1.f - eps * s2 / (1.f + eps * eps);
+        if (r3 <= g) {
+            *eps_out = eps;
+            return fmaxf(-1.f, 1.f - t);
+        }
+    }
+    *ok = false;
+    *eps_out = 1.f;
+    return 1.f;
+}
+
+// Moller: eps = W/T on [w_cc/T, 1/2] from the 1/eps^2 envelope, accepted with
+// g(eps) / (2 + c/4), g = 1 + (eps/(1-eps))^2 + c eps^2 - d eps/(1-eps).
+__device__ __forceinline__ float sample_moller(float T, float wcc, Rng& r, uint32_t k0, uint32_t k1, bool* ok)
+{
+    float tau = T / MC2F, g = tau + 1.f;
+    float c = (tau / g) * (tau / g), d = (2.f * tau + 1.f) / (g * g);
+    float e0 = wcc / T, gmax = 2.f + 0.25f * c;
+    for (int it = 0; it < SAMPLE_LIMIT; ++it) {
+        float r1 = rng_u(r, k0, k1), r2 = rng_u(r, k0, k1);
+        float eps = e0 / (1.f - r1 * (1.f - 2.f * e0));
+        eps = fminf(fmaxf(eps, e0), 0.5f);
+        float q = eps / (1.f - eps);
+        float gv = 1.f + q * q + c * eps * eps - d * q;
+        if (r2 * gmax <= gv) return eps;
+    }
+    *ok = false;
+    return e0;
+}
+
+// Bremsstrahlung photon energy on [w_cb, T] from the 1/k envelope, accepted with
+// [(4/3 - 4/3 y + y^2) S1 + (1 - y) S2] / (4/3 S1 + S2), y = k / (T + mc^2).
+__device__ __forceinline__ float sample_brems(float T, float wcb, float S1, float S2, Rng& r, uint32_t k0, uint32_t k1,
+                                              bool* ok)
+{
+    float E = T + MC2F, lr = __logf(T / wcb);
+    float gmax = (4.f / 3.f) * S1 + S2;
+    for (int it = 0; it < SAMPLE_LIMIT; ++it) {
+        float r1 = rng_u(r, k0, k1), r2 = rng_u(r, k0, k1);
+        float k = fminf(wcb * __expf(r1 * lr), T);
+        float y = k / E;
+        float gv = (4.f / 3.f - (4.f / 3.f) * y + y * y) * S1 + (1.f - y) * S2;
+        if (r2 * gmax <= gv) return fmaxf(k, wcb);
+    }
+    *ok = false;
+    return wcb;
+}
+
+// Multiple-scattering cos(theta) for G1 = s / lambda_1: Wentzel distribution with
+// screening A chosen so that <1 - cos> = 1 - exp(-G1) (table of ln A at ln G1).
+__device__ __forceinline__ float sample_ms(const SmemTables& T, float G1, Rng& r, uint32_t k0, uint32_t k1)
+{
+    if (!(G1 >= 1e-12f)) return 1.f;
+    float xi = rng_u(r, k0, k1);
+    if (G1 >= 15.f) return 2.f * xi - 1.f;
+    float x = (__logf(G1) - LN_G_LO) * INV_DLNG;
+    x = fminf(fmaxf(x, 0.f), (float)(NG - 1) - 1e-3f);
+    int j = (int)x;
+    float A = __expf(lerp1(T.msA[j], T.msA[j + 1], x - (float)j));
+    float q = 1.f - xi;                              // [0, 1)
+    float u = 2.f * A * q / (1.f + A - q);
+    return fmaxf(-1.f, 1.f - u);
+}
+
+// Rotate unit direction (u,v,w) by polar cosine mu and azimuth phi = 2 pi xi.
+__device__ __forceinline__ void rotate(float& u, float& v, float& w, float mu, float xi)
+{
+    float st = sqrtf(fmaxf(0.f, 1.f - mu * mu));
+    float sp, cp;
+    __sincosf(6.283185307179586f * xi, &sp, &cp);
+    float s = sqrtf(fmaxf(0.f, 1.f - w * w));
+    float nu, nv, nw;
+    if (s > 1e-5f) {
+        float is = 1.f / s;
+        nu = u * mu + st * (u * w * cp - v * sp) * is;
+        nv = v * mu + st * (v * w * cp + u * sp) * is;
+        nw = w * mu - s * st * cp;
+    } else {
+        float sg = w >= 0.f ? 1.f : -1.f;
+        nu = st * cp;
+        nv = st * sp;
+        nw = sg * mu;
+    }
+    float inv = rsqrtf(nu * nu + nv * nv + nw * nw);
+    u = nu * inv;
+    v = nv * inv;
+    w = nw * inv;
+}
+
+// ---- voxel geometry -----------------------------------------------------------------------
+// Distance from (x,y,z) along (u,v,w) to the faces of voxel (ix,iy,iz);
+// *face = axis*2 + (direction > 0).
+__device__ __forceinline__ float dist_to_face(float x, float y, float z, float u, float v, float w, int ix, int iy,
+                                              int iz, float dx, float dy, float dz, int* face)
+{
+    float best = 3.0e38f;
+    int f = 0;
+    if (u != 0.f) {
+        float t = ((u > 0.f ? (float)(ix + 1) : (float)ix) * dx - x) / u;
+        t = fmaxf(t, 0.f);
+        if (t < best) { best = t; f = u > 0.f ? 1 : 0; }
+    }
+    if (v != 0.f) {
+        float t = ((v > 0.f ? (float)(iy + 1) : (float)iy) * dy - y) / v;
+        t = fmaxf(t, 0.f);
+        if (t < best) { best = t; f = v > 0.f ? 3 : 2; }
+    }
+    if (w != 0.f) {
+        float t = ((w > 0.f ? (float)(iz + 1) : (float)iz) * dz - z) / w;
+        t = fmaxf(t, 0.f);
+        if (t < best) { best = t; f = w > 0.f ? 5 : 4; }
+    }
+    *face = f;
+    return best;
+}
+
+}  // namespace ocmc
+
+namespace ocmc {
+
+// ---- shared-memory staging of the tables ------------------------------------------------
+constexpr size_t SMEM_TABLE_BYTES =
+    (size_t)NMAT * NE * (sizeof(float4) * 2 + sizeof(float2)) + (size_t)(NE + NMAT * NR + NG + 4 * NMAT) * sizeof(float);
+
+__device__ __forceinline__ SmemTables carve_tables(unsigned char* smem)
+{
+    SmemTables T;
+    T.ph = reinterpret_cast<float4*>(smem);
+    T.el = T.ph + NMAT * NE;
+    T.el2 = reinterpret_cast<float2*>(T.el + NMAT * NE);
+    T.phmaj = reinterpret_cast<float*>(T.el2 + NMAT * NE);
+    T.rinv = T.phmaj + NE;
+    T.msA = T.rinv + NMAT * NR;
+    T.rmeta = T.msA + NG;
+    T.msc = T.rmeta + 2 * NMAT;
+    return T;
+}
+
+__device__ __forceinline__ SmemTables stage_tables(const Tables& t, unsigned char* smem)
+{
+    SmemTables T = carve_tables(smem);
+    for (int i = threadIdx.x; i < NMAT * NE; i += blockDim.x) {
+        T.ph[i] = t.ph[i];
+        T.el[i] = t.el[i];
+        T.el2[i] = t.el2[i];
+    }
+    for (int i = threadIdx.x; i < NE; i += blockDim.x) T.phmaj[i] = t.phmaj[i];
+    for (int i = threadIdx.x; i < NMAT * NR; i += blockDim.x) T.rinv[i] = t.rinv[i];
+    for (int i = threadIdx.x; i < NG; i += blockDim.x) T.msA[i] = t.msA[i];
+    if (threadIdx.x < 2 * NMAT) {
+        T.rmeta[threadIdx.x] = t.rmeta[threadIdx.x];
+        T.msc[threadIdx.x] = t.msc[threadIdx.x];
+    }
+    __syncthreads();
+    return T;
+}
+
+// ---- particle state in registers ------------------------------------------------------------
+enum { PHOTON = 0, ELECTRON = 1, POSITRON = 2 };
+
+struct Lane {
+    float x, y, z, u, v, w, E;
+    int ix, iy, iz, type, batch, steps;
+    Rng r;
+};
+
+__device__ __forceinline__ int batch_of(uint32_t h0, uint32_t h1, int B)
+{
+    unsigned long long h = ((unsigned long long)h1 << 32) | h0;
+    return (int)(h % (unsigned long long)B);
+}
+
+// Source particle of history h (Sec. 2.2 "Materials": point source at SSD with the
+// field defined at the surface, or a parallel beam; energy bins in decreasing
+// energy, Sec. 2.2.1). Draws: energy within the bin, then the two field
+// coordinates. Returns false if the ray misses the phantom; p.E is set either way.
+__device__ __forceinline__ bool init_primary(const TransportArgs& a, unsigned long long h, Lane& p)
+{
+    const SourceDev& s = a.src;
+    p.r.h0 = (uint32_t)h;
+    p.r.h1 = (uint32_t)(h >> 32);
+    p.r.sub = 0u;
+    p.r.n = 0u;
+    p.r.blk = 0xFFFFFFFFu;
+    p.type = s.particle == 0 ? PHOTON : ELECTRON;
+    p.batch = batch_of(p.r.h0, p.r.h1, a.pp.n_batches);
+    p.steps = 0;
+    int lo = 0, hi = s.n_bins - 1;               // last q with bound[q] <= h
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (s.bound[mid] <= h) lo = mid; else hi = mid - 1;
+    }
+    int bin = s.order[lo];
+    float e0 = s.lo[bin], e1 = s.hi[bin];
+    p.E = e0 + rng_u(p.r, a.key0, a.key1) * (e1 - e0);
+    float fa = rng_u(p.r, a.key0, a.key1) - 0.5f, fb = rng_u(p.r, a.key0, a.key1) - 0.5f;
+    float P[3], O[3], d[3];
+    for (int k = 0; k < 3; ++k) P[k] = s.iso[k] + fa * s.fx * s.e1[k] + fb * s.fy * s.e2[k];
+    float tmin;
+    if (s.ssd > 0.f) {
+        for (int k = 0; k < 3; ++k) { O[k] = s.iso[k] - s.ssd * s.dir[k]; d[k] = P[k] - O[k]; }
+        float inv = rsqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+        for (int k = 0; k < 3; ++k) d[k] *= inv;
+        tmin = 0.f;
+    } else {
+        for (int k = 0; k < 3; ++k) { O[k] = P[k]; d[k] = s.dir[k]; }
+        tmin = -3.0e38f;
+    }
+    const float Lb[3] = {a.nx * a.dx, a.ny * a.dy, a.nz * a.dz};
+    float tmax = 3.0e38f;
+    int ent = -1;
+    for (int k = 0; k < 3; ++k) {
+        if (fabsf(d[k]) < 1e-30f) {
+            if (O[k] < 0.f || O[k] > Lb[k]) return false;
+            continue;
+        }
+        float t1 = (0.f - O[k]) / d[k], t2 = (Lb[k] - O[k]) / d[k];
+        float tn = fminf(t1, t2), tx = fmaxf(t1, t2);
+        if (tn > tmin) { tmin = tn; ent = k * 2 + (t1 < t2 ? 0 : 1); }
+        tmax = fminf(tmax, tx);
+    }
+    if (!(tmax > tmin)) return false;
+    p.x = O[0] + tmin * d[0];
+    p.y = O[1] + tmin * d[1];
+    p.z = O[2] + tmin * d[2];
+    if (ent >= 0) {                              // put the entry point exactly on its face
+        float f = (ent & 1) ? Lb[ent >> 1] : 0.f;
+        if ((ent >> 1) == 0) p.x = f; else if ((ent >> 1) == 1) p.y = f; else p.z = f;
+    }
+    p.u = d[0]; p.v = d[1]; p.w = d[2];
+    p.ix = min(max((int)floorf(p.x / a.dx), 0), a.nx - 1);
+    p.iy = min(max((int)floorf(p.y / a.dy), 0), a.ny - 1);
+    p.iz = min(max((int)floorf(p.z / a.dz), 0), a.nz - 1);
+    return true;
+}
+
+}  // namespace ocmc

@@ -1,0 +1,137 @@
+// ocmc_internal.h -- definitions shared by the engine's translation units.
+//
+// Physics tables: per material (0 water, 1 cortical bone, 2 lung), NE nodes
+// uniform in ln E on [E_LO, E_HI], quantities per unit density (g/cm^3):
+//   ph[m][i]  = { ln mu_total, mu_C / mu_total, mu_pe / mu_total, mu_total }   (cm^2/g)
+//   el[m][i]  = { ln R, 1/lambda_1, sigma_Moller, sigma_brems }                (R in g/cm^2)
+//   el2[m][i] = { R(E_i) - R(E_i (1 - f_maxe)), hard-event majorant on [E_i, E_i+1) }
+//   rinv[m][j] = ln E at ln R = lnR0[m] + j dlnR[m], j < NR
+//   msA[j]     = ln A (Wentzel screening) at ln G1 = ln G1_LO + j dlnG
+//   phmaj[i]   = ln mu_max(E_i): photon Woodcock majorant over the phantom (1/cm)
+//   msc[m]     = { S1, S2 }: bremsstrahlung spectrum constants (per gram)
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace ocmc {
+
+constexpr int NE = 512;
+constexpr int NR = 512;
+constexpr int NG = 512;
+constexpr int NMAT = 3;
+constexpr int MAX_BINS = 256;
+constexpr double E_LO = 1.0e-3;   // MeV
+constexpr double E_HI = 32.0;     // MeV
+constexpr double G1_LO = 1.0e-12; // below: no deflection
+constexpr double G1_ISO = 15.0;   // at and above: isotropic deflection
+constexpr double MC2 = 0.51099895000;
+constexpr float TALLY_SCALE = 268435456.0f;   // 2^28 fixed-point units per MeV
+constexpr int MAX_DIM = 1024;
+
+// error bits written by kernels
+constexpr int ERR_OVERFLOW = 1;
+constexpr int ERR_LIMIT = 2;
+constexpr int ERR_PHANTOM = 4;
+
+// run statistics slots (uint64, device)
+enum Stat {
+    ST_FICT = 0, ST_COMPTON, ST_PHOTO, ST_PAIR, ST_MOLLER, ST_BREMS, ST_HARD_FICT,
+    ST_ANNIH, ST_ESCAPED, ST_MISSED, ST_GEO, ST_VIOL, ST_DROPPED, ST_TRANSMITTED,
+    ST_WARP_ITERS, ST_LANES_PHOTON, ST_LANES_CHARGED, ST_HISTORIES,
+    // fixed-point energies (2^28 units per MeV)
+    ST_E_IN, ST_E_ESC, ST_E_MISS, ST_E_KILLED, ST_E_TRANS, ST_E_DROPPED,
+    ST_COUNT
+};
+
+struct Tables {
+    float4* ph;     // NMAT*NE
+    float* phmaj;   // NE
+    float4* el;     // NMAT*NE
+    float2* el2;    // NMAT*NE
+    float* rinv;    // NMAT*NR
+    float* msA;     // NG
+    float* rmeta;   // NMAT*2: lnR0, 1/dlnR
+    float* msc;     // NMAT*2: bremsstrahlung screening sums S1, S2 (per gram)
+    double* scratch;        // NMAT*NE interval ranges
+    unsigned int* rho_max;  // NMAT, float bits of the max density per material
+};
+
+// Per-material composition for the table builder (public compositions:
+// water H2O; ICRP cortical bone; ICRP lung).
+struct MatDef {
+    int n;
+    int Z[13];
+    double A[13];
+    double w[13];
+    double I_eV;
+    double rho0;
+};
+
+struct PhysParams {
+    float e_abs_e, e_abs_g, w_cc, w_cb, d_maxs, f_maxe, s_min;
+    int flags;
+    int n_batches;
+};
+
+// 48-byte particle record of the secondary stacks.
+struct __align__(16) PRec {
+    float x, y, z, E;
+    float u, v, w;
+    uint32_t vt;     // ix | iy << 10 | iz << 20 | type << 30
+    uint32_t h0, h1, sub, n;
+};
+
+struct SourceDev {
+    int particle;            // 0 photon, 1 electron
+    int n_bins;
+    float fx, fy, ssd;
+    float iso[3], e1[3], e2[3], dir[3];
+    unsigned long long bound[MAX_BINS + 1];   // stratification bounds (history ids)
+    int order[MAX_BINS];                      // bin processed at position q
+    float lo[MAX_BINS], hi[MAX_BINS];         // bin edges
+};
+
+struct TransportArgs {
+    // geometry
+    int nx, ny, nz;
+    float dx, dy, dz;
+    const float* density;
+    const uint8_t* material;
+    long long nvox;
+    // tables
+    Tables t;
+    PhysParams pp;
+    // run
+    unsigned long long first, count, n_total;
+    uint32_t key0, key1;
+    unsigned long long* tally;
+    // scratch
+    PRec* stacks;               // per warp: 2 stacks of `cap` records
+    int cap;
+    int switch_high, switch_low;
+    unsigned long long* hist_counter;
+    unsigned long long* stats;  // ST_COUNT
+    int* err;
+    SourceDev src;
+};
+
+// kernels / launchers (defined in the .cu files)
+cudaError_t build_tables(const Tables& t, const PhysParams& pp, const float* density, const uint8_t* material,
+                         long long nvox, int* d_err, cudaStream_t s);
+cudaError_t launch_transport(const TransportArgs& a, int blocks, int threads, size_t smem, cudaStream_t s);
+size_t transport_smem_bytes(int threads);
+int transport_max_blocks_per_sm(int threads, size_t smem);
+cudaError_t launch_finalize(const long long* tally, const float* density, int B, long long nvox, double voxel_volume,
+                            const double* inv_nb, double inv_n, float* dose, float* sigma, cudaStream_t s);
+cudaError_t launch_test_philox(uint32_t key0, uint32_t key1, uint32_t c1, uint32_t c2, uint32_t c3,
+                               uint32_t first_block, uint32_t n_blocks, uint32_t* out, cudaStream_t s);
+cudaError_t launch_test_source(const TransportArgs& a, unsigned long long n_total, unsigned long long first,
+                               unsigned long long count, float* out, cudaStream_t s);
+cudaError_t launch_test_sample(const TransportArgs& a, int kind, int m, float E, float aux, unsigned long long n,
+                               float* out, cudaStream_t s);
+cudaError_t launch_test_tables(const TransportArgs& a, int m, const float* E, int n, float* out, cudaStream_t s);
+cudaError_t launch_test_csda(const TransportArgs& a, int m, const float* T, const float* X, int n, float* out,
+                             cudaStream_t s);
+void material_defs(MatDef out[NMAT]);
+
+}  // namespace ocmc

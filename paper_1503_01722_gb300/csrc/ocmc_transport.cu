@@ -1,0 +1,483 @@
+// ocmc_transport.cu -- persistent coupled photon-electron transport kernel.
+//
+// Method (Tian et al., Sec. 2.1): photons fly by Woodcock tracking against a
+// phantom-wide majorant and interact by Compton scattering, photoelectric
+// absorption or pair production; electrons and positrons take Class II
+// condensed-history steps d = min(d_vox, d_maxs, d_maxe, d_event), each inside
+// one voxel, with a random-hinge multiple-scattering deflection, CSDA energy
+// loss deposited in the step's voxel, and discrete Moller / bremsstrahlung
+// events sampled by Woodcock tracking in energy; positrons annihilate into two
+// photons at the end of their track.
+//
+// Scheduling (Sec. 2.2.1, Table 1): the paper launches batches of up to M
+// particles of one type, taken from the photon stack, the electron stack or
+// the source. Here every warp runs that loop by itself inside one persistent
+// launch: its 32 lanes always hold particles of one type (warp mode); free
+// lanes refill from the warp's own stack of that type, then from the source
+// (energy-sorted history ids from a global counter); the warp switches type
+// when its lanes run dry or the other stack grows large. Secondaries are
+// pushed to the warp's stacks. A warp ends when the source is exhausted and
+// its stacks are empty; no warp ever waits on another.
+//
+// Dose tally (Sec. 2.2.2): 64-bit fixed-point integer atomics (2^-28 MeV
+// units) into the tally of batch (history id mod B). Integer addition is
+// associative and every particle's random stream is keyed by its lineage, so
+// the tally is bit-identical for any launch configuration and timing.
+#include "ocmc_device.cuh"
+
+namespace ocmc {
+
+namespace {
+
+constexpr unsigned FULL = 0xFFFFFFFFu;
+constexpr int MAX_WARPS = 32;
+constexpr int STEP_LIMIT = 1 << 22;
+
+struct Ctx {
+    const TransportArgs& a;
+    const SmemTables& T;
+    PRec* stk;                   // warp's stacks: [0, cap) photons, [cap, 2cap) charged
+    int* top;                    // shared: top[0] photons, top[1] charged
+    unsigned long long* st;      // shared block statistics
+    float inv_dx, inv_dy, inv_dz, Lx, Ly, Lz;
+    bool ok;
+};
+
+__device__ __forceinline__ void stat_add(Ctx& c, int k, unsigned long long v) { atomicAdd(c.st + k, v); }
+
+__device__ __forceinline__ unsigned long long fx(float e) { return (unsigned long long)__float2ll_rn(e * TALLY_SCALE); }
+
+__device__ __forceinline__ void deposit(Ctx& c, int batch, int ix, int iy, int iz, float dE)
+{
+    if (dE > 0.f) {
+        long long v = ix + (long long)c.a.nx * (iy + (long long)c.a.ny * iz);
+        atomicAdd(c.a.tally + (long long)batch * c.a.nvox + v, fx(dE));
+    }
+}
+
+__device__ __forceinline__ void push(Ctx& c, int t, float x, float y, float z, float E, float u, float v, float w, int ix,
+                                     int iy, int iz, int type, uint32_t h0, uint32_t h1, uint32_t sub)
+{
+    int slot = atomicAdd(c.top + t, 1);
+    if (slot >= c.a.cap) {
+        atomicOr(c.a.err, ERR_OVERFLOW);
+        stat_add(c, ST_DROPPED, 1);
+        stat_add(c, ST_E_DROPPED, fx(E));
+        return;
+    }
+    PRec* r = c.stk + (size_t)t * c.a.cap + slot;
+    uint32_t vt = (uint32_t)ix | ((uint32_t)iy << 10) | ((uint32_t)iz << 20) | ((uint32_t)type << 30);
+    uint4* q = reinterpret_cast<uint4*>(r);
+    q[0] = make_uint4(__float_as_uint(x), __float_as_uint(y), __float_as_uint(z), __float_as_uint(E));
+    q[1] = make_uint4(__float_as_uint(u), __float_as_uint(v), __float_as_uint(w), vt);
+    q[2] = make_uint4(h0, h1, sub, 0u);
+}
+
+__device__ __forceinline__ void push_lane(Ctx& c, int t, const Lane& p)
+{
+    int slot = atomicAdd(c.top + t, 1);
+    if (slot >= c.a.cap) {
+        atomicOr(c.a.err, ERR_OVERFLOW);
+        stat_add(c, ST_DROPPED, 1);
+        stat_add(c, ST_E_DROPPED, fx(p.E));
+        return;
+    }
+    PRec* r = c.stk + (size_t)t * c.a.cap + slot;
+    uint32_t vt = (uint32_t)p.ix | ((uint32_t)p.iy << 10) | ((uint32_t)p.iz << 20) | ((uint32_t)p.type << 30);
+    uint4* q = reinterpret_cast<uint4*>(r);
+    q[0] = make_uint4(__float_as_uint(p.x), __float_as_uint(p.y), __float_as_uint(p.z), __float_as_uint(p.E));
+    q[1] = make_uint4(__float_as_uint(p.u), __float_as_uint(p.v), __float_as_uint(p.w), vt);
+    q[2] = make_uint4(p.r.h0, p.r.h1, p.r.sub, p.r.n);
+}
+
+__device__ __forceinline__ void pop_lane(const Ctx& c, int t, int slot, Lane& p)
+{
+    const uint4* q = reinterpret_cast<const uint4*>(c.stk + (size_t)t * c.a.cap + slot);
+    uint4 a = q[0], b = q[1], d = q[2];
+    p.x = __uint_as_float(a.x); p.y = __uint_as_float(a.y); p.z = __uint_as_float(a.z); p.E = __uint_as_float(a.w);
+    p.u = __uint_as_float(b.x); p.v = __uint_as_float(b.y); p.w = __uint_as_float(b.z);
+    p.ix = b.w & 1023u; p.iy = (b.w >> 10) & 1023u; p.iz = (b.w >> 20) & 1023u; p.type = b.w >> 30;
+    p.r.h0 = d.x; p.r.h1 = d.y; p.r.sub = d.z; p.r.n = d.w; p.r.blk = 0xFFFFFFFFu;
+    p.batch = batch_of(d.x, d.y, c.a.pp.n_batches);
+    p.steps = 0;
+}
+
+__device__ __forceinline__ void escape(Ctx& c, const Lane& p)
+{
+    stat_add(c, ST_ESCAPED, 1);
+    stat_add(c, ST_E_ESC, fx(p.E));
+}
+
+// e-/e+ created at p's position with energy E and direction d: pushed if above the
+// absorption energy, otherwise deposited (a positron then annihilates).
+__device__ void emit_charged(Ctx& c, const Lane& p, int type, float E, float du, float dv, float dw, uint32_t slot);
+
+// Two photons of mc^2, back to back and isotropic, from a positron with stream r.
+__device__ __forceinline__ void annihilate(Ctx& c, const Lane& p, Rng& r)
+{
+    float wc = 2.f * rng_u(r, c.a.key0, c.a.key1) - 1.f, xi = rng_u(r, c.a.key0, c.a.key1);
+    float st = sqrtf(fmaxf(0.f, 1.f - wc * wc)), sp, cp;
+    __sincosf(6.283185307179586f * xi, &sp, &cp);
+    stat_add(c, ST_ANNIH, 1);
+    if (MC2F >= c.a.pp.e_abs_g) {
+        push(c, 0, p.x, p.y, p.z, MC2F, st * cp, st * sp, wc, p.ix, p.iy, p.iz, PHOTON, r.h0, r.h1,
+             child_sub(r.sub, r.n, 0));
+        push(c, 0, p.x, p.y, p.z, MC2F, -st * cp, -st * sp, -wc, p.ix, p.iy, p.iz, PHOTON, r.h0, r.h1,
+             child_sub(r.sub, r.n, 1));
+    } else {
+        deposit(c, p.batch, p.ix, p.iy, p.iz, 2.f * MC2F);
+    }
+}
+
+__device__ void emit_charged(Ctx& c, const Lane& p, int type, float E, float du, float dv, float dw, uint32_t slot)
+{
+    uint32_t sub = child_sub(p.r.sub, p.r.n, slot);
+    if (E >= c.a.pp.e_abs_e && !(c.a.pp.flags & 8)) {
+        push(c, 1, p.x, p.y, p.z, E, du, dv, dw, p.ix, p.iy, p.iz, type, p.r.h0, p.r.h1, sub);
+        return;
+    }
+    deposit(c, p.batch, p.ix, p.iy, p.iz, E);
+    if (type == POSITRON) {
+        Rng r;
+        r.h0 = p.r.h0; r.h1 = p.r.h1; r.sub = sub; r.n = 0; r.blk = 0xFFFFFFFFu;
+        annihilate(c, p, r);
+    }
+}
+
+// One Woodcock flight and, if real, the interaction. Returns false when the photon ends.
+__device__ __forceinline__ bool photon_step(Ctx& c, Lane& p, unsigned& n_fict)
+{
+    const TransportArgs& a = c.a;
+    const SmemTables& T = c.T;
+    const uint32_t k0 = a.key0, k1 = a.key1;
+    EIdx ei = e_index(p.E);
+    float lnmaj = lerp1(T.phmaj[ei.i], T.phmaj[ei.i + 1], ei.f);
+    if (lnmaj < -1e29f) { escape(c, p); return false; }
+    float mumax = __expf(lnmaj);
+    float s = -__logf(rng_u(p.r, k0, k1)) / mumax;
+    p.x = fmaf(s, p.u, p.x);
+    p.y = fmaf(s, p.v, p.y);
+    p.z = fmaf(s, p.w, p.z);
+    if (!(p.x >= 0.f && p.y >= 0.f && p.z >= 0.f && p.x <= c.Lx && p.y <= c.Ly && p.z <= c.Lz)) {
+        if ((a.pp.flags & 4) && p.z > c.Lz) {
+            stat_add(c, ST_TRANSMITTED, 1);
+            stat_add(c, ST_E_TRANS, fx(p.E));
+        }
+        escape(c, p);
+        return false;
+    }
+    p.ix = min((int)(p.x * c.inv_dx), a.nx - 1);
+    p.iy = min((int)(p.y * c.inv_dy), a.ny - 1);
+    p.iz = min((int)(p.z * c.inv_dz), a.nz - 1);
+    long long vox = p.ix + (long long)a.nx * (p.iy + (long long)a.ny * p.iz);
+    float rho = __ldg(a.density + vox);
+    int m = __ldg(a.material + vox);
+    float4 pa = T.ph[m * NE + ei.i], pb = T.ph[m * NE + ei.i + 1];
+    float mu = rho * __expf(lerp1(pa.x, pb.x, ei.f));
+    if (mu > mumax * 1.00001f) stat_add(c, ST_VIOL, 1);
+    if (rng_u(p.r, k0, k1) * mumax >= mu) { n_fict++; return true; }
+    if (a.pp.flags & 4) { stat_add(c, ST_E_KILLED, fx(p.E)); return false; }
+    float fC = lerp1(pa.y, pb.y, ei.f), fP = lerp1(pa.z, pb.z, ei.f);
+    float xi = rng_u(p.r, k0, k1);
+    if (xi >= fC && xi < fC + fP) {
+        stat_add(c, ST_PHOTO, 1);
+        deposit(c, p.batch, p.ix, p.iy, p.iz, p.E);
+        return false;
+    }
+    if (xi >= fC + fP && p.E > 2.f * MC2F) {
+        stat_add(c, ST_PAIR, 1);
+        float avail = p.E - 2.f * MC2F;
+        float Tm = rng_u(p.r, k0, k1) * avail, Tp = avail - Tm;
+        emit_charged(c, p, ELECTRON, Tm, p.u, p.v, p.w, 0);
+        emit_charged(c, p, POSITRON, Tp, p.u, p.v, p.w, 1);
+        return false;
+    }
+    // Compton scattering (also the rare pair selection below threshold from table interpolation)
+    stat_add(c, ST_COMPTON, 1);
+    float eps;
+    float cth = sample_compton(p.E, p.r, k0, k1, &eps, &c.ok);
+    float xphi = rng_u(p.r, k0, k1);
+    float E0 = p.E, E1 = eps * E0, Te = E0 - E1;
+    float u0 = p.u, v0 = p.v, w0 = p.w;
+    rotate(p.u, p.v, p.w, cth, xphi);
+    if (Te > 0.f) {
+        float qu = E0 * u0 - E1 * p.u, qv = E0 * v0 - E1 * p.v, qw = E0 * w0 - E1 * p.w;
+        float inv = rsqrtf(fmaxf(qu * qu + qv * qv + qw * qw, 1e-30f));
+        emit_charged(c, p, ELECTRON, Te, qu * inv, qv * inv, qw * inv, 0);
+    }
+    p.E = E1;
+    if (p.E < a.pp.e_abs_g) {
+        deposit(c, p.batch, p.ix, p.iy, p.iz, p.E);
+        return false;
+    }
+    return true;
+}
+
+__device__ __forceinline__ bool cross_face(const Ctx& c, Lane& p, int face)
+{
+    int ax = face >> 1;
+    bool up = face & 1;
+    if (ax == 0) { p.ix += up ? 1 : -1; p.x = (float)(up ? p.ix : p.ix + 1) * c.a.dx; }
+    else if (ax == 1) { p.iy += up ? 1 : -1; p.y = (float)(up ? p.iy : p.iy + 1) * c.a.dy; }
+    else { p.iz += up ? 1 : -1; p.z = (float)(up ? p.iz : p.iz + 1) * c.a.dz; }
+    return p.ix >= 0 && p.iy >= 0 && p.iz >= 0 && p.ix < c.a.nx && p.iy < c.a.ny && p.iz < c.a.nz;
+}
+
+// A charged particle that fell below its absorption energy.
+__device__ __forceinline__ void absorb_charged(Ctx& c, Lane& p)
+{
+    deposit(c, p.batch, p.ix, p.iy, p.iz, p.E);
+    if (p.type == POSITRON) annihilate(c, p, p.r);
+}
+
+// One condensed-history step. Returns false when the particle ends.
+__device__ __forceinline__ bool charged_step(Ctx& c, Lane& p, unsigned& n_hfict)
+{
+    const TransportArgs& a = c.a;
+    const SmemTables& T = c.T;
+    const uint32_t k0 = a.key0, k1 = a.key1;
+    long long vox = p.ix + (long long)a.nx * (p.iy + (long long)a.ny * p.iz);
+    float rho = __ldg(a.density + vox);
+    int m = __ldg(a.material + vox);
+    int face;
+    float sv = dist_to_face(p.x, p.y, p.z, p.u, p.v, p.w, p.ix, p.iy, p.iz, a.dx, a.dy, a.dz, &face);
+    if (!(rho > 0.f) || sv < a.pp.s_min) {
+        // nothing to interact with, or a boundary closer than s_min: cross geometrically
+        p.x = fmaf(sv, p.u, p.x);
+        p.y = fmaf(sv, p.v, p.y);
+        p.z = fmaf(sv, p.w, p.z);
+        stat_add(c, ST_GEO, 1);
+        if (!cross_face(c, p, face)) { escape(c, p); return false; }
+        return true;
+    }
+    EIdx ei = e_index(p.E);
+    const int mb = m * NE;
+    float4 A = T.el[mb + ei.i], B = T.el[mb + ei.i + 1];
+    float2 C = T.el2[mb + ei.i], D = T.el2[mb + ei.i + 1];
+    float lnR = lerp1(A.x, B.x, ei.f);
+    float s_maxe = lerp1(C.x, D.x, ei.f) / rho;
+    float sighat = (a.pp.flags & 1) ? 0.f : C.y;
+    float d_ev = sighat > 0.f ? -__logf(rng_u(p.r, k0, k1)) / (rho * sighat) : 3.0e38f;
+    float s = sv;
+    int lim = 0;
+    if (a.pp.d_maxs < s) { s = a.pp.d_maxs; lim = 1; }
+    if (s_maxe < s) { s = s_maxe; lim = 2; }
+    if (d_ev < s) { s = d_ev; lim = 3; }
+    // random hinge: s1 straight, deflect, then the rest (clipped to this voxel)
+    float s1 = rng_u(p.r, k0, k1) * s;
+    float hx = fmaf(s1, p.u, p.x), hy = fmaf(s1, p.v, p.y), hz = fmaf(s1, p.w, p.z);
+    float E0 = p.E;
+    float Efull = csda_end(T, m, E0, lnR, rho * s);
+    if (!(a.pp.flags & 2)) {
+        EIdx em = e_index(0.5f * (E0 + Efull));
+        float l1 = lerp1(T.el[mb + em.i].y, T.el[mb + em.i + 1].y, em.f);
+        float cth = sample_ms(T, rho * s * l1, p.r, k0, k1);
+        float xphi = rng_u(p.r, k0, k1);
+        rotate(p.u, p.v, p.w, cth, xphi);
+    }
+    int face2;
+    float tex = dist_to_face(hx, hy, hz, p.u, p.v, p.w, p.ix, p.iy, p.iz, a.dx, a.dy, a.dz, &face2);
+    float rem = s - s1, Eend;
+    bool crossed;
+    if (rem < tex) {
+        p.x = fmaf(rem, p.u, hx);
+        p.y = fmaf(rem, p.v, hy);
+        p.z = fmaf(rem, p.w, hz);
+        Eend = Efull;
+        crossed = false;
+    } else {
+        p.x = fmaf(tex, p.u, hx);
+        p.y = fmaf(tex, p.v, hy);
+        p.z = fmaf(tex, p.w, hz);
+        Eend = csda_end(T, m, E0, lnR, rho * (s1 + tex));
+        crossed = true;
+    }
+    deposit(c, p.batch, p.ix, p.iy, p.iz, E0 - Eend);
+    p.E = Eend;
+    if (crossed && !cross_face(c, p, face2)) { escape(c, p); return false; }
+    if (p.E < a.pp.e_abs_e) { absorb_charged(c, p); return false; }
+    if (lim == 3 && !crossed) {
+        EIdx e2 = e_index(p.E);
+        float4 A2 = T.el[mb + e2.i], B2 = T.el[mb + e2.i + 1];
+        float sM = p.E > 2.f * a.pp.w_cc ? lerp1(A2.z, B2.z, e2.f) : 0.f;
+        float sB = p.E > a.pp.w_cb ? lerp1(A2.w, B2.w, e2.f) : 0.f;
+        float tot = sM + sB;
+        if (tot > sighat * 1.00001f) stat_add(c, ST_VIOL, 1);
+        if (rng_u(p.r, k0, k1) * sighat < tot) {
+            if (rng_u(p.r, k0, k1) * tot < sM) {
+                stat_add(c, ST_MOLLER, 1);
+                float Tk = p.E;
+                float eps = sample_moller(Tk, a.pp.w_cc, p.r, k0, k1, &c.ok);
+                float W = eps * Tk, T1 = Tk - W;
+                float xphi = rng_u(p.r, k0, k1);
+                float mu1 = sqrtf(fminf(1.f, T1 * (Tk + 2.f * MC2F) / (Tk * (T1 + 2.f * MC2F))));
+                float mu2 = sqrtf(fminf(1.f, W * (Tk + 2.f * MC2F) / (Tk * (W + 2.f * MC2F))));
+                float su = p.u, sv2 = p.v, sw = p.w;
+                rotate(su, sv2, sw, mu2, xphi + 0.5f);
+                emit_charged(c, p, ELECTRON, W, su, sv2, sw, 2);
+                rotate(p.u, p.v, p.w, mu1, xphi);
+                p.E = T1;
+            } else {
+                stat_add(c, ST_BREMS, 1);
+                float Tk = p.E;
+                float k = sample_brems(Tk, a.pp.w_cb, T.msc[2 * m], T.msc[2 * m + 1], p.r, k0, k1, &c.ok);
+                float th = MC2F / (Tk + MC2F);
+                float xphi = rng_u(p.r, k0, k1);
+                float gu = p.u, gv = p.v, gw = p.w;
+                rotate(gu, gv, gw, __cosf(th), xphi);
+                if (k >= a.pp.e_abs_g)
+                    push(c, 0, p.x, p.y, p.z, k, gu, gv, gw, p.ix, p.iy, p.iz, PHOTON, p.r.h0, p.r.h1,
+                         child_sub(p.r.sub, p.r.n, 3));
+                else
+                    deposit(c, p.batch, p.ix, p.iy, p.iz, k);
+                p.E = Tk - k;
+            }
+            if (p.E < a.pp.e_abs_e) { absorb_charged(c, p); return false; }
+        } else {
+            n_hfict++;
+        }
+    }
+    return true;
+}
+
+__global__ void __launch_bounds__(256) k_transport(const TransportArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int s_top[MAX_WARPS][2];
+    __shared__ unsigned long long s_st[ST_COUNT];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    for (int i = threadIdx.x; i < ST_COUNT; i += blockDim.x) s_st[i] = 0ull;
+    if (lane == 0) { s_top[wib][0] = 0; s_top[wib][1] = 0; }
+    SmemTables T = stage_tables(a.t, smem);   // ends with __syncthreads()
+
+    const long long gw = (long long)blockIdx.x * (blockDim.x >> 5) + wib;
+    Ctx c{a, T, a.stacks + (size_t)gw * 2 * a.cap, s_top[wib], s_st,
+          1.f / a.dx, 1.f / a.dy, 1.f / a.dz, a.nx * a.dx, a.ny * a.dy, a.nz * a.dz, true};
+    const unsigned lt = (1u << lane) - 1u;
+    const int src_mode = a.src.particle == 0 ? 0 : 1;
+    int mode = src_mode;
+    bool src_done = a.count == 0;
+    bool active = false, just_switched = false;
+    Lane p;
+    unsigned n_fict = 0, n_hfict = 0;
+    unsigned long long iters = 0, lanes_ph = 0, lanes_ch = 0, hist = 0, e_in = 0, e_miss = 0, missed = 0;
+
+    for (;;) {
+        __syncwarp();
+        int top0 = min(c.top[0], a.cap), top1 = min(c.top[1], a.cap);
+        unsigned act = __ballot_sync(FULL, active);
+        int nfree = 32 - __popc(act);
+        if (nfree > 0) {
+            int topm = mode ? top1 : top0;
+            int rank = __popc(~act & lt);
+            int take = min(nfree, topm);
+            if (!active && rank < take) {
+                pop_lane(c, mode, topm - 1 - rank, p);
+                active = true;
+            }
+            int want = nfree - take;
+            if (want > 0 && mode == src_mode && !src_done) {
+                unsigned long long base = 0;
+                if (lane == 0) base = atomicAdd(a.hist_counter, (unsigned long long)want);
+                base = __shfl_sync(FULL, base, 0);
+                if (base + want >= a.count) src_done = true;
+                int r2 = rank - take;
+                if (!active && r2 >= 0 && r2 < want && base + r2 < a.count) {
+                    hist++;
+                    bool in = init_primary(a, a.first + base + r2, p);
+                    float ecut = p.type == PHOTON ? a.pp.e_abs_g : a.pp.e_abs_e;
+                    if (!in) {
+                        missed++;
+                        e_miss += fx(p.E);
+                    } else {
+                        e_in += fx(p.E);
+                        if (p.E >= ecut && !(p.type != PHOTON && (a.pp.flags & 8))) active = true;
+                        else deposit(c, p.batch, p.ix, p.iy, p.iz, p.E);
+                    }
+                }
+            }
+            __syncwarp();
+            if (lane == 0) c.top[mode] = topm - take;
+            __syncwarp();
+            if (mode) top1 = topm - take; else top0 = topm - take;
+            act = __ballot_sync(FULL, active);
+        }
+        int nact = __popc(act);
+        int other = 1 - mode;
+        int topm = mode ? top1 : top0, topo = mode ? top0 : top1;
+        bool m_avail = topm > 0 || (mode == src_mode && !src_done);
+        bool o_avail = topo > 0 || (other == src_mode && !src_done);
+        if (nact == 0) {
+            if (m_avail) continue;
+            if (o_avail) { mode = other; continue; }
+            break;
+        }
+        bool sw = false;
+        if (o_avail && !just_switched) {     // at most one switch between two steps
+            // the other group must be strictly larger (or the source), so a switch is never undone at once
+            if (!m_avail && nact <= a.switch_low && (topo > nact || (other == src_mode && !src_done))) sw = true;
+            else if (topo >= a.switch_high && topo >= 2 * (nact + topm)) sw = true;
+        }
+        if (sw) {
+            if (active) { push_lane(c, mode, p); active = false; }
+            mode = other;
+            just_switched = true;
+            continue;
+        }
+        just_switched = false;
+        if (lane == 0) {
+            iters++;
+            if (mode) lanes_ch += nact; else lanes_ph += nact;
+        }
+        if (active) {
+            active = mode ? charged_step(c, p, n_hfict) : photon_step(c, p, n_fict);
+            if (active && ++p.steps > STEP_LIMIT) {
+                atomicOr(a.err, ERR_LIMIT);
+                stat_add(c, ST_DROPPED, 1);
+                stat_add(c, ST_E_DROPPED, fx(p.E));
+                active = false;
+            }
+            if (!c.ok) {
+                atomicOr(a.err, ERR_LIMIT);
+                c.ok = true;
+            }
+        }
+    }
+    // per-warp and per-lane statistics
+    atomicAdd(s_st + ST_FICT, (unsigned long long)n_fict);
+    atomicAdd(s_st + ST_HARD_FICT, (unsigned long long)n_hfict);
+    atomicAdd(s_st + ST_HISTORIES, hist);
+    atomicAdd(s_st + ST_E_IN, e_in);
+    atomicAdd(s_st + ST_E_MISS, e_miss);
+    atomicAdd(s_st + ST_MISSED, missed);
+    if (lane == 0) {
+        atomicAdd(s_st + ST_WARP_ITERS, iters);
+        atomicAdd(s_st + ST_LANES_PHOTON, lanes_ph);
+        atomicAdd(s_st + ST_LANES_CHARGED, lanes_ch);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < ST_COUNT; i += blockDim.x)
+        if (s_st[i]) atomicAdd(a.stats + i, s_st[i]);
+}
+
+}  // namespace
+
+size_t transport_smem_bytes(int /*threads*/) { return SMEM_TABLE_BYTES; }
+
+int transport_max_blocks_per_sm(int threads, size_t smem)
+{
+    cudaFuncSetAttribute(k_transport, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_transport, threads, smem) != cudaSuccess) return 0;
+    return n;
+}
+
+cudaError_t launch_transport(const TransportArgs& a, int blocks, int threads, size_t smem, cudaStream_t s)
+{
+    cudaError_t e = cudaFuncSetAttribute(k_transport, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_transport<<<blocks, threads, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace ocmc

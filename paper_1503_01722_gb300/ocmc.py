@@ -1,0 +1,267 @@
+"""Thin ctypes binding of the engine's C ABI (include/ocmc.h).
+
+Argument marshalling only: every step of the transport runs in the CUDA
+library libocmc.so. Importing this module loads the library and raises if it
+is missing; there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "libocmc.so")
+
+OK, ERR_ARG, ERR_CUDA, ERR_OOM, ERR_OVERFLOW, ERR_TIMEOUT, ERR_STATE = range(7)
+FLAG_NO_HARD, FLAG_NO_MS, FLAG_KILL_FIRST_REAL, FLAG_KERMA = 1, 2, 4, 8
+TALLY_SCALE = 2.0 ** 28
+
+
+class OcmcError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"ocmc status {status}: {msg}")
+        self.status = status
+
+
+class Params(C.Structure):
+    _fields_ = [("e_abs_e", C.c_float), ("e_abs_g", C.c_float), ("w_cc", C.c_float), ("w_cb", C.c_float),
+                ("d_maxs", C.c_float), ("f_maxe", C.c_float), ("s_min", C.c_float),
+                ("n_batches", C.c_int32), ("flags", C.c_int32),
+                ("block_threads", C.c_int32), ("blocks_per_sm", C.c_int32), ("stack_capacity", C.c_int32),
+                ("switch_high", C.c_int32), ("switch_low", C.c_int32)]
+
+
+class Stats(C.Structure):
+    _fields_ = [(n, C.c_uint64) for n in (
+        "histories", "photon_flights", "fictitious", "compton", "photo", "pair", "electron_steps", "moller",
+        "brems", "hard_fictitious", "annihilations", "escaped", "missed", "geo_crossings",
+        "majorant_violations", "dropped", "transmitted", "warp_iterations", "lane_steps")] + \
+        [(n, C.c_double) for n in ("e_in", "e_dep", "e_esc", "e_miss", "pair_mass", "annih_mass", "e_killed",
+                                   "e_trans", "e_dropped", "last_run_ms")]
+
+
+def _load():
+    if not os.path.exists(_LIB_PATH):
+        raise ImportError(f"{_LIB_PATH} not found: build it with paper_1503_01722_gb300.build.build()")
+    L = C.CDLL(_LIB_PATH)
+    P = C.c_void_p
+    sig = {
+        "ocmc_default_params": (None, [C.POINTER(Params)]),
+        "ocmc_init": (C.c_int, [C.POINTER(P), C.c_int, C.POINTER(Params)]),
+        "ocmc_set_params": (C.c_int, [P, C.POINTER(Params)]),
+        "ocmc_create_phantom": (C.c_int, [P, C.c_int, C.c_int, C.c_int, P, P, C.c_float, C.c_float, C.c_float]),
+        "ocmc_set_source": (C.c_int, [P, C.c_int, C.c_int, P, P, C.c_float, C.c_float, C.c_float,
+                                      C.POINTER(C.c_float), C.POINTER(C.c_float)]),
+        "ocmc_run": (C.c_int, [P, C.c_uint64, C.c_uint64, P]),
+        "ocmc_run_range": (C.c_int, [P, C.c_uint64, C.c_uint64, C.c_uint64, C.c_uint64, P]),
+        "ocmc_get_dose": (C.c_int, [P, P, P, C.c_int]),
+        "ocmc_get_raw_tally": (C.c_int, [P, P, C.c_int]),
+        "ocmc_add_raw_tally": (C.c_int, [P, P, C.c_int, C.c_uint64, C.c_uint64]),
+        "ocmc_reset_tally": (C.c_int, [P]),
+        "ocmc_get_stats": (C.c_int, [P, C.POINTER(Stats)]),
+        "ocmc_get_shape": (C.c_int, [P, C.POINTER(C.c_int64), C.POINTER(C.c_int32)]),
+        "ocmc_last_error": (C.c_char_p, [P]),
+        "ocmc_destroy": (None, [P]),
+        "ocmc_test_philox": (C.c_int, [C.c_int, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32,
+                                       C.c_uint32, C.c_uint32, P]),
+        "ocmc_test_source": (C.c_int, [P, C.c_uint64, C.c_uint64, C.c_uint64, C.c_uint64, P]),
+        "ocmc_test_sample": (C.c_int, [P, C.c_int, C.c_int, C.c_float, C.c_float, C.c_uint64, C.c_uint64, P]),
+        "ocmc_test_tables": (C.c_int, [P, C.c_int, P, C.c_int, P]),
+        "ocmc_test_csda": (C.c_int, [P, C.c_int, P, P, C.c_int, P]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    return L
+
+
+lib = _load()
+
+
+def default_params(**kw) -> Params:
+    p = Params()
+    lib.ocmc_default_params(C.byref(p))
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise AttributeError(k)
+        setattr(p, k, v)
+    if "e_abs_e" in kw and "w_cc" not in kw:
+        p.w_cc = p.e_abs_e
+    if "e_abs_g" in kw and "w_cb" not in kw:
+        p.w_cb = p.e_abs_g
+    return p
+
+
+def _ptr(a):
+    """Host numpy array or CUDA tensor -> (void*, on_device)."""
+    if isinstance(a, np.ndarray):
+        if not a.flags.c_contiguous:
+            raise ValueError("array must be C-contiguous")
+        return C.c_void_p(a.ctypes.data), 0
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return C.c_void_p(a.data_ptr()), 1 if a.is_cuda else 0
+    raise TypeError(type(a))
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return C.c_void_p(stream.cuda_stream)
+    return C.c_void_p(int(stream))
+
+
+class Engine:
+    """One engine context on one GPU (ocmc_ctx)."""
+
+    def __init__(self, device: int = 0, params: Params | None = None, **kw):
+        self._c = C.c_void_p()
+        p = params if params is not None else default_params(**kw)
+        self._check(lib.ocmc_init(C.byref(self._c), device, C.byref(p)), init=True)
+        self.params = p
+        self.device = device
+        self.shape = None
+
+    def _check(self, status, init=False):
+        if status != OK:
+            msg = lib.ocmc_last_error(None if init else self._c).decode()
+            raise OcmcError(status, msg)
+
+    def close(self):
+        if getattr(self, "_c", None) and self._c.value:
+            lib.ocmc_destroy(self._c)
+            self._c = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def set_params(self, params: Params | None = None, **kw):
+        if params is None:
+            params = Params.from_buffer_copy(self.params)
+            for k, v in kw.items():
+                setattr(params, k, v)
+        self._check(lib.ocmc_set_params(self._c, C.byref(params)))
+        self.params = params
+
+    def create_phantom(self, phantom=None, *, density=None, material=None, voxel=None):
+        """phantom: object with .density (nz,ny,nx) float32, .material uint8, .voxel (dx,dy,dz)."""
+        if phantom is not None:
+            density, material, voxel = phantom.density, phantom.material, phantom.voxel
+        d = np.ascontiguousarray(density, np.float32)
+        m = np.ascontiguousarray(material, np.uint8)
+        nz, ny, nx = d.shape
+        self._check(lib.ocmc_create_phantom(self._c, nx, ny, nz, C.c_void_p(d.ctypes.data),
+                                            C.c_void_p(m.ctypes.data), *map(float, voxel)))
+        self.shape = (nz, ny, nx)
+
+    def set_source(self, beam=None, *, particle=None, edges=None, weights=None, field=None, ssd=None,
+                   iso=None, direction=None):
+        if beam is not None:
+            particle, edges, weights = beam.particle, beam.edges, beam.weights
+            field, ssd, iso, direction = beam.field, beam.ssd, beam.iso, beam.direction
+        e = np.ascontiguousarray(edges, np.float32)
+        w = np.ascontiguousarray(weights, np.float32)
+        iso_c = (C.c_float * 3)(*iso)
+        dir_c = (C.c_float * 3)(*direction)
+        self._check(lib.ocmc_set_source(self._c, int(particle), len(w), C.c_void_p(e.ctypes.data),
+                                        C.c_void_p(w.ctypes.data), float(field[0]), float(field[1]),
+                                        float(ssd), iso_c, dir_c))
+
+    def run(self, n_histories: int, seed: int = 1, stream=None):
+        self._check(lib.ocmc_run(self._c, int(n_histories), int(seed), _stream_ptr(stream)))
+
+    def run_range(self, first: int, count: int, n_total: int, seed: int = 1, stream=None):
+        self._check(lib.ocmc_run_range(self._c, int(first), int(count), int(n_total), int(seed),
+                                       _stream_ptr(stream)))
+
+    def dose(self, out=None, sigma=True):
+        """Dose (MeV/g per source particle) and batch sigma as (nz,ny,nx) arrays.
+        `out` may be a (dose, sigma) pair of CUDA tensors to write on the device."""
+        if out is not None:
+            d, s = out
+            pd, dev = _ptr(d)
+            ps = _ptr(s)[0] if s is not None else None
+            self._check(lib.ocmc_get_dose(self._c, pd, ps, dev))
+            return d, s
+        d = np.empty(self.shape, np.float32)
+        s = np.empty(self.shape, np.float32) if sigma else None
+        self._check(lib.ocmc_get_dose(self._c, C.c_void_p(d.ctypes.data),
+                                      C.c_void_p(s.ctypes.data) if sigma else None, 0))
+        return d, s
+
+    def raw_tally(self, out=None):
+        nvox, B = C.c_int64(), C.c_int32()
+        self._check(lib.ocmc_get_shape(self._c, C.byref(nvox), C.byref(B)))
+        if out is not None:
+            p, dev = _ptr(out)
+            self._check(lib.ocmc_get_raw_tally(self._c, p, dev))
+            return out
+        t = np.empty((B.value,) + self.shape, np.int64)
+        self._check(lib.ocmc_get_raw_tally(self._c, C.c_void_p(t.ctypes.data), 0))
+        return t
+
+    def add_raw_tally(self, tally, first: int, count: int):
+        p, dev = _ptr(tally if not isinstance(tally, np.ndarray) else np.ascontiguousarray(tally, np.int64))
+        self._check(lib.ocmc_add_raw_tally(self._c, p, dev, int(first), int(count)))
+
+    def reset(self):
+        self._check(lib.ocmc_reset_tally(self._c))
+
+    def stats(self) -> dict:
+        s = Stats()
+        self._check(lib.ocmc_get_stats(self._c, C.byref(s)))
+        return {k: getattr(s, k) for k, _ in Stats._fields_}
+
+    # ---- building blocks for the tests ----
+    def test_source(self, n_total, first=0, count=None, seed=1):
+        count = n_total - first if count is None else count
+        out = np.empty((count, 8), np.float32)
+        self._check(lib.ocmc_test_source(self._c, n_total, first, count, seed, C.c_void_p(out.ctypes.data)))
+        return out
+
+    def test_sample(self, kind, E, n, seed=1, material=0, aux=0.0):
+        out = np.empty(n, np.float32)
+        self._check(lib.ocmc_test_sample(self._c, kind, material, float(E), float(aux), n, seed,
+                                         C.c_void_p(out.ctypes.data)))
+        return out
+
+    def test_tables(self, material, E):
+        E = np.ascontiguousarray(E, np.float32)
+        out = np.empty((len(E), 8), np.float32)
+        self._check(lib.ocmc_test_tables(self._c, material, C.c_void_p(E.ctypes.data), len(E),
+                                         C.c_void_p(out.ctypes.data)))
+        return out
+
+    def test_csda(self, material, T, X):
+        T = np.ascontiguousarray(T, np.float32)
+        X = np.ascontiguousarray(X, np.float32)
+        out = np.empty(len(T), np.float32)
+        self._check(lib.ocmc_test_csda(self._c, material, C.c_void_p(T.ctypes.data), C.c_void_p(X.ctypes.data),
+                                       len(T), C.c_void_p(out.ctypes.data)))
+        return out
+
+
+def test_philox(key, c1, c2, c3, first_block, n_blocks, device=0):
+    out = np.empty((n_blocks, 4), np.uint32)
+    st = lib.ocmc_test_philox(device, key[0], key[1], c1, c2, c3, first_block, n_blocks,
+                              C.c_void_p(out.ctypes.data))
+    if st != OK:
+        raise OcmcError(st, lib.ocmc_last_error(None).decode())
+    return out
+
+
+SAMPLE_COMPTON, SAMPLE_MOLLER, SAMPLE_BREMS, SAMPLE_MS = 0, 1, 2, 3

@@ -1,0 +1,229 @@
+"""Dose parity of the CUDA engine with the CPU oracle at equal history counts.
+
+Criterion (statistical, the method being Monte Carlo sampling): inside the
+10% isodose of the oracle's dose (the paper's evaluation region, Sec. 3.1),
+|D_gpu - D_oracle| <= 3 sigma_combined in at least 99% of the voxels, and the
+mean signed difference below 0.5% of D_max. sigma comes from B batch means on
+each side. Also: energy conservation, bit-reproducibility for any launch
+configuration, sharded runs, error statuses.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import ocmc_inputs as I
+import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ocmc():
+    from paper_1503_01722_gb300 import build
+    build.build()
+    from paper_1503_01722_gb300 import ocmc as m
+    return m
+
+
+def agreement(D, S, Dr, Sr):
+    mask = Dr >= 0.1 * Dr.max()
+    comb = np.sqrt(S ** 2 + Sr ** 2)[mask]
+    diff = (D - Dr)[mask]
+    z = np.abs(diff) / np.where(comb > 0, comb, np.inf)
+    return {
+        "n": int(mask.sum()),
+        "within3": float(np.mean(z <= 3.0)),
+        "mean_signed": float(diff.mean() / Dr.max()),
+        "mean_abs": float(np.abs(diff).mean() / Dr.max()),
+        "sigma_rel": float(np.mean(Sr[mask] / Dr[mask])),
+    }
+
+
+def run_both(ocmc, ph, beam, n, seed=1, B=50, **kw):
+    with ocmc.Engine(0, n_batches=B, **kw) as e:
+        e.create_phantom(ph)
+        e.set_source(beam)
+        e.run(n, seed=seed)
+        D, S = e.dose()
+        st = e.stats()
+        tally = e.raw_tally()
+    r = O.run(ph, beam, n, seed=seed, p=O.params(n_batches=B))
+    Dr, Sr = r.dose()
+    return D, S, Dr, Sr, st, tally, r
+
+
+def check_conservation(st):
+    bal = st["e_in"] + st["annih_mass"] - st["e_dep"] - st["e_esc"] - st["pair_mass"] - st["e_killed"]
+    assert abs(bal) <= 2e-5 * st["e_in"], (bal, st)
+    assert st["dropped"] == 0 and st["majorant_violations"] == 0, st
+
+
+CASES = {
+    # 15 MeV e-, 10x10 parallel field, water 61x61x60 at 0.5 cm, 5e4 histories
+    "electron_water_61": (lambda: I.electron_water_61(), 50_000),
+    # 6 MV photons at SSD 100, 10x10, slab phantom coarsened to 40^3 at 0.75 cm
+    "photon_slab_40": (lambda: (lambda ph: (ph, I.beam_on(ph, 0, I.spectrum_6mv(), (10, 10), 100.0)))(
+        I.scaled(I.slab(), 3)), 200_000),
+    # 15 MeV e- on the half-slab phantom coarsened to 40^3
+    "electron_half_slab_40": (lambda: (lambda ph: (ph, I.beam_on(ph, 1, I.mono(15.0), (10, 10), 100.0)))(
+        I.scaled(I.half_slab(), 3)), 20_000),
+    # 20 MeV photons on a random heterogeneous phantom with a ragged 24x20x28 grid (pairs, annihilations)
+    "photon_random_20MeV": (lambda: (lambda ph: (ph, I.beam_on(ph, 0, I.mono(20.0), (6, 5), 80.0)))(
+        I.random_phantom()), 60_000),
+}
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_dose_parity(ocmc, case):
+    make, n = CASES[case]
+    ph, beam = make()
+    D, S, Dr, Sr, st, tally, r = run_both(ocmc, ph, beam, n)
+    a = agreement(D, S, Dr, Sr)
+    print(case, a)
+    check_conservation(st)
+    assert st["histories"] == n
+    assert a["within3"] >= 0.99, a
+    assert abs(a["mean_signed"]) < 0.005, a
+    # the deposited energy of the whole phantom agrees within its statistical error
+    e_gpu, e_orc = st["e_dep"] / n, r.ledger["e_dep"] / n
+    sd = math.sqrt(((tally.sum(axis=(1, 2, 3)) / 2 ** 28 / (n / 50) - e_gpu) ** 2).sum() / (50 * 49)) * 1.5
+    assert abs(e_gpu - e_orc) < 4 * sd + 1e-3 * e_orc, (e_gpu, e_orc, sd)
+
+
+def test_bit_reproducible_across_runs_and_launch_shapes(ocmc):
+    ph = I.scaled(I.half_slab(), 4)
+    beam = I.beam_on(ph, 0, I.spectrum_6mv(), (10, 10), 100.0)
+    tallies = []
+    for kw in ({}, {}, {"block_threads": 128}, {"block_threads": 64, "blocks_per_sm": 2, "stack_capacity": 256},
+               {"switch_high": 1 << 20, "switch_low": 0}, {"switch_high": 33, "switch_low": 31}):
+        with ocmc.Engine(0, **kw) as e:
+            e.create_phantom(ph)
+            e.set_source(beam)
+            e.run(30_000, seed=9)
+            tallies.append(e.raw_tally())
+    for t in tallies[1:]:
+        assert np.array_equal(t, tallies[0])
+    assert tallies[0].sum() > 0
+
+
+def test_ranges_add_up_to_one_run(ocmc):
+    ph, beam = I.electron_water_61()
+    n = 4000
+    with ocmc.Engine(0) as e:
+        e.create_phantom(ph)
+        e.set_source(beam)
+        e.run(n, seed=3)
+        full = e.raw_tally()
+        D1, _ = e.dose()
+        e.reset()
+        for a, b in ((0, 1234), (1234, 3000), (3000, 4000)):
+            e.run_range(a, b - a, n, seed=3)
+        parts = e.raw_tally()
+        D2, _ = e.dose()
+        # resume from a saved tally: add the saved partial run, then the rest
+        e.reset()
+        e.run_range(0, 2500, n, seed=3)
+        saved = e.raw_tally()
+        e.reset()
+        e.add_raw_tally(saved, 0, 2500)
+        e.run_range(2500, 1500, n, seed=3)
+        resumed = e.raw_tally()
+    assert np.array_equal(full, parts) and np.array_equal(full, resumed)
+    assert np.array_equal(D1, D2)
+
+
+def test_narrow_beam_transmission(ocmc):
+    E = 1.25
+    ph = I.slab((9, 9, 48), (1.0, 1.0, 0.25), layers=((3.0, 5.0, I.BONE), (5.0, 9.0, I.LUNG)))
+    beam = I.pencil(ph, 0, E)
+    n = 400_000
+    with ocmc.Engine(0, flags=ocmc.FLAG_KILL_FIRST_REAL) as e:
+        e.create_phantom(ph)
+        e.set_source(beam)
+        e.run(n, seed=5)
+        st = e.stats()
+    tau = sum(I.RHO[m] * O.mu(m, E) * (z1 - z0) for z0, z1, m in
+              ((0, 3.0, 0), (3.0, 5.0, 1), (5.0, 9.0, 2), (9.0, 12.0, 0)))
+    p = math.exp(-tau)
+    got = st["transmitted"] / n
+    assert abs(got - p) < 4 * math.sqrt(p * (1 - p) / n), (got, p)
+    assert st["fictitious"] > 0.3 * st["photon_flights"]
+
+
+def test_csda_range_no_hard_no_ms(ocmc):
+    """Without hard events and deflections an electron pencil deposits up to its CSDA range."""
+    from scipy import integrate
+    E0 = 10.0
+    dz = 0.05
+    ph = I.homogeneous((5, 5, 200), (4.0, 4.0, dz))
+    beam = I.pencil(ph, 1, E0)
+    with ocmc.Engine(0, flags=ocmc.FLAG_NO_HARD | ocmc.FLAG_NO_MS) as e:
+        e.create_phantom(ph)
+        e.set_source(beam)
+        e.run(64, seed=2)
+        D, _ = e.dose()
+    L = lambda t: O.L_col(0, t, 0.2) + O.L_rad(0, t, 0.01)
+    R = integrate.quad(lambda t: 1 / L(t), 0.2, E0, epsrel=1e-10)[0]
+    depth = D.sum(axis=(1, 2))
+    last = np.nonzero(depth)[0].max()
+    assert abs((last + 0.5) * dz - R) <= 0.01 * R + dz, ((last + 0.5) * dz, R)
+
+
+def test_vacuum_phantom(ocmc):
+    ph = I.homogeneous((10, 10, 10), (1.0, 1.0, 1.0), density=0.0)
+    for particle, E in ((0, 2.0), (1, 10.0)):
+        with ocmc.Engine(0) as e:
+            e.create_phantom(ph)
+            e.set_source(I.beam_on(ph, particle, I.mono(E), (4, 4), 100.0))
+            e.run(1000, seed=1)
+            st = e.stats()
+            assert e.raw_tally().sum() == 0
+        assert abs(st["e_esc"] - st["e_in"]) < 1e-5 * st["e_in"]
+
+
+def test_error_statuses(ocmc):
+    with ocmc.Engine(0) as e:
+        with pytest.raises(ocmc.OcmcError) as x:
+            e.run(10, seed=1)
+        assert x.value.status == ocmc.ERR_STATE
+        ph = I.homogeneous((4, 4, 4), (1.0, 1.0, 1.0))
+        bad = I.Phantom(ph.density.copy(), ph.material.copy(), ph.voxel)
+        bad.material[0, 0, 0] = 7
+        with pytest.raises(ocmc.OcmcError) as x:
+            e.create_phantom(bad)
+        assert x.value.status == ocmc.ERR_ARG
+        bad = I.Phantom(ph.density.copy(), ph.material.copy(), ph.voxel)
+        bad.density[1, 1, 1] = np.nan
+        with pytest.raises(ocmc.OcmcError) as x:
+            e.create_phantom(bad)
+        assert x.value.status == ocmc.ERR_ARG
+        e.create_phantom(ph)
+        with pytest.raises(ocmc.OcmcError) as x:
+            e.set_source(particle=0, edges=[1.0, 2.0], weights=[0.0], field=(1, 1), ssd=100, iso=(2, 2, 0),
+                         direction=(0, 0, 1))
+        assert x.value.status == ocmc.ERR_ARG
+        with pytest.raises(ocmc.OcmcError):
+            e.dose()
+
+
+def test_stack_overflow_is_reported_not_faulted(ocmc):
+    """A tiny stack with type switching disabled overflows under a photon beam: the
+    kernel drops the excess, flags OCMC_ERR_OVERFLOW and the context stays usable."""
+    ph = I.homogeneous((20, 20, 20), (1.0, 1.0, 1.0))
+    beam = I.beam_on(ph, 0, I.mono(6.0), (10, 10), 100.0)
+    with ocmc.Engine(0, stack_capacity=64, switch_high=1 << 20, switch_low=0) as e:
+        e.create_phantom(ph)
+        e.set_source(beam)
+        e.run(200_000, seed=1)
+        with pytest.raises(ocmc.OcmcError) as x:
+            e.dose()
+        assert x.value.status == ocmc.ERR_OVERFLOW
+        st = e.stats()
+        assert st["dropped"] > 0
+        bal = st["e_in"] + st["annih_mass"] - st["e_dep"] - st["e_esc"] - st["pair_mass"] - st["e_dropped"]
+        assert abs(bal) < 2e-5 * st["e_in"]
+        e.reset()
+        e.set_params(stack_capacity=0, switch_high=0, switch_low=0)
+        e.run(2000, seed=2)
+        e.dose()
