@@ -1,0 +1,320 @@
+"""Throughput benchmark of the GB300 Monte Carlo dose engine.
+
+One step = one pass of the whole transport path over one batch of histories:
+tally reset, the persistent transport launch (source sampling, photon Woodcock
+flights and interactions, electron condensed-history steps, fixed-point
+tally), and the dose/sigma finalisation on the device. Default workload: 6 MV
+photon beam, 10x10 cm^2 at SSD 100 cm, on the water/bone/lung slab phantom of
+120^3 voxels at 0.25 cm, 10^8 histories per step (synthetic inputs).
+
+Prints one JSON line (rank 0). `--impl reference` times the CPU oracle on the
+host cores instead (the reference arm of this build).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import ocmc_inputs as I  # noqa: E402
+
+# Thread-instructions per lane-step of the transport kernel (ncu
+# smsp__thread_inst_executed.sum divided by the kernel's own lane-step counter)
+# and DRAM bytes per history, from the ncu capture summarised in
+# profiles/transport_photon_slab_120.md. None until that profile exists.
+INST_PER_LANE_STEP = None
+DRAM_BYTES_PER_HISTORY = None
+
+WORKLOADS = {
+    "photon_slab_120": (I.photon_slab_120, 100_000_000,
+                        "6 MV photon beam (24-bin closed-form spectrum), 10x10 cm2 at SSD 100 cm, slab phantom "
+                        "120^3 at 0.25 cm (water 0-3, bone 1.85 3-5, lung 0.26 5-12, water), cutoffs e 200 keV / "
+                        "gamma 10 keV"),
+    "electron_water_61": (I.electron_water_61, 50_000,
+                          "15 MeV electron beam, 10x10 cm2 parallel, water 61x61x60 at 0.5 cm"),
+    "photon_half_slab_120": (I.photon_half_slab_120, 100_000_000,
+                             "6 MV photon beam, 10x10 at SSD 100, half-slab phantom 120^3 at 0.25 cm"),
+    "electron_half_slab_120": (I.electron_half_slab_120, 10_000_000,
+                               "15 MeV electron beam, 10x10 at SSD 100, half-slab phantom 120^3 at 0.25 cm"),
+}
+
+
+def sm_peak_thread_inst(sm_mhz: float, sms: int = 152) -> float:
+    """Issue-limited peak: 4 SM sub-partitions x 32 lanes per clock per SM."""
+    return sms * 4 * 32 * sm_mhz * 1e6
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in getattr(self, "lines", []):
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, f[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+def cpu_baseline(ph, beam, target_s=15.0):
+    """The oracle, as it stands, on all host cores for a bounded sample."""
+    import oracle as O
+    threads = os.cpu_count() or 1
+    pilot = max(200, 20 * threads)
+    t = time.perf_counter()
+    O.run(ph, beam, pilot, seed=1, threads=threads)
+    rate = pilot / (time.perf_counter() - t)
+    n = int(min(max(rate * target_s, 2 * pilot), 5_000_000))
+    t = time.perf_counter()
+    O.run(ph, beam, n, seed=1, threads=threads, n_total=n)
+    dt = time.perf_counter() - t
+    return {"value": n / dt, "unit": "histories/s", "cores": threads, "kind": "oracle",
+            "sample": f"{n} histories of the same workload (histories 0..{n - 1}), {dt:.1f} s"}
+
+
+def run_reference(args, ph, beam, desc):
+    import oracle as O
+    threads = os.cpu_count() or 1
+    pilot = max(200, 20 * threads)
+    t = time.perf_counter()
+    O.run(ph, beam, pilot, seed=1, threads=threads)
+    rate = pilot / (time.perf_counter() - t)
+    budget = 150.0 / max(1, args.steps + args.warmup)
+    n = int(min(max(rate * budget, pilot), 5_000_000))
+    for _ in range(args.warmup):
+        O.run(ph, beam, n, seed=1, threads=threads)
+    times = []
+    for k in range(args.steps):
+        t = time.perf_counter()
+        O.run(ph, beam, n, seed=1 + k, threads=threads)
+        times.append(time.perf_counter() - t)
+    value = n * args.steps / sum(times)
+    line = {
+        "impl": "reference", "metric": "histories/s", "value": value, "unit": "histories/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": desc, "histories_per_step": n, "l2": "n/a (CPU)"},
+        "cpu_baseline": {"value": value, "unit": "histories/s", "cores": threads, "kind": "oracle",
+                         "sample": f"{n} histories per step of the same workload"},
+        "e2e": {"value": value, "unit": "histories/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="photon_slab_120", choices=list(WORKLOADS))
+    ap.add_argument("--histories", type=int, default=0, help="histories per step and GPU (default: workload's)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+
+    make, n_default, desc = WORKLOADS[args.workload]
+    ph, beam = make()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        if rank == 0:
+            run_reference(args, ph, beam, desc)
+        return
+
+    import torch
+    from paper_1503_01722_gb300 import ocmc
+    from paper_1503_01722_gb300 import sharding
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    n = args.histories or n_default
+    eng = ocmc.Engine(local)
+    eng.create_phantom(ph)
+    eng.set_source(beam)
+    shape = ph.density.shape
+    dose = torch.empty(shape, dtype=torch.float32, device="cuda")
+    sig = torch.empty(shape, dtype=torch.float32, device="cuda")
+    B = eng.params.n_batches
+    tally = torch.empty((B,) + shape, dtype=torch.int64, device="cuda") if world > 1 else None
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def step(k):
+        eng.reset()
+        first, count, total = sharding.shard(rank, world, n)
+        eng.run_range(first, count, total, seed=1)
+        if world > 1:
+            sharding.allreduce_tally(eng, tally, dist)
+            eng.reset()
+            eng.add_raw_tally(tally, 0, total)
+        eng.dose(out=(dose, sig))
+
+    for k in range(args.warmup):
+        step(k)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ms, kern_ms, lane_steps = [], [], []
+    with ClockSampler(local) as clk:
+        wall0 = time.perf_counter()
+        for k in range(args.steps):
+            flush.fill_(float(k))                     # evict L2 between steps (outside the step events)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            step(k)
+            e1.record()
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            st = eng.stats()
+            kern_ms.append(st["last_run_ms"])
+            lane_steps.append(st["lane_steps"])
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - wall0
+    if dist:
+        dist.barrier()
+    total_ms = sum(ms)
+    if dist:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = n * world * args.steps / (total_ms / 1e3)
+
+    # end to end through the C ABI with host buffers: phantom upload from pinned memory,
+    # tables, transport, and the dose + sigma read back to pinned memory, every step
+    e2e = None
+    if not args.no_e2e:
+        dens_h = torch.from_numpy(np.ascontiguousarray(ph.density)).pin_memory()
+        mat_h = torch.from_numpy(np.ascontiguousarray(ph.material)).pin_memory()
+        dose_h = torch.empty(shape, dtype=torch.float32).pin_memory()
+        sig_h = torch.empty(shape, dtype=torch.float32).pin_memory()
+        e2e_eng = ocmc.Engine(local)
+        e2e_ms = []
+        for k in range(args.warmup + args.steps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            e2e_eng.create_phantom(density=dens_h.numpy(), material=mat_h.numpy(), voxel=ph.voxel)
+            e2e_eng.set_source(beam)
+            first, count, total = sharding.shard(rank, world, n)
+            e2e_eng.run_range(first, count, total, seed=1)
+            e2e_eng.dose(out=(dose_h, sig_h))
+            dt = time.perf_counter() - t0
+            if k >= args.warmup:
+                e2e_ms.append(dt * 1e3)
+        e2e_eng.close()
+        e2e_total = sum(e2e_ms)
+        if dist:
+            t = torch.tensor([e2e_total], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_total = float(t.item())
+        nvox = ph.density.size
+        e2e = {"value": n * world * args.steps / (e2e_total / 1e3), "unit": "histories/s",
+               "h2d_bytes_per_step": int(nvox * 4 + nvox * 1 + (len(beam.edges) + len(beam.weights)) * 4),
+               "d2h_bytes_per_step": int(nvox * 8)}
+
+    clocks = clk.summary()
+    peaks = measured_peaks()
+    kern = statistics.mean(kern_ms)
+    ls = statistics.mean(lane_steps)
+    sm_mhz = clocks["sm_mhz"] or peaks.get("sm_max_mhz", 2070.0)
+    peak = sm_peak_thread_inst(sm_mhz) / 1e12
+    achieved = None if INST_PER_LANE_STEP is None else ls * INST_PER_LANE_STEP / (kern / 1e3) / 1e12
+    roofline = {
+        "bound": "alu", "kernel": "k_transport",
+        "achieved": achieved, "peak": peak, "unit": "Tinst/s",
+        "frac": None if achieved is None else achieved / peak,
+        "peak_basis": f"152 SMs x 128 lanes x median SM clock under load ({sm_mhz:.0f} MHz)",
+        "traffic": None if DRAM_BYTES_PER_HISTORY is None else DRAM_BYTES_PER_HISTORY * n,
+        "kernel_ms": kern, "lane_steps_per_launch": ls,
+        "hbm_gbs_achieved_if_traffic": None if DRAM_BYTES_PER_HISTORY is None else
+        DRAM_BYTES_PER_HISTORY * n / (kern / 1e3) / 1e9,
+        "hbm_peak_gbs_measured": peaks.get("hbm_gbs"),
+    }
+    line = {
+        "metric": "histories/s", "value": value, "unit": "histories/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": desc, "histories_per_step": n * world, "histories_per_gpu": n,
+                   "l2": "flushed between steps (256 MB write)", "seed": 1, "n_batches": B,
+                   "parallelism": f"histories sharded over {world} GPU(s), int64 tally all-reduce" if world > 1
+                   else "1 GPU"},
+        "e2e": e2e,
+        "gpu_launches": 2 * args.steps,
+        "roofline": roofline,
+        "clocks": clocks,
+        "wall_s": wall,
+        "kernel_stats_last_step": {k: v for k, v in eng.stats().items() if isinstance(v, (int, float))},
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(ph, beam)
+    if rank == 0:
+        print(json.dumps(line))
+    eng.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

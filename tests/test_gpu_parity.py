@@ -212,7 +212,8 @@ def test_stack_overflow_is_reported_not_faulted(ocmc):
     kernel drops the excess, flags OCMC_ERR_OVERFLOW and the context stays usable."""
     ph = I.homogeneous((20, 20, 20), (1.0, 1.0, 1.0))
     beam = I.beam_on(ph, 0, I.mono(6.0), (10, 10), 100.0)
-    with ocmc.Engine(0, stack_capacity=64, switch_high=1 << 20, switch_low=0) as e:
+    # one warp per SM: ~1300 histories per warp fill a 64-entry electron stack
+    with ocmc.Engine(0, stack_capacity=64, switch_high=1 << 20, block_threads=32, blocks_per_sm=1) as e:
         e.create_phantom(ph)
         e.set_source(beam)
         e.run(200_000, seed=1)
@@ -224,6 +225,6 @@ def test_stack_overflow_is_reported_not_faulted(ocmc):
         bal = st["e_in"] + st["annih_mass"] - st["e_dep"] - st["e_esc"] - st["pair_mass"] - st["e_dropped"]
         assert abs(bal) < 2e-5 * st["e_in"]
         e.reset()
-        e.set_params(stack_capacity=0, switch_high=0, switch_low=0)
+        e.set_params(stack_capacity=0, switch_high=0, block_threads=0, blocks_per_sm=0)
         e.run(2000, seed=2)
         e.dose()
