@@ -31,7 +31,7 @@ import ocmc_inputs as I  # noqa: E402
 # smsp__thread_inst_executed.sum divided by the kernel's own lane-step counter)
 # and DRAM bytes per history, from the ncu capture summarised in
 # profiles/transport_photon_slab_120.md. None until that profile exists.
-INST_PER_LANE_STEP = None
+INST_PER_LANE_STEP = 732.4
 DRAM_BYTES_PER_HISTORY = None
 
 WORKLOADS = {
@@ -118,9 +118,11 @@ def cpu_baseline(ph, beam, target_s=15.0):
     import oracle as O
     threads = os.cpu_count() or 1
     pilot = max(200, 20 * threads)
-    t = time.perf_counter()
-    O.run(ph, beam, pilot, seed=1, threads=threads)
-    rate = pilot / (time.perf_counter() - t)
+    for _ in range(2):                                  # second pilot sized to ~2 s
+        t = time.perf_counter()
+        O.run(ph, beam, pilot, seed=1, threads=threads)
+        rate = pilot / (time.perf_counter() - t)
+        pilot = int(min(max(rate * 2.0, pilot), 1_000_000))
     n = int(min(max(rate * target_s, 2 * pilot), 5_000_000))
     t = time.perf_counter()
     O.run(ph, beam, n, seed=1, threads=threads, n_total=n)
