@@ -30,7 +30,7 @@ import ocmc_inputs as I  # noqa: E402
 # Thread-instructions per lane-step of the transport kernel (ncu
 # smsp__thread_inst_executed.sum divided by the kernel's own lane-step counter)
 # and DRAM bytes per history, from the ncu capture summarised in
-# profiles/transport_photon_slab_120.md. None until that profile exists.
+# profiles/k_transport_photon_slab_120.md (re-measured whenever the kernel changes).
 INST_PER_LANE_STEP = 732.4
 DRAM_BYTES_PER_HISTORY = None
 
