@@ -219,6 +219,42 @@ ocmc_status ocmc_test_tables(ocmc_ctx* ctx, int material, const float* E_host, i
 ocmc_status ocmc_test_csda(ocmc_ctx* ctx, int material, const float* T_host, const float* X_host,
                            int n, float* out_host);
 
+/* ---- allocation-free transport -----------------------------------------------
+ * The paper has no counterpart to this call. It is for callers that cannot
+ * allocate device memory: code running under another framework's allocator or
+ * memory pool (which must own every device allocation), treatment-planning hosts
+ * that forbid allocation after start-up, and plug-ins handed only device
+ * pointers. It transports histories [first, first+count) of a run of n_total,
+ * exactly as ocmc_run_range does on a context with the same phantom, source,
+ * parameters and seed (the same tally, bit for bit), and ADDS the deposited
+ * energy into tally_dev (int64, n_batches x nx*ny*nz, units 2^-28 MeV; zero it
+ * first for a fresh run). It calls no cudaMalloc, cudaFree or allocating routine.
+ *
+ * All scratch memory (physics tables, secondary-particle stacks, history counter,
+ * statistics, error flag) is one static device array of
+ * OCMC_NOALLOC_SCRATCH_BYTES that every GPU which loads the library holds until
+ * the process exits. Each call clears the counter, statistics and error flag and
+ * rebuilds the tables; the array otherwise keeps the last call's contents. Calls
+ * that overlap on the GPU (other streams, other host threads) share the array and
+ * race: serialise them. The first call on a device looks up the array's address
+ * with that device current and caches it: make it before any stream capture.
+ *
+ * density_dev, material_dev: device arrays as in ocmc_create_phantom (values are
+ * checked on the device; bad values give OCMC_ERR_ARG). Source arguments as in
+ * ocmc_set_source (host arrays). params: NULL for defaults; a launch shape
+ * (block_threads, blocks_per_sm, stack_capacity) whose stacks do not fit in the
+ * static array is rejected with OCMC_ERR_ARG. Runs on cuda_stream and
+ * synchronises it before returning. err_msg (host, may be NULL) receives a message
+ * of at most err_len bytes on failure. */
+#define OCMC_NOALLOC_SCRATCH_BYTES (64ull * 1024ull * 1024ull)
+ocmc_status ocmc_run_noalloc(int device, int nx, int ny, int nz, const float* density_dev,
+                             const uint8_t* material_dev, float dx, float dy, float dz, int particle,
+                             int n_bins, const float* bin_edges_host, const float* weights_host,
+                             float field_x, float field_y, float ssd, const float iso[3], const float dir[3],
+                             const ocmc_params* params, uint64_t first, uint64_t count, uint64_t n_total,
+                             uint64_t seed, int64_t* tally_dev, void* cuda_stream, char* err_msg,
+                             size_t err_len);
+
 #ifdef __cplusplus
 }
 #endif

@@ -70,6 +70,11 @@ def _load():
         "ocmc_test_sample": (C.c_int, [P, C.c_int, C.c_int, C.c_float, C.c_float, C.c_uint64, C.c_uint64, P]),
         "ocmc_test_tables": (C.c_int, [P, C.c_int, P, C.c_int, P]),
         "ocmc_test_csda": (C.c_int, [P, C.c_int, P, P, C.c_int, P]),
+        "ocmc_run_noalloc": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, P, P, C.c_float, C.c_float, C.c_float,
+                                       C.c_int, C.c_int, P, P, C.c_float, C.c_float, C.c_float,
+                                       C.POINTER(C.c_float), C.POINTER(C.c_float), C.POINTER(Params),
+                                       C.c_uint64, C.c_uint64, C.c_uint64, C.c_uint64, P, P, C.c_char_p,
+                                       C.c_size_t]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -265,3 +270,29 @@ def test_philox(key, c1, c2, c3, first_block, n_blocks, device=0):
 
 
 SAMPLE_COMPTON, SAMPLE_MOLLER, SAMPLE_BREMS, SAMPLE_MS = 0, 1, 2, 3
+
+
+def run_noalloc(density, material, voxel, beam, tally, first, count, n_total, seed=1, params=None, device=0,
+                stream=None):
+    """Allocation-free transport (ocmc_run_noalloc) for callers that cannot allocate
+    device memory: `density` (float32), `material` (uint8) and `tally` (int64,
+    n_batches x nz x ny x nx, added into) are CUDA tensors the caller owns; every
+    scratch buffer is the library's fixed static device array. Calls that overlap on
+    the GPU share that array and must be serialised by the caller."""
+    pd, dd = _ptr(density)
+    pm, dm = _ptr(material)
+    pt, dt = _ptr(tally)
+    if not (dd and dm and dt):
+        raise ValueError("density, material and tally must be CUDA tensors")
+    nz, ny, nx = density.shape
+    e = np.ascontiguousarray(beam.edges, np.float32)
+    w = np.ascontiguousarray(beam.weights, np.float32)
+    p = params if params is not None else default_params()
+    msg = C.create_string_buffer(256)
+    st = lib.ocmc_run_noalloc(device, nx, ny, nz, pd, pm, *map(float, voxel), int(beam.particle), len(w),
+                              C.c_void_p(e.ctypes.data), C.c_void_p(w.ctypes.data), float(beam.field[0]),
+                              float(beam.field[1]), float(beam.ssd), (C.c_float * 3)(*beam.iso),
+                              (C.c_float * 3)(*beam.direction), C.byref(p), int(first), int(count), int(n_total),
+                              int(seed), pt, _stream_ptr(stream), msg, 256)
+    if st != OK:
+        raise OcmcError(st, msg.value.decode())
