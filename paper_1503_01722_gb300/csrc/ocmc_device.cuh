@@ -29,11 +29,29 @@ struct Rng {
     uint4 buf;
 };
 
+// One out-of-line copy of the generator for draws beyond a step's first block:
+// call sites stay small, so the transport kernel's code fits the instruction cache.
+static __device__ __noinline__ uint4 philox_block(uint32_t b, uint32_t h0, uint32_t h1, uint32_t sub, uint32_t k0, uint32_t k1)
+{
+    return philox4x32_10(make_uint4(b, h0, h1, sub), k0, k1);
+}
+
+// Every transport step starts on a fresh block: n is rounded up to a multiple of 4
+// and that block is generated by all lanes of the warp together (no divergence for
+// the first four draws of a step). The rounding depends only on the particle's own
+// step sequence, so streams stay independent of scheduling.
+__device__ __forceinline__ void rng_step_start(Rng& r, uint32_t k0, uint32_t k1)
+{
+    r.n = (r.n + 3u) & ~3u;
+    r.blk = r.n >> 2;
+    r.buf = philox4x32_10(make_uint4(r.blk, r.h0, r.h1, r.sub), k0, k1);
+}
+
 __device__ __forceinline__ float rng_u(Rng& r, uint32_t k0, uint32_t k1)
 {
     uint32_t b = r.n >> 2;
     if (b != r.blk) {
-        r.buf = philox4x32_10(make_uint4(b, r.h0, r.h1, r.sub), k0, k1);
+        r.buf = philox_block(b, r.h0, r.h1, r.sub, k0, k1);
         r.blk = b;
     }
     uint32_t i = r.n & 3u;

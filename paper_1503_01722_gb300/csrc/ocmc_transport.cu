@@ -45,7 +45,12 @@ struct Ctx {
 
 __device__ __forceinline__ void stat_add(Ctx& c, int k, unsigned long long v) { atomicAdd(c.st + k, v); }
 
-__device__ __forceinline__ unsigned long long fx(float e) { return (unsigned long long)__float2ll_rn(e * TALLY_SCALE); }
+// fixed-point energy (round to nearest even); the 32-bit conversion is exact below 16 MeV
+__device__ __forceinline__ unsigned long long fx(float e)
+{
+    float q = e * TALLY_SCALE;
+    return q < 4294967040.f ? (unsigned long long)__float2uint_rn(q) : (unsigned long long)__float2ll_rn(q);
+}
 
 __device__ __forceinline__ void deposit(Ctx& c, int batch, int ix, int iy, int iz, float dE)
 {
@@ -150,6 +155,7 @@ __device__ __forceinline__ bool photon_step(Ctx& c, Lane& p, unsigned& n_fict)
     const TransportArgs& a = c.a;
     const SmemTables& T = c.T;
     const uint32_t k0 = a.key0, k1 = a.key1;
+    rng_step_start(p.r, k0, k1);
     EIdx ei = e_index(p.E);
     float lnmaj = lerp1(T.phmaj[ei.i], T.phmaj[ei.i + 1], ei.f);
     if (lnmaj < -1e29f) { escape(c, p); return false; }
@@ -250,6 +256,7 @@ __device__ __forceinline__ bool charged_step(Ctx& c, Lane& p, unsigned& n_hfict)
         if (!cross_face(c, p, face)) { escape(c, p); return false; }
         return true;
     }
+    rng_step_start(p.r, k0, k1);
     EIdx ei = e_index(p.E);
     const int mb = m * NE;
     float4 A = T.el[mb + ei.i], B = T.el[mb + ei.i + 1];
@@ -340,7 +347,7 @@ __device__ __forceinline__ bool charged_step(Ctx& c, Lane& p, unsigned& n_hfict)
     return true;
 }
 
-__global__ void __launch_bounds__(256) k_transport(const TransportArgs a)
+__global__ void __maxnreg__(80) k_transport(const TransportArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_top[MAX_WARPS][2];
