@@ -17,6 +17,10 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libocmc.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include"), "-I", CSRC]
+# FP32 transport code: approximate division/sqrt and flush-to-zero (deterministic for a given
+# binary; the physics tables are built in FP64 in ocmc_tables.cu, which keeps IEEE semantics)
+FAST = ["-ftz=true", "-prec-div=false", "-prec-sqrt=false"]
+FAST_FILES = {"ocmc_transport.cu", "ocmc_aux.cu", "ocmc_noalloc.cu"}
 
 
 def _nvcc():
@@ -35,7 +39,7 @@ def _stale(target, deps):
 
 def build(force: bool = False, verbose: bool = False) -> str:
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
-    headers = glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(CSRC, "*.cuh")) + \
+    headers = [os.path.abspath(__file__)] + glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(CSRC, "*.cuh")) + \
         glob.glob(os.path.join(ROOT, "include", "*.h"))
     os.makedirs(BUILD, exist_ok=True)
     nvcc = _nvcc()
@@ -43,7 +47,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
     def compile_one(src):
         obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
         if force or _stale(obj, [src] + headers):
-            cmd = [nvcc, *ARCH, *FLAGS, "-c", src, "-o", obj + ".tmp"]
+            extra = FAST if os.path.basename(src) in FAST_FILES else []
+            cmd = [nvcc, *ARCH, *FLAGS, *extra, "-c", src, "-o", obj + ".tmp"]
             r = subprocess.run(cmd, capture_output=True, text=True)
             if r.returncode != 0:
                 raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")

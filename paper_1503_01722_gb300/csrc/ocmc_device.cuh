@@ -112,17 +112,20 @@ __device__ __forceinline__ float range_to_lnE(const SmemTables& T, int m, float 
     return lerp1(r[j], r[j + 1], f);
 }
 
-// Energy after CSDA slowing over mass thickness X (g/cm^2) from energy E with
-// ln R(E) = lnR: E_end = E exp(g(ln(R - X)) - g(ln R)), g the inverse range
+// Energy after CSDA slowing over mass thickness X (g/cm^2) from energy E, with
+// R = R(E) and g0 = g(ln R): E_end = E exp(g(ln(R - X)) - g0), g the inverse range
 // table; exact at X = 0 and monotone in X.
-__device__ __forceinline__ float csda_end(const SmemTables& T, int m, float E, float lnR, float X)
+__device__ __forceinline__ float csda_end2(const SmemTables& T, int m, float E, float R, float g0, float X)
 {
-    float R = __expf(lnR);
     float R1 = R - X;
     if (!(R1 > 0.f)) return 0.f;
-    float g0 = range_to_lnE(T, m, lnR);
     float g1 = range_to_lnE(T, m, __logf(R1));
     return fminf(E, E * __expf(g1 - g0));
+}
+
+__device__ __forceinline__ float csda_end(const SmemTables& T, int m, float E, float lnR, float X)
+{
+    return csda_end2(T, m, E, __expf(lnR), range_to_lnE(T, m, lnR), X);
 }
 
 // ---- interaction samplers -------------------------------------------------------------------
@@ -244,18 +247,15 @@ __device__ __forceinline__ float dist_to_face(float x, float y, float z, float u
     float best = 3.0e38f;
     int f = 0;
     if (u != 0.f) {
-        float t = ((u > 0.f ? (float)(ix + 1) : (float)ix) * dx - x) / u;
-        t = fmaxf(t, 0.f);
+        float t = fmaxf(__fdividef((u > 0.f ? (float)(ix + 1) : (float)ix) * dx - x, u), 0.f);
         if (t < best) { best = t; f = u > 0.f ? 1 : 0; }
     }
     if (v != 0.f) {
-        float t = ((v > 0.f ? (float)(iy + 1) : (float)iy) * dy - y) / v;
-        t = fmaxf(t, 0.f);
+        float t = fmaxf(__fdividef((v > 0.f ? (float)(iy + 1) : (float)iy) * dy - y, v), 0.f);
         if (t < best) { best = t; f = v > 0.f ? 3 : 2; }
     }
     if (w != 0.f) {
-        float t = ((w > 0.f ? (float)(iz + 1) : (float)iz) * dz - z) / w;
-        t = fmaxf(t, 0.f);
+        float t = fmaxf(__fdividef((w > 0.f ? (float)(iz + 1) : (float)iz) * dz - z, w), 0.f);
         if (t < best) { best = t; f = w > 0.f ? 5 : 4; }
     }
     *face = f;

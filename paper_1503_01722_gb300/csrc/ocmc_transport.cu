@@ -274,7 +274,8 @@ __device__ __forceinline__ bool charged_step(Ctx& c, Lane& p, unsigned& n_hfict)
     float s1 = rng_u(p.r, k0, k1) * s;
     float hx = fmaf(s1, p.u, p.x), hy = fmaf(s1, p.v, p.y), hz = fmaf(s1, p.w, p.z);
     float E0 = p.E;
-    float Efull = csda_end(T, m, E0, lnR, rho * s);
+    const float R0 = __expf(lnR), g0 = range_to_lnE(T, m, lnR);
+    float Efull = csda_end2(T, m, E0, R0, g0, rho * s);
     if (!(a.pp.flags & 2)) {
         EIdx em = e_index(0.5f * (E0 + Efull));
         float l1 = lerp1(T.el[mb + em.i].y, T.el[mb + em.i + 1].y, em.f);
@@ -296,7 +297,7 @@ __device__ __forceinline__ bool charged_step(Ctx& c, Lane& p, unsigned& n_hfict)
         p.x = fmaf(tex, p.u, hx);
         p.y = fmaf(tex, p.v, hy);
         p.z = fmaf(tex, p.w, hz);
-        Eend = csda_end(T, m, E0, lnR, rho * (s1 + tex));
+        Eend = csda_end2(T, m, E0, R0, g0, rho * (s1 + tex));
         crossed = true;
     }
     deposit(c, p.batch, p.ix, p.iy, p.iz, E0 - Eend);
