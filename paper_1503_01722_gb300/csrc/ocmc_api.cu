@@ -408,7 +408,7 @@ ocmc_status ocmc_run_range(ocmc_ctx* c, uint64_t first, uint64_t count, uint64_t
     a.key1 = (uint32_t)(seed >> 32);
     a.stacks = c->d_stacks;
     a.cap = cap;
-    a.switch_high = c->p.switch_high ? c->p.switch_high : 64;
+    a.switch_high = c->p.switch_high ? c->p.switch_high : 128;
     a.switch_low = c->p.switch_low ? c->p.switch_low : 8;
     CK(cudaMemsetAsync(c->d_counter, 0, sizeof(unsigned long long), s), "counter reset");
     CK(cudaEventRecord(c->ev0, s), "event");

@@ -314,6 +314,7 @@ struct Lane {
 
 __device__ __forceinline__ int batch_of(uint32_t h0, uint32_t h1, int B)
 {
+    if (h1 == 0u) return (int)(h0 % (uint32_t)B);          // 32-bit path for ids below 2^32
     unsigned long long h = ((unsigned long long)h1 << 32) | h0;
     return (int)(h % (unsigned long long)B);
 }

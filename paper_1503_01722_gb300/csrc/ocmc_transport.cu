@@ -149,6 +149,16 @@ __device__ void emit_charged(Ctx& c, const Lane& p, int type, float E, float du,
     }
 }
 
+// Pair production: e- and e+ along the photon, sharing E - 2 mc^2 uniformly.
+__device__ __forceinline__ void pair_event(Ctx& c, Lane& p)
+{
+    stat_add(c, ST_PAIR, 1);
+    float avail = p.E - 2.f * MC2F;
+    float Tm = rng_u(p.r, c.a.key0, c.a.key1) * avail, Tp = avail - Tm;
+    emit_charged(c, p, ELECTRON, Tm, p.u, p.v, p.w, 0);
+    emit_charged(c, p, POSITRON, Tp, p.u, p.v, p.w, 1);
+}
+
 // One Woodcock flight and, if real, the interaction. Returns false when the photon ends.
 __device__ __forceinline__ bool photon_step(Ctx& c, Lane& p, unsigned& n_fict)
 {
@@ -191,11 +201,7 @@ __device__ __forceinline__ bool photon_step(Ctx& c, Lane& p, unsigned& n_fict)
         return false;
     }
     if (xi >= fC + fP && p.E > 2.f * MC2F) {
-        stat_add(c, ST_PAIR, 1);
-        float avail = p.E - 2.f * MC2F;
-        float Tm = rng_u(p.r, k0, k1) * avail, Tp = avail - Tm;
-        emit_charged(c, p, ELECTRON, Tm, p.u, p.v, p.w, 0);
-        emit_charged(c, p, POSITRON, Tp, p.u, p.v, p.w, 1);
+        pair_event(c, p);
         return false;
     }
     // Compton scattering (also the rare pair selection below threshold from table interpolation)
@@ -227,6 +233,40 @@ __device__ __forceinline__ bool cross_face(const Ctx& c, Lane& p, int face)
     else if (ax == 1) { p.iy += up ? 1 : -1; p.y = (float)(up ? p.iy : p.iy + 1) * c.a.dy; }
     else { p.iz += up ? 1 : -1; p.z = (float)(up ? p.iz : p.iz + 1) * c.a.dz; }
     return p.ix >= 0 && p.iy >= 0 && p.iz >= 0 && p.ix < c.a.nx && p.iy < c.a.ny && p.iz < c.a.nz;
+}
+
+// Discrete hard event at the end of a step: Moller (probability sM / tot) or bremsstrahlung.
+__device__ __forceinline__ void hard_event(Ctx& c, Lane& p, int m, float sM, float tot)
+{
+    const SmemTables& T = c.T;
+    if (rng_u(p.r, c.a.key0, c.a.key1) * tot < sM) {
+        stat_add(c, ST_MOLLER, 1);
+        float Tk = p.E;
+        float eps = sample_moller(Tk, c.a.pp.w_cc, p.r, c.a.key0, c.a.key1, &c.ok);
+        float W = eps * Tk, T1 = Tk - W;
+        float xphi = rng_u(p.r, c.a.key0, c.a.key1);
+        float mu1 = sqrtf(fminf(1.f, T1 * (Tk + 2.f * MC2F) / (Tk * (T1 + 2.f * MC2F))));
+        float mu2 = sqrtf(fminf(1.f, W * (Tk + 2.f * MC2F) / (Tk * (W + 2.f * MC2F))));
+        float su = p.u, sv2 = p.v, sw = p.w;
+        rotate(su, sv2, sw, mu2, xphi + 0.5f);
+        emit_charged(c, p, ELECTRON, W, su, sv2, sw, 2);
+        rotate(p.u, p.v, p.w, mu1, xphi);
+        p.E = T1;
+    } else {
+        stat_add(c, ST_BREMS, 1);
+        float Tk = p.E;
+        float k = sample_brems(Tk, c.a.pp.w_cb, T.msc[2 * m], T.msc[2 * m + 1], p.r, c.a.key0, c.a.key1, &c.ok);
+        float th = MC2F / (Tk + MC2F);
+        float xphi = rng_u(p.r, c.a.key0, c.a.key1);
+        float gu = p.u, gv = p.v, gw = p.w;
+        rotate(gu, gv, gw, __cosf(th), xphi);
+        if (k >= c.a.pp.e_abs_g)
+            push(c, 0, p.x, p.y, p.z, k, gu, gv, gw, p.ix, p.iy, p.iz, PHOTON, p.r.h0, p.r.h1,
+                 child_sub(p.r.sub, p.r.n, 3));
+        else
+            deposit(c, p.batch, p.ix, p.iy, p.iz, k);
+        p.E = Tk - k;
+    }
 }
 
 // A charged particle that fell below its absorption energy.
@@ -312,34 +352,7 @@ __device__ __forceinline__ bool charged_step(Ctx& c, Lane& p, unsigned& n_hfict)
         float tot = sM + sB;
         if (tot > sighat * 1.00001f) stat_add(c, ST_VIOL, 1);
         if (rng_u(p.r, k0, k1) * sighat < tot) {
-            if (rng_u(p.r, k0, k1) * tot < sM) {
-                stat_add(c, ST_MOLLER, 1);
-                float Tk = p.E;
-                float eps = sample_moller(Tk, a.pp.w_cc, p.r, k0, k1, &c.ok);
-                float W = eps * Tk, T1 = Tk - W;
-                float xphi = rng_u(p.r, k0, k1);
-                float mu1 = sqrtf(fminf(1.f, T1 * (Tk + 2.f * MC2F) / (Tk * (T1 + 2.f * MC2F))));
-                float mu2 = sqrtf(fminf(1.f, W * (Tk + 2.f * MC2F) / (Tk * (W + 2.f * MC2F))));
-                float su = p.u, sv2 = p.v, sw = p.w;
-                rotate(su, sv2, sw, mu2, xphi + 0.5f);
-                emit_charged(c, p, ELECTRON, W, su, sv2, sw, 2);
-                rotate(p.u, p.v, p.w, mu1, xphi);
-                p.E = T1;
-            } else {
-                stat_add(c, ST_BREMS, 1);
-                float Tk = p.E;
-                float k = sample_brems(Tk, a.pp.w_cb, T.msc[2 * m], T.msc[2 * m + 1], p.r, k0, k1, &c.ok);
-                float th = MC2F / (Tk + MC2F);
-                float xphi = rng_u(p.r, k0, k1);
-                float gu = p.u, gv = p.v, gw = p.w;
-                rotate(gu, gv, gw, __cosf(th), xphi);
-                if (k >= a.pp.e_abs_g)
-                    push(c, 0, p.x, p.y, p.z, k, gu, gv, gw, p.ix, p.iy, p.iz, PHOTON, p.r.h0, p.r.h1,
-                         child_sub(p.r.sub, p.r.n, 3));
-                else
-                    deposit(c, p.batch, p.ix, p.iy, p.iz, k);
-                p.E = Tk - k;
-            }
+            hard_event(c, p, m, sM, tot);
             if (p.E < a.pp.e_abs_e) { absorb_charged(c, p); return false; }
         } else {
             n_hfict++;
@@ -348,7 +361,7 @@ __device__ __forceinline__ bool charged_step(Ctx& c, Lane& p, unsigned& n_hfict)
     return true;
 }
 
-__global__ void __maxnreg__(80) k_transport(const TransportArgs a)
+__global__ void __maxnreg__(80) k_transport(const __grid_constant__ TransportArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_top[MAX_WARPS][2];
