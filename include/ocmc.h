@@ -71,6 +71,11 @@ typedef struct {
     int32_t stack_capacity; /* per-warp capacity of each secondary stack          */
     int32_t switch_high;    /* other-type stack size that makes a warp switch type */
     int32_t switch_low;     /* active lanes at or below which a warp switches type */
+    uint32_t stream_tag;    /* XORed into the high word of every history's random  */
+                            /* stream (0); 0x80000000|b reproduces beamlet b       */
+    float beamlet_capacity_scale; /* scales the pilot estimate of beamlet table    */
+                            /* sizes (0 = 1); tables that fill up are enlarged and */
+                            /* the run repeated, so any value gives the same dose  */
 } ocmc_params;
 
 /* Run statistics accumulated since the last ocmc_reset_tally(). */
@@ -181,6 +186,49 @@ const char* ocmc_last_error(ocmc_ctx* ctx);
 
 /* Release the context and its device memory. NULL is ignored. */
 void ocmc_destroy(ocmc_ctx* ctx);
+
+/* ---- batched beamlets --------------------------------------------------------
+ * Many small beams transported together in one persistent launch, captured once in
+ * a CUDA graph and replayed, each beamlet with its own sparse tally (an open-
+ * addressing hash of voxel -> int64 energy). Extends the paper's per-source loop
+ * (Sec. 2.2.1, Table 1) to a queue of sources; the per-history physics is the same.
+ * Beamlet b's histories use random streams whose history high word is
+ * 0x80000000 | b, so a single-beam run with stream_tag = 0x80000000 | b, the same
+ * source, seed and n_histories gives beamlet b's tally densely, bit for bit. */
+typedef struct {
+    float field_x, field_y;  /* cm, rectangle in the plane through iso normal to dir */
+    float ssd;               /* cm; > 0 point source at iso - ssd*dir, <= 0 parallel  */
+    float iso[3];            /* cm, field centre                                      */
+    float dir[3];            /* beam axis (normalised by the library)                 */
+    uint64_t n_histories;    /* 1 .. 2^32 - 1                                         */
+} ocmc_beamlet;
+
+/* Define the beamlets (all share particle type and energy spectrum, as in
+ * ocmc_set_source, with n_bins <= 32). 1 <= n_beamlets <= 65536. Host arrays,
+ * copied. Invalidates table sizes and the captured graph. */
+ocmc_status ocmc_set_beamlets(ocmc_ctx* ctx, int particle, int n_bins, const float* bin_edges_host,
+                              const float* weights_host, int n_beamlets, const ocmc_beamlet* beamlets_host);
+
+/* Transport every beamlet's histories with Philox key `seed` (replacing the
+ * previous beamlet tallies). The first call after ocmc_set_beamlets sizes each
+ * table from two pilot runs (distinct-voxel footprint at two history counts,
+ * extrapolated as a power law) and captures the launch in a CUDA graph; later
+ * calls replay it. A table that fills up is enlarged and the run repeated.
+ * Synchronises cuda_stream. */
+ocmc_status ocmc_run_beamlets(ocmc_ctx* ctx, uint64_t seed, void* cuda_stream);
+
+/* Beamlet b's non-zero voxels in increasing voxel order: idx_host (int32 voxel
+ * index), dose_host (MeV/g per history of that beamlet), raw_host (int64, 2^-28
+ * MeV); any of the three may be NULL. At most `capacity` entries are written;
+ * *nnz receives the number of non-zero voxels. */
+ocmc_status ocmc_get_beamlet_dose(ocmc_ctx* ctx, int beamlet, int32_t* idx_host, float* dose_host,
+                                  int64_t* raw_host, int64_t capacity, int64_t* nnz);
+
+/* Autotuner: times the transport of `pilot_histories` histories of the current
+ * source for a set of launch shapes (threads per block, type-switch thresholds,
+ * stack capacity) and keeps the fastest in the context's parameters (copied to
+ * *chosen if not NULL). Resets the tally. The dose does not depend on the choice. */
+ocmc_status ocmc_autotune(ocmc_ctx* ctx, uint64_t pilot_histories, ocmc_params* chosen);
 
 /* ---- test access to the engine's building blocks ---------------------------
  * These run the same device functions the transport kernel uses, so the

@@ -182,6 +182,34 @@ def random_phantom(n=(24, 20, 28), voxel=(0.5, 0.5, 0.5), seed=0):
     return Phantom(dens, mat, tuple(float(v) for v in voxel))
 
 
+def beamlets(ph: Phantom, n_beamlets=512, seed=1, log10_mean=5.0, log10_sd=0.5, lo=10_000, hi=1_000_000,
+             field=(0.5, 0.5), sad=100.0, offset=4.0):
+    """Pencil beamlets at random gantry angles about the y axis through the phantom centre:
+    field 0.5x0.5 cm^2 in the isocentre plane, point source at SAD, beam's-eye-view
+    offsets uniform in [-offset, offset] cm, histories 10^N(log10_mean, log10_sd)
+    clipped to [lo, hi]. Returns a list of dicts for Engine.set_beamlets."""
+    rng = np.random.default_rng(seed)
+    lx, ly, lz = ph.size_cm
+    c = np.array([lx / 2, ly / 2, lz / 2])
+    out = []
+    for _ in range(n_beamlets):
+        th = rng.uniform(0.0, 2.0 * math.pi)
+        d = np.array([math.sin(th), 0.0, math.cos(th)])
+        e1 = np.array([d[2], 0.0, -d[0]])
+        e2 = np.array([0.0, 1.0, 0.0])
+        a, b = rng.uniform(-offset, offset, 2)
+        n = int(np.clip(round(10.0 ** rng.normal(log10_mean, log10_sd)), lo, hi))
+        out.append({"field": tuple(field), "ssd": float(sad), "iso": tuple(c + a * e1 + b * e2),
+                    "direction": tuple(d), "n_histories": n})
+    return out
+
+
+def beamlets_ct():
+    """512 6 MV pencil beamlets on the CT-like phantom 256x256x128 at 0.2 cm."""
+    ph = ct_like()
+    return ph, spectrum_6mv(), beamlets(ph)
+
+
 def pencil(ph: Phantom, particle, E, direction=(0.0, 0.0, 1.0)):
     """Infinitely thin parallel beam along +z through the x-y centre."""
     lx, ly, _ = ph.size_cm

@@ -1,6 +1,5 @@
 // ocmc_api.cu -- the C ABI (include/ocmc.h): context, validation, memory and launches.
-#include "ocmc.h"
-#include "ocmc_internal.h"
+#include "ocmc_ctx.h"
 
 #include <cmath>
 #include <cstdio>
@@ -15,47 +14,6 @@ cudaError_t launch_add_tally(long long* tally, const long long* in, long long n,
 cudaError_t launch_sum_tally(const long long* tally, long long n, unsigned long long* out, cudaStream_t s);
 }
 
-struct ocmc_ctx {
-    int device = 0;
-    int sms = 0;
-    ocmc_params p{};
-    std::string err;
-    // phantom
-    int nx = 0, ny = 0, nz = 0;
-    float dx = 0.f, dy = 0.f, dz = 0.f;
-    long long nvox = 0;
-    float* d_density = nullptr;
-    uint8_t* d_material = nullptr;
-    bool have_phantom = false;
-    // source
-    bool have_source = false;
-    int particle = 0, n_bins = 0;
-    std::vector<float> edges, weights;
-    float fx = 0.f, fy = 0.f, ssd = 0.f, iso[3] = {0, 0, 0}, dir[3] = {0, 0, 1}, e1[3], e2[3];
-    // tables
-    Tables t{};
-    bool tables_valid = false;
-    // tally and its history counts per batch
-    long long* d_tally = nullptr;
-    int tally_B = 0;
-    std::vector<double> nb;
-    // run scratch
-    unsigned long long* d_stats = nullptr;
-    unsigned long long* d_counter = nullptr;
-    unsigned long long* d_sum = nullptr;
-    int* d_err = nullptr;
-    PRec* d_stacks = nullptr;
-    size_t stack_records = 0;
-    // outputs
-    float* d_dose = nullptr;
-    float* d_sigma = nullptr;
-    double* d_invnb = nullptr;
-    int invnb_cap = 0;
-    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-    bool timed = false;
-    cudaStream_t last_stream = nullptr;
-    bool ran = false;
-};
 
 namespace {
 
@@ -110,6 +68,8 @@ const char* check_params(const ocmc_params* p)
     if (p->stack_capacity != 0 && (p->stack_capacity < 64 || p->stack_capacity > (1 << 20)))
         return "stack_capacity must be 0 or in [64, 2^20]";
     if (p->switch_high < 0 || p->switch_low < 0 || p->switch_low > 32) return "bad switch thresholds";
+    if (!(p->beamlet_capacity_scale >= 0.f && p->beamlet_capacity_scale <= 1e6f))
+        return "beamlet_capacity_scale must be in [0, 1e6]";
     return nullptr;
 }
 
@@ -171,6 +131,7 @@ void fill_args(const ocmc_ctx* c, TransportArgs& a)
     a.pp.d_maxs = c->p.d_maxs; a.pp.f_maxe = c->p.f_maxe; a.pp.s_min = c->p.s_min;
     a.pp.flags = c->p.flags;
     a.pp.n_batches = c->p.n_batches;
+    a.stream_tag = c->p.stream_tag;
     a.tally = reinterpret_cast<unsigned long long*>(c->d_tally);
     a.stats = c->d_stats;
     a.err = c->d_err;
@@ -215,6 +176,62 @@ void launch_shape(const ocmc_ctx* c, int* threads, int* blocks, int* cap)
 }
 
 }  // namespace
+
+namespace ocmc {
+ocmc_status ctx_fail(ocmc_ctx* c, ocmc_status s, const std::string& msg) { return fail(c, s, msg); }
+ocmc_status ctx_cuda_fail(ocmc_ctx* c, cudaError_t e, const char* where) { return cuda_fail(c, e, where); }
+ocmc_status ctx_ensure_tables(ocmc_ctx* c, cudaStream_t s) { return ensure_tables(c, s); }
+void ctx_fill_args(const ocmc_ctx* c, TransportArgs& a) { fill_args(c, a); }
+void ctx_launch_shape(const ocmc_ctx* c, int* threads, int* blocks, int* cap) { launch_shape(c, threads, blocks, cap); }
+
+ocmc_status ctx_ensure_stacks(ocmc_ctx* c, size_t need)
+{
+    if (need > c->stack_records) {
+        if (c->ran || c->last_stream) cudaDeviceSynchronize();
+        CK(dalloc(&c->d_stacks, need), "stack allocation");
+        c->stack_records = need;
+    }
+    return OCMC_OK;
+}
+
+void stratify_bins(const float* edges, const float* weights, int nb, unsigned long long N, int* order,
+                   unsigned long long* bound)
+{
+    for (int i = 0; i < nb; ++i) order[i] = i;
+    for (int i = 1; i < nb; ++i) {
+        int v = order[i], j = i - 1;
+        while (j >= 0 && (edges[order[j]] < edges[v] || (edges[order[j]] == edges[v] && order[j] > v))) {
+            order[j + 1] = order[j];
+            --j;
+        }
+        order[j + 1] = v;
+    }
+    double W = 0.0, cum = 0.0;
+    for (int q = 0; q < nb; ++q) W += (double)weights[order[q]];
+    bound[0] = 0;
+    for (int q = 1; q < nb; ++q) {
+        cum += (double)weights[order[q - 1]];
+        unsigned long long u = (unsigned long long)std::floor((double)N * cum / W);
+        if (u > N) u = N;
+        if (u < bound[q - 1]) u = bound[q - 1];
+        bound[q] = u;
+    }
+    bound[nb] = N;
+}
+
+void beam_frame(const float dir[3], float d[3], float e1[3], float e2[3])
+{
+    double v[3] = {dir[0], dir[1], dir[2]};
+    double n = std::sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+    for (int k = 0; k < 3; ++k) v[k] /= n;
+    double a[3] = {v[2], 0.0, -v[0]};   // y_hat x dir
+    if (std::sqrt(a[0] * a[0] + a[2] * a[2]) < 1e-6) { a[0] = 0.0; a[1] = -v[2]; a[2] = v[1]; }   // x_hat x dir
+    double na = std::sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
+    for (int k = 0; k < 3; ++k) a[k] /= na;
+    double b[3] = {v[1] * a[2] - v[2] * a[1], v[2] * a[0] - v[0] * a[2], v[0] * a[1] - v[1] * a[0]};
+    for (int k = 0; k < 3; ++k) { d[k] = (float)v[k]; e1[k] = (float)a[k]; e2[k] = (float)b[k]; }
+}
+}  // namespace ocmc
 
 extern "C" {
 
@@ -584,6 +601,11 @@ void ocmc_destroy(ocmc_ctx* c)
     dfree(&c->d_sigma); dfree(&c->d_invnb);
     dfree(&c->t.ph); dfree(&c->t.el); dfree(&c->t.el2); dfree(&c->t.phmaj); dfree(&c->t.rinv); dfree(&c->t.msA);
     dfree(&c->t.rmeta); dfree(&c->t.msc); dfree(&c->t.scratch); dfree(&c->t.rho_max);
+    dfree(&c->d_bl); dfree(&c->d_bl_prefix); dfree(&c->d_bl_offs); dfree(&c->d_bl_caps); dfree(&c->d_bl_nnz);
+    dfree(&c->d_bl_over); dfree(&c->d_bl_keys); dfree(&c->d_bl_vals); dfree(&c->d_dense); dfree(&c->d_chunks);
+    dfree(&c->d_oidx); dfree(&c->d_odose); dfree(&c->d_oraw);
+    if (c->bl_exec) cudaGraphExecDestroy(c->bl_exec);
+    if (c->bl_capture) cudaStreamDestroy(c->bl_capture);
     if (c->ev0) cudaEventDestroy(c->ev0);
     if (c->ev1) cudaEventDestroy(c->ev1);
     delete c;

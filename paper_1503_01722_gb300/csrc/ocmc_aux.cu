@@ -141,7 +141,119 @@ __global__ void k_sum_tally(const long long* t, long long n, unsigned long long*
     }
 }
 
+// ---- batched-beamlet tables ------------------------------------------------------------------
+__global__ void k_bl_count(const unsigned int* keys, const unsigned long long* offs, const unsigned int* caps,
+                           unsigned long long* nnz)
+{
+    const int b = blockIdx.x;
+    const unsigned int* k = keys + offs[b];
+    unsigned long long c = 0;
+    for (unsigned int i = threadIdx.x; i < caps[b]; i += blockDim.x) c += k[i] != BL_EMPTY;
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xFFFFFFFFu, c, o);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(nnz + b, c);
+}
+
+__global__ void k_bl_scatter(const unsigned int* keys, const unsigned long long* vals, unsigned long long cap,
+                             long long* dense)
+{
+    for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < cap;
+         i += (unsigned long long)gridDim.x * blockDim.x) {
+        unsigned int k = keys[i];
+        if (k != BL_EMPTY) dense[k] = (long long)vals[i];   // keys are unique within a table
+    }
+}
+
+constexpr int CHUNK = 1024;   // voxels per compaction block (= threads per block)
+
+__global__ void k_chunk_count(const long long* dense, long long nvox, unsigned int* counts)
+{
+    long long v = blockIdx.x * (long long)CHUNK + threadIdx.x;
+    int nz = v < nvox && dense[v] != 0;
+    int c = __syncthreads_count(nz);
+    if (threadIdx.x == 0) counts[blockIdx.x] = c;
+}
+
+// exclusive scan of n counts in place (one block); total to *nnz
+__global__ void k_scan_counts(unsigned int* counts, int n, unsigned long long* nnz)
+{
+    __shared__ unsigned int part[1024];
+    const int per = (n + blockDim.x - 1) / blockDim.x;
+    const int b0 = threadIdx.x * per, b1 = min(n, b0 + per);
+    unsigned int s = 0;
+    for (int i = b0; i < b1; ++i) s += counts[i];
+    part[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = 1; o < (int)blockDim.x; o <<= 1) {
+        unsigned int v = threadIdx.x >= (unsigned)o ? part[threadIdx.x - o] : 0u;
+        __syncthreads();
+        part[threadIdx.x] += v;
+        __syncthreads();
+    }
+    unsigned int run = threadIdx.x ? part[threadIdx.x - 1] : 0u;
+    for (int i = b0; i < b1; ++i) {
+        unsigned int c = counts[i];
+        counts[i] = run;
+        run += c;
+    }
+    if (threadIdx.x == blockDim.x - 1) *nnz = part[threadIdx.x];
+}
+
+__global__ void k_compact(const long long* dense, long long nvox, const unsigned int* offsets, int* idx,
+                          long long* raw, float* dose, const float* density, double scale)
+{
+    __shared__ unsigned int warp_base[CHUNK / 32];
+    long long v = blockIdx.x * (long long)CHUNK + threadIdx.x;
+    long long q = v < nvox ? dense[v] : 0;
+    bool nz = q != 0;
+    unsigned int bal = __ballot_sync(0xFFFFFFFFu, nz);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) warp_base[w] = __popc(bal);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned int r = 0;
+        for (int i = 0; i < CHUNK / 32; ++i) { unsigned int c = warp_base[i]; warp_base[i] = r; r += c; }
+    }
+    __syncthreads();
+    if (nz) {
+        unsigned int pos = offsets[blockIdx.x] + warp_base[w] + __popc(bal & ((1u << lane) - 1u));
+        if (idx) idx[pos] = (int)v;
+        if (raw) raw[pos] = q;
+        if (dose) {
+            float rho = density[v];
+            dose[pos] = rho > 0.f ? (float)((double)q * scale / rho) : 0.f;
+        }
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_bl_count(const unsigned int* keys, const unsigned long long* offs, const unsigned int* caps, int n,
+                            unsigned long long* nnz, cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(nnz, 0, sizeof(unsigned long long) * n, s);
+    if (e != cudaSuccess) return e;
+    k_bl_count<<<n, 256, 0, s>>>(keys, offs, caps, nnz);
+    return cudaGetLastError();
+}
+
+// Entries of one beamlet table in increasing voxel order (deterministic whatever the
+// slot order): scatter into a dense scratch, count per 1024-voxel chunk, scan, compact.
+cudaError_t launch_bl_extract(const unsigned int* keys, const unsigned long long* vals, unsigned long long cap,
+                              long long nvox, long long* dense, unsigned int* block_counts, int* idx_out,
+                              long long* raw_out, float* dose_out, const float* density, double scale,
+                              unsigned long long* nnz_out, cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(dense, 0, sizeof(long long) * nvox, s);
+    if (e != cudaSuccess) return e;
+    int sb = (int)std::min<unsigned long long>((cap + 255) / 256, 152 * 8);
+    k_bl_scatter<<<sb > 0 ? sb : 1, 256, 0, s>>>(keys, vals, cap, dense);
+    int nchunks = (int)((nvox + CHUNK - 1) / CHUNK);
+    k_chunk_count<<<nchunks, CHUNK, 0, s>>>(dense, nvox, block_counts);
+    k_scan_counts<<<1, 1024, 0, s>>>(block_counts, nchunks, nnz_out);
+    if (idx_out || raw_out || dose_out)
+        k_compact<<<nchunks, CHUNK, 0, s>>>(dense, nvox, block_counts, idx_out, raw_out, dose_out, density, scale);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_add_tally(long long* tally, const long long* in, long long n, cudaStream_t s)
 {

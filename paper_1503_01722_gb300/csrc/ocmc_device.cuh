@@ -319,40 +319,42 @@ __device__ __forceinline__ int batch_of(uint32_t h0, uint32_t h1, int B)
     return (int)(h % (unsigned long long)B);
 }
 
-// Source particle of history h (Sec. 2.2 "Materials": point source at SSD with the
-// field defined at the surface, or a parallel beam; energy bins in decreasing
-// energy, Sec. 2.2.1). Draws: energy within the bin, then the two field
-// coordinates. Returns false if the ray misses the phantom; p.E is set either way.
-__device__ __forceinline__ bool init_primary(const TransportArgs& a, unsigned long long h, Lane& p)
+// Source particle of history h of a beam with geometry g (Sec. 2.2 "Materials": point
+// source at SSD with the field defined at the surface, or a parallel beam; energy
+// bins in decreasing energy, Sec. 2.2.1). Draws: energy within the bin, then the
+// two field coordinates. Returns false if the ray misses the phantom; p.E is set
+// either way. The stream is (history lo, history hi ^ h1_tag, sub-stream 0).
+template <class G>
+__device__ __forceinline__ bool init_source(const TransportArgs& a, const G& g, const unsigned long long* bound,
+                                            unsigned long long h, uint32_t h1_tag, Lane& p)
 {
     const SourceDev& s = a.src;
     p.r.h0 = (uint32_t)h;
-    p.r.h1 = (uint32_t)(h >> 32);
+    p.r.h1 = (uint32_t)(h >> 32) ^ h1_tag;
     p.r.sub = 0u;
     p.r.n = 0u;
     p.r.blk = 0xFFFFFFFFu;
     p.type = s.particle == 0 ? PHOTON : ELECTRON;
-    p.batch = batch_of(p.r.h0, p.r.h1, a.pp.n_batches);
     p.steps = 0;
     int lo = 0, hi = s.n_bins - 1;               // last q with bound[q] <= h
     while (lo < hi) {
         int mid = (lo + hi + 1) >> 1;
-        if (s.bound[mid] <= h) lo = mid; else hi = mid - 1;
+        if (bound[mid] <= h) lo = mid; else hi = mid - 1;
     }
     int bin = s.order[lo];
     float e0 = s.lo[bin], e1 = s.hi[bin];
     p.E = e0 + rng_u(p.r, a.key0, a.key1) * (e1 - e0);
     float fa = rng_u(p.r, a.key0, a.key1) - 0.5f, fb = rng_u(p.r, a.key0, a.key1) - 0.5f;
     float P[3], O[3], d[3];
-    for (int k = 0; k < 3; ++k) P[k] = s.iso[k] + fa * s.fx * s.e1[k] + fb * s.fy * s.e2[k];
+    for (int k = 0; k < 3; ++k) P[k] = g.iso[k] + fa * g.fx * g.e1[k] + fb * g.fy * g.e2[k];
     float tmin;
-    if (s.ssd > 0.f) {
-        for (int k = 0; k < 3; ++k) { O[k] = s.iso[k] - s.ssd * s.dir[k]; d[k] = P[k] - O[k]; }
+    if (g.ssd > 0.f) {
+        for (int k = 0; k < 3; ++k) { O[k] = g.iso[k] - g.ssd * g.dir[k]; d[k] = P[k] - O[k]; }
         float inv = rsqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
         for (int k = 0; k < 3; ++k) d[k] *= inv;
         tmin = 0.f;
     } else {
-        for (int k = 0; k < 3; ++k) { O[k] = P[k]; d[k] = s.dir[k]; }
+        for (int k = 0; k < 3; ++k) { O[k] = P[k]; d[k] = g.dir[k]; }
         tmin = -3.0e38f;
     }
     const float Lb[3] = {a.nx * a.dx, a.ny * a.dy, a.nz * a.dz};
@@ -381,6 +383,28 @@ __device__ __forceinline__ bool init_primary(const TransportArgs& a, unsigned lo
     p.iy = min(max((int)floorf(p.y / a.dy), 0), a.ny - 1);
     p.iz = min(max((int)floorf(p.z / a.dz), 0), a.nz - 1);
     return true;
+}
+
+// Single-beam source: history h of the run, batch = h mod B.
+__device__ __forceinline__ bool init_primary(const TransportArgs& a, unsigned long long h, Lane& p)
+{
+    p.batch = batch_of((uint32_t)h, (uint32_t)(h >> 32), a.pp.n_batches);
+    return init_source(a, a.src, a.src.bound, h, a.stream_tag, p);
+}
+
+// Batched beamlets: global history g -> (beamlet b, its history h); stream high word
+// tagged with 0x80000000 | b, which also tells the tally which beamlet a particle
+// belongs to.
+__device__ __forceinline__ bool init_beamlet(const TransportArgs& a, unsigned long long g, Lane& p)
+{
+    int lo = 0, hi = a.n_beamlets - 1;           // last b with prefix[b] <= g
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (a.bl_prefix[mid] <= g) lo = mid; else hi = mid - 1;
+    }
+    const BeamletDev& B = a.beamlets[lo];
+    p.batch = 0;
+    return init_source(a, B, B.bound, g - a.bl_prefix[lo], BL_TAG | (uint32_t)lo, p);
 }
 
 }  // namespace ocmc

@@ -91,6 +91,23 @@ struct SourceDev {
     float lo[MAX_BINS], hi[MAX_BINS];         // bin edges
 };
 
+// Batched beamlets: each beamlet is an independent beam with its own histories,
+// random streams (history counter high word = 0x80000000 | beamlet) and sparse
+// tally (open-addressing hash: uint32 voxel key, int64 value).
+constexpr int MAX_BL_BINS = 32;
+constexpr unsigned int BL_EMPTY = 0xFFFFFFFFu;
+constexpr unsigned int BL_TAG = 0x80000000u;
+
+struct BeamletDev {
+    float fx, fy, ssd, pad0;
+    float iso[3], e1[3], e2[3], dir[3];
+    unsigned long long table_off;              // first slot of this beamlet's table
+    unsigned int cap_mask;                     // table capacity - 1 (power of two)
+    unsigned int pad1;
+    unsigned long long n;                      // histories
+    unsigned long long bound[MAX_BL_BINS + 1]; // energy-bin stratification of its histories
+};
+
 struct TransportArgs {
     // geometry
     int nx, ny, nz;
@@ -113,6 +130,14 @@ struct TransportArgs {
     unsigned long long* stats;  // ST_COUNT
     int* err;
     SourceDev src;
+    uint32_t stream_tag;                 // XORed into the high history word (single-beam mode)
+    // batched beamlets (beamlets == nullptr: single-beam mode with the dense tally)
+    const BeamletDev* beamlets;
+    const unsigned long long* bl_prefix; // n_beamlets + 1 prefix sums of histories
+    int n_beamlets;
+    unsigned int* bl_keys;
+    unsigned long long* bl_vals;
+    unsigned int* bl_overflow;           // per-beamlet table-full flags
 };
 
 // kernels / launchers (defined in the .cu files)
@@ -133,5 +158,11 @@ cudaError_t launch_test_tables(const TransportArgs& a, int m, const float* E, in
 cudaError_t launch_test_csda(const TransportArgs& a, int m, const float* T, const float* X, int n, float* out,
                              cudaStream_t s);
 void material_defs(MatDef out[NMAT]);
+cudaError_t launch_bl_count(const unsigned int* keys, const unsigned long long* offs, const unsigned int* caps, int n,
+                            unsigned long long* nnz, cudaStream_t s);
+cudaError_t launch_bl_extract(const unsigned int* keys, const unsigned long long* vals, unsigned long long cap,
+                              long long nvox, long long* dense, unsigned int* block_counts, int* idx_out,
+                              long long* raw_out, float* dose_out, const float* density, double scale,
+                              unsigned long long* nnz_out, cudaStream_t s);
 
 }  // namespace ocmc

@@ -52,11 +52,35 @@ __device__ __forceinline__ unsigned long long fx(float e)
     return q < 4294967040.f ? (unsigned long long)__float2uint_rn(q) : (unsigned long long)__float2ll_rn(q);
 }
 
-__device__ __forceinline__ void deposit(Ctx& c, int batch, int ix, int iy, int iz, float dE)
+// Batched-beamlet tally: add q to voxel v of beamlet b's open-addressing table
+// (linear probing, key claimed by compare-and-swap). A full table sets the
+// beamlet's overflow flag; the host then enlarges that table and runs again.
+__device__ __noinline__ void hash_add(const TransportArgs& a, uint32_t b, uint32_t v, unsigned long long q)
+{
+    const BeamletDev& B = a.beamlets[b];
+    unsigned int* keys = a.bl_keys + B.table_off;
+    unsigned long long* vals = a.bl_vals + B.table_off;
+    const uint32_t mask = B.cap_mask;
+    uint32_t h = v * 0x9E3779B1u;
+    uint32_t s = (h ^ (h >> 15)) & mask;
+    for (int probe = 0; probe <= (int)min(mask, 4095u); ++probe) {
+        uint32_t k = *((volatile unsigned int*)(keys + s));
+        if (k == BL_EMPTY) k = atomicCAS(keys + s, BL_EMPTY, v);
+        if (k == BL_EMPTY || k == v) {
+            atomicAdd(vals + s, q);
+            return;
+        }
+        s = (s + 1u) & mask;
+    }
+    atomicOr(a.bl_overflow + b, 1u);
+}
+
+__device__ __forceinline__ void deposit(Ctx& c, const Lane& p, int ix, int iy, int iz, float dE)
 {
     if (dE > 0.f) {
         long long v = ix + (long long)c.a.nx * (iy + (long long)c.a.ny * iz);
-        atomicAdd(c.a.tally + (long long)batch * c.a.nvox + v, fx(dE));
+        if (c.a.beamlets) hash_add(c.a, p.r.h1 & ~BL_TAG, (uint32_t)v, fx(dE));
+        else atomicAdd(c.a.tally + (long long)p.batch * c.a.nvox + v, fx(dE));
     }
 }
 
@@ -103,7 +127,7 @@ __device__ __forceinline__ void pop_lane(const Ctx& c, int t, int slot, Lane& p)
     p.u = __uint_as_float(b.x); p.v = __uint_as_float(b.y); p.w = __uint_as_float(b.z);
     p.ix = b.w & 1023u; p.iy = (b.w >> 10) & 1023u; p.iz = (b.w >> 20) & 1023u; p.type = b.w >> 30;
     p.r.h0 = d.x; p.r.h1 = d.y; p.r.sub = d.z; p.r.n = d.w; p.r.blk = 0xFFFFFFFFu;
-    p.batch = batch_of(d.x, d.y, c.a.pp.n_batches);
+    p.batch = c.a.beamlets ? 0 : batch_of(d.x, d.y ^ c.a.stream_tag, c.a.pp.n_batches);
     p.steps = 0;
 }
 
@@ -130,7 +154,7 @@ __device__ __forceinline__ void annihilate(Ctx& c, const Lane& p, Rng& r)
         push(c, 0, p.x, p.y, p.z, MC2F, -st * cp, -st * sp, -wc, p.ix, p.iy, p.iz, PHOTON, r.h0, r.h1,
              child_sub(r.sub, r.n, 1));
     } else {
-        deposit(c, p.batch, p.ix, p.iy, p.iz, 2.f * MC2F);
+        deposit(c, p, p.ix, p.iy, p.iz, 2.f * MC2F);
     }
 }
 
@@ -141,7 +165,7 @@ __device__ void emit_charged(Ctx& c, const Lane& p, int type, float E, float du,
         push(c, 1, p.x, p.y, p.z, E, du, dv, dw, p.ix, p.iy, p.iz, type, p.r.h0, p.r.h1, sub);
         return;
     }
-    deposit(c, p.batch, p.ix, p.iy, p.iz, E);
+    deposit(c, p, p.ix, p.iy, p.iz, E);
     if (type == POSITRON) {
         Rng r;
         r.h0 = p.r.h0; r.h1 = p.r.h1; r.sub = sub; r.n = 0; r.blk = 0xFFFFFFFFu;
@@ -197,7 +221,7 @@ __device__ __forceinline__ bool photon_step(Ctx& c, Lane& p, unsigned& n_fict)
     float xi = rng_u(p.r, k0, k1);
     if (xi >= fC && xi < fC + fP) {
         stat_add(c, ST_PHOTO, 1);
-        deposit(c, p.batch, p.ix, p.iy, p.iz, p.E);
+        deposit(c, p, p.ix, p.iy, p.iz, p.E);
         return false;
     }
     if (xi >= fC + fP && p.E > 2.f * MC2F) {
@@ -219,7 +243,7 @@ __device__ __forceinline__ bool photon_step(Ctx& c, Lane& p, unsigned& n_fict)
     }
     p.E = E1;
     if (p.E < a.pp.e_abs_g) {
-        deposit(c, p.batch, p.ix, p.iy, p.iz, p.E);
+        deposit(c, p, p.ix, p.iy, p.iz, p.E);
         return false;
     }
     return true;
@@ -264,7 +288,7 @@ __device__ __forceinline__ void hard_event(Ctx& c, Lane& p, int m, float sM, flo
             push(c, 0, p.x, p.y, p.z, k, gu, gv, gw, p.ix, p.iy, p.iz, PHOTON, p.r.h0, p.r.h1,
                  child_sub(p.r.sub, p.r.n, 3));
         else
-            deposit(c, p.batch, p.ix, p.iy, p.iz, k);
+            deposit(c, p, p.ix, p.iy, p.iz, k);
         p.E = Tk - k;
     }
 }
@@ -272,7 +296,7 @@ __device__ __forceinline__ void hard_event(Ctx& c, Lane& p, int m, float sM, flo
 // A charged particle that fell below its absorption energy.
 __device__ __forceinline__ void absorb_charged(Ctx& c, Lane& p)
 {
-    deposit(c, p.batch, p.ix, p.iy, p.iz, p.E);
+    deposit(c, p, p.ix, p.iy, p.iz, p.E);
     if (p.type == POSITRON) annihilate(c, p, p.r);
 }
 
@@ -340,7 +364,7 @@ __device__ __forceinline__ bool charged_step(Ctx& c, Lane& p, unsigned& n_hfict)
         Eend = csda_end2(T, m, E0, R0, g0, rho * (s1 + tex));
         crossed = true;
     }
-    deposit(c, p.batch, p.ix, p.iy, p.iz, E0 - Eend);
+    deposit(c, p, p.ix, p.iy, p.iz, E0 - Eend);
     p.E = Eend;
     if (crossed && !cross_face(c, p, face2)) { escape(c, p); return false; }
     if (p.E < a.pp.e_abs_e) { absorb_charged(c, p); return false; }
@@ -405,7 +429,7 @@ __global__ void __maxnreg__(80) k_transport(const __grid_constant__ TransportArg
                 int r2 = rank - take;
                 if (!active && r2 >= 0 && r2 < want && base + r2 < a.count) {
                     hist++;
-                    bool in = init_primary(a, a.first + base + r2, p);
+                    bool in = a.beamlets ? init_beamlet(a, base + r2, p) : init_primary(a, a.first + base + r2, p);
                     float ecut = p.type == PHOTON ? a.pp.e_abs_g : a.pp.e_abs_e;
                     if (!in) {
                         missed++;
@@ -413,7 +437,7 @@ __global__ void __maxnreg__(80) k_transport(const __grid_constant__ TransportArg
                     } else {
                         e_in += fx(p.E);
                         if (p.E >= ecut && !(p.type != PHOTON && (a.pp.flags & 8))) active = true;
-                        else deposit(c, p.batch, p.ix, p.iy, p.iz, p.E);
+                        else deposit(c, p, p.ix, p.iy, p.iz, p.E);
                     }
                 }
             }

@@ -30,7 +30,13 @@ class Params(C.Structure):
                 ("d_maxs", C.c_float), ("f_maxe", C.c_float), ("s_min", C.c_float),
                 ("n_batches", C.c_int32), ("flags", C.c_int32),
                 ("block_threads", C.c_int32), ("blocks_per_sm", C.c_int32), ("stack_capacity", C.c_int32),
-                ("switch_high", C.c_int32), ("switch_low", C.c_int32)]
+                ("switch_high", C.c_int32), ("switch_low", C.c_int32), ("stream_tag", C.c_uint32),
+                ("beamlet_capacity_scale", C.c_float)]
+
+
+class Beamlet(C.Structure):
+    _fields_ = [("field_x", C.c_float), ("field_y", C.c_float), ("ssd", C.c_float), ("iso", C.c_float * 3),
+                ("dir", C.c_float * 3), ("n_histories", C.c_uint64)]
 
 
 class Stats(C.Structure):
@@ -70,6 +76,10 @@ def _load():
         "ocmc_test_sample": (C.c_int, [P, C.c_int, C.c_int, C.c_float, C.c_float, C.c_uint64, C.c_uint64, P]),
         "ocmc_test_tables": (C.c_int, [P, C.c_int, P, C.c_int, P]),
         "ocmc_test_csda": (C.c_int, [P, C.c_int, P, P, C.c_int, P]),
+        "ocmc_set_beamlets": (C.c_int, [P, C.c_int, C.c_int, P, P, C.c_int, P]),
+        "ocmc_run_beamlets": (C.c_int, [P, C.c_uint64, P]),
+        "ocmc_get_beamlet_dose": (C.c_int, [P, C.c_int, P, P, P, C.c_int64, C.POINTER(C.c_int64)]),
+        "ocmc_autotune": (C.c_int, [P, C.c_uint64, C.POINTER(Params)]),
         "ocmc_run_noalloc": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, P, P, C.c_float, C.c_float, C.c_float,
                                        C.c_int, C.c_int, P, P, C.c_float, C.c_float, C.c_float,
                                        C.POINTER(C.c_float), C.POINTER(C.c_float), C.POINTER(Params),
@@ -230,6 +240,45 @@ class Engine:
         s = Stats()
         self._check(lib.ocmc_get_stats(self._c, C.byref(s)))
         return {k: getattr(s, k) for k, _ in Stats._fields_}
+
+    # ---- batched beamlets ----
+    def set_beamlets(self, particle, edges, weights, beamlets):
+        """beamlets: sequence of dicts/objects with field (fx, fy), ssd, iso, direction, n_histories."""
+        e = np.ascontiguousarray(edges, np.float32)
+        w = np.ascontiguousarray(weights, np.float32)
+        arr = (Beamlet * len(beamlets))()
+        for i, b in enumerate(beamlets):
+            g = b if isinstance(b, dict) else b.__dict__
+            arr[i].field_x, arr[i].field_y = map(float, g["field"])
+            arr[i].ssd = float(g["ssd"])
+            arr[i].iso[:] = [float(v) for v in g["iso"]]
+            arr[i].dir[:] = [float(v) for v in g["direction"]]
+            arr[i].n_histories = int(g["n_histories"])
+        self._check(lib.ocmc_set_beamlets(self._c, int(particle), len(w), C.c_void_p(e.ctypes.data),
+                                          C.c_void_p(w.ctypes.data), len(beamlets), arr))
+        self.n_beamlets = len(beamlets)
+
+    def run_beamlets(self, seed=1, stream=None):
+        self._check(lib.ocmc_run_beamlets(self._c, int(seed), _stream_ptr(stream)))
+
+    def beamlet_dose(self, b):
+        """(voxel indices int32, dose float32 MeV/g per history, raw int64) in voxel order."""
+        nnz = C.c_int64()
+        self._check(lib.ocmc_get_beamlet_dose(self._c, int(b), None, None, None, 0, C.byref(nnz)))
+        n = nnz.value
+        idx = np.empty(n, np.int32)
+        dose = np.empty(n, np.float32)
+        raw = np.empty(n, np.int64)
+        self._check(lib.ocmc_get_beamlet_dose(self._c, int(b), C.c_void_p(idx.ctypes.data),
+                                              C.c_void_p(dose.ctypes.data), C.c_void_p(raw.ctypes.data), n,
+                                              C.byref(nnz)))
+        return idx, dose, raw
+
+    def autotune(self, pilot_histories):
+        p = Params()
+        self._check(lib.ocmc_autotune(self._c, int(pilot_histories), C.byref(p)))
+        self.params = p
+        return p
 
     # ---- building blocks for the tests ----
     def test_source(self, n_total, first=0, count=None, seed=1):
