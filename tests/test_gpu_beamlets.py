@@ -85,9 +85,11 @@ def test_tables_that_overflow_are_enlarged_with_identical_result(ocmc, setup):
 
 def test_beamlet_dose_statistically_matches_oracle(ocmc, setup):
     ph, spec, bl = setup
+    # a widened beamlet (3x3 cm2) gives a 10%-isodose region of several hundred voxels
     b = 4
     B = dict(bl[b])
-    B["n_histories"] = 60_000
+    B["field"] = (3.0, 3.0)
+    B["n_histories"] = 150_000
     beam = I.Beam(0, spec[0], spec[1], B["field"], B["ssd"], B["iso"], B["direction"])
     with ocmc.Engine(0, n_batches=50, stream_tag=0x80000000 | b) as e:
         e.create_phantom(ph)
