@@ -33,7 +33,11 @@ constexpr unsigned FULL = 0xFFFFFFFFu;
 constexpr int MAX_WARPS = 32;
 constexpr int STEP_LIMIT = 1 << 22;
 
-struct Ctx {
+// BL: batched-beamlet mode (sparse hash tallies) or single-beam mode (dense tally);
+// a compile-time flag so the single-beam kernel carries no beamlet code.
+template <bool BL>
+struct CtxT {
+    static constexpr bool beamlets = BL;
     const TransportArgs& a;
     const SmemTables& T;
     PRec* stk;                   // warp's stacks: [0, cap) photons, [cap, 2cap) charged
@@ -43,7 +47,8 @@ struct Ctx {
     bool ok;
 };
 
-__device__ __forceinline__ void stat_add(Ctx& c, int k, unsigned long long v) { atomicAdd(c.st + k, v); }
+template <class C>
+__device__ __forceinline__ void stat_add(C& c, int k, unsigned long long v) { atomicAdd(c.st + k, v); }
 
 // fixed-point energy (round to nearest even); the 32-bit conversion is exact below 16 MeV
 __device__ __forceinline__ unsigned long long fx(float e)
@@ -75,16 +80,18 @@ __device__ __noinline__ void hash_add(const TransportArgs& a, uint32_t b, uint32
     atomicOr(a.bl_overflow + b, 1u);
 }
 
-__device__ __forceinline__ void deposit(Ctx& c, const Lane& p, int ix, int iy, int iz, float dE)
+template <class C>
+__device__ __forceinline__ void deposit(C& c, const Lane& p, int ix, int iy, int iz, float dE)
 {
     if (dE > 0.f) {
         long long v = ix + (long long)c.a.nx * (iy + (long long)c.a.ny * iz);
-        if (c.a.beamlets) hash_add(c.a, p.r.h1 & ~BL_TAG, (uint32_t)v, fx(dE));
+        if constexpr (C::beamlets) hash_add(c.a, p.r.h1 & ~BL_TAG, (uint32_t)v, fx(dE));
         else atomicAdd(c.a.tally + (long long)p.batch * c.a.nvox + v, fx(dE));
     }
 }
 
-__device__ __forceinline__ void push(Ctx& c, int t, float x, float y, float z, float E, float u, float v, float w, int ix,
+template <class C>
+__device__ __forceinline__ void push(C& c, int t, float x, float y, float z, float E, float u, float v, float w, int ix,
                                      int iy, int iz, int type, uint32_t h0, uint32_t h1, uint32_t sub)
 {
     int slot = atomicAdd(c.top + t, 1);
@@ -102,7 +109,8 @@ __device__ __forceinline__ void push(Ctx& c, int t, float x, float y, float z, f
     q[2] = make_uint4(h0, h1, sub, 0u);
 }
 
-__device__ __forceinline__ void push_lane(Ctx& c, int t, const Lane& p)
+template <class C>
+__device__ __forceinline__ void push_lane(C& c, int t, const Lane& p)
 {
     int slot = atomicAdd(c.top + t, 1);
     if (slot >= c.a.cap) {
@@ -119,7 +127,8 @@ __device__ __forceinline__ void push_lane(Ctx& c, int t, const Lane& p)
     q[2] = make_uint4(p.r.h0, p.r.h1, p.r.sub, p.r.n);
 }
 
-__device__ __forceinline__ void pop_lane(const Ctx& c, int t, int slot, Lane& p)
+template <class C>
+__device__ __forceinline__ void pop_lane(const C& c, int t, int slot, Lane& p)
 {
     const uint4* q = reinterpret_cast<const uint4*>(c.stk + (size_t)t * c.a.cap + slot);
     uint4 a = q[0], b = q[1], d = q[2];
@@ -127,11 +136,13 @@ __device__ __forceinline__ void pop_lane(const Ctx& c, int t, int slot, Lane& p)
     p.u = __uint_as_float(b.x); p.v = __uint_as_float(b.y); p.w = __uint_as_float(b.z);
     p.ix = b.w & 1023u; p.iy = (b.w >> 10) & 1023u; p.iz = (b.w >> 20) & 1023u; p.type = b.w >> 30;
     p.r.h0 = d.x; p.r.h1 = d.y; p.r.sub = d.z; p.r.n = d.w; p.r.blk = 0xFFFFFFFFu;
-    p.batch = c.a.beamlets ? 0 : batch_of(d.x, d.y ^ c.a.stream_tag, c.a.pp.n_batches);
+    if constexpr (C::beamlets) p.batch = 0;
+    else p.batch = batch_of(d.x, d.y ^ c.a.stream_tag, c.a.pp.n_batches);
     p.steps = 0;
 }
 
-__device__ __forceinline__ void escape(Ctx& c, const Lane& p)
+template <class C>
+__device__ __forceinline__ void escape(C& c, const Lane& p)
 {
     stat_add(c, ST_ESCAPED, 1);
     stat_add(c, ST_E_ESC, fx(p.E));
@@ -139,10 +150,12 @@ __device__ __forceinline__ void escape(Ctx& c, const Lane& p)
 
 // e-/e+ created at p's position with energy E and direction d: pushed if above the
 // absorption energy, otherwise deposited (a positron then annihilates).
-__device__ void emit_charged(Ctx& c, const Lane& p, int type, float E, float du, float dv, float dw, uint32_t slot);
+template <class C>
+__device__ void emit_charged(C& c, const Lane& p, int type, float E, float du, float dv, float dw, uint32_t slot);
 
 // Two photons of mc^2, back to back and isotropic, from a positron with stream r.
-__device__ __forceinline__ void annihilate(Ctx& c, const Lane& p, Rng& r)
+template <class C>
+__device__ __forceinline__ void annihilate(C& c, const Lane& p, Rng& r)
 {
     float wc = 2.f * rng_u(r, c.a.key0, c.a.key1) - 1.f, xi = rng_u(r, c.a.key0, c.a.key1);
     float st = sqrtf(fmaxf(0.f, 1.f - wc * wc)), sp, cp;
@@ -158,7 +171,8 @@ __device__ __forceinline__ void annihilate(Ctx& c, const Lane& p, Rng& r)
     }
 }
 
-__device__ void emit_charged(Ctx& c, const Lane& p, int type, float E, float du, float dv, float dw, uint32_t slot)
+template <class C>
+__device__ void emit_charged(C& c, const Lane& p, int type, float E, float du, float dv, float dw, uint32_t slot)
 {
     uint32_t sub = child_sub(p.r.sub, p.r.n, slot);
     if (E >= c.a.pp.e_abs_e && !(c.a.pp.flags & 8)) {
@@ -174,7 +188,8 @@ __device__ void emit_charged(Ctx& c, const Lane& p, int type, float E, float du,
 }
 
 // Pair production: e- and e+ along the photon, sharing E - 2 mc^2 uniformly.
-__device__ __forceinline__ void pair_event(Ctx& c, Lane& p)
+template <class C>
+__device__ __forceinline__ void pair_event(C& c, Lane& p)
 {
     stat_add(c, ST_PAIR, 1);
     float avail = p.E - 2.f * MC2F;
@@ -184,7 +199,8 @@ __device__ __forceinline__ void pair_event(Ctx& c, Lane& p)
 }
 
 // One Woodcock flight and, if real, the interaction. Returns false when the photon ends.
-__device__ __forceinline__ bool photon_step(Ctx& c, Lane& p, unsigned& n_fict)
+template <class C>
+__device__ __forceinline__ bool photon_step(C& c, Lane& p, unsigned& n_fict)
 {
     const TransportArgs& a = c.a;
     const SmemTables& T = c.T;
@@ -249,7 +265,8 @@ __device__ __forceinline__ bool photon_step(Ctx& c, Lane& p, unsigned& n_fict)
     return true;
 }
 
-__device__ __forceinline__ bool cross_face(const Ctx& c, Lane& p, int face)
+template <class C>
+__device__ __forceinline__ bool cross_face(const C& c, Lane& p, int face)
 {
     int ax = face >> 1;
     bool up = face & 1;
@@ -260,7 +277,8 @@ __device__ __forceinline__ bool cross_face(const Ctx& c, Lane& p, int face)
 }
 
 // Discrete hard event at the end of a step: Moller (probability sM / tot) or bremsstrahlung.
-__device__ __forceinline__ void hard_event(Ctx& c, Lane& p, int m, float sM, float tot)
+template <class C>
+__device__ __forceinline__ void hard_event(C& c, Lane& p, int m, float sM, float tot)
 {
     const SmemTables& T = c.T;
     if (rng_u(p.r, c.a.key0, c.a.key1) * tot < sM) {
@@ -294,14 +312,16 @@ __device__ __forceinline__ void hard_event(Ctx& c, Lane& p, int m, float sM, flo
 }
 
 // A charged particle that fell below its absorption energy.
-__device__ __forceinline__ void absorb_charged(Ctx& c, Lane& p)
+template <class C>
+__device__ __forceinline__ void absorb_charged(C& c, Lane& p)
 {
     deposit(c, p, p.ix, p.iy, p.iz, p.E);
     if (p.type == POSITRON) annihilate(c, p, p.r);
 }
 
 // One condensed-history step. Returns false when the particle ends.
-__device__ __forceinline__ bool charged_step(Ctx& c, Lane& p, unsigned& n_hfict)
+template <class C>
+__device__ __forceinline__ bool charged_step(C& c, Lane& p, unsigned& n_hfict)
 {
     const TransportArgs& a = c.a;
     const SmemTables& T = c.T;
@@ -324,10 +344,10 @@ __device__ __forceinline__ bool charged_step(Ctx& c, Lane& p, unsigned& n_hfict)
     EIdx ei = e_index(p.E);
     const int mb = m * NE;
     float4 A = T.el[mb + ei.i], B = T.el[mb + ei.i + 1];
-    float2 C = T.el2[mb + ei.i], D = T.el2[mb + ei.i + 1];
+    float2 C2 = T.el2[mb + ei.i], D2 = T.el2[mb + ei.i + 1];
     float lnR = lerp1(A.x, B.x, ei.f);
-    float s_maxe = lerp1(C.x, D.x, ei.f) / rho;
-    float sighat = (a.pp.flags & 1) ? 0.f : C.y;
+    float s_maxe = lerp1(C2.x, D2.x, ei.f) / rho;
+    float sighat = (a.pp.flags & 1) ? 0.f : C2.y;
     float d_ev = sighat > 0.f ? -__logf(rng_u(p.r, k0, k1)) / (rho * sighat) : 3.0e38f;
     float s = sv;
     int lim = 0;
@@ -385,6 +405,7 @@ __device__ __forceinline__ bool charged_step(Ctx& c, Lane& p, unsigned& n_hfict)
     return true;
 }
 
+template <bool BL>
 __global__ void __maxnreg__(80) k_transport(const __grid_constant__ TransportArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -396,7 +417,7 @@ __global__ void __maxnreg__(80) k_transport(const __grid_constant__ TransportArg
     SmemTables T = stage_tables(a.t, smem);   // ends with __syncthreads()
 
     const long long gw = (long long)blockIdx.x * (blockDim.x >> 5) + wib;
-    Ctx c{a, T, a.stacks + (size_t)gw * 2 * a.cap, s_top[wib], s_st,
+    CtxT<BL> c{a, T, a.stacks + (size_t)gw * 2 * a.cap, s_top[wib], s_st,
           1.f / a.dx, 1.f / a.dy, 1.f / a.dz, a.nx * a.dx, a.ny * a.dy, a.nz * a.dz, true};
     const unsigned lt = (1u << lane) - 1u;
     const int src_mode = a.src.particle == 0 ? 0 : 1;
@@ -429,7 +450,9 @@ __global__ void __maxnreg__(80) k_transport(const __grid_constant__ TransportArg
                 int r2 = rank - take;
                 if (!active && r2 >= 0 && r2 < want && base + r2 < a.count) {
                     hist++;
-                    bool in = a.beamlets ? init_beamlet(a, base + r2, p) : init_primary(a, a.first + base + r2, p);
+                    bool in;
+                    if constexpr (BL) in = init_beamlet(a, base + r2, p);
+                    else in = init_primary(a, a.first + base + r2, p);
                     float ecut = p.type == PHOTON ? a.pp.e_abs_g : a.pp.e_abs_e;
                     if (!in) {
                         missed++;
@@ -511,17 +534,24 @@ size_t transport_smem_bytes(int /*threads*/) { return SMEM_TABLE_BYTES; }
 
 int transport_max_blocks_per_sm(int threads, size_t smem)
 {
-    cudaFuncSetAttribute(k_transport, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_transport<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_transport<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_transport, threads, smem) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_transport<false>, threads, smem) != cudaSuccess) return 0;
     return n;
 }
 
 cudaError_t launch_transport(const TransportArgs& a, int blocks, int threads, size_t smem, cudaStream_t s)
 {
-    cudaError_t e = cudaFuncSetAttribute(k_transport, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    k_transport<<<blocks, threads, smem, s>>>(a);
+    if (a.beamlets) {
+        cudaError_t e = cudaFuncSetAttribute(k_transport<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k_transport<true><<<blocks, threads, smem, s>>>(a);
+    } else {
+        cudaError_t e = cudaFuncSetAttribute(k_transport<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k_transport<false><<<blocks, threads, smem, s>>>(a);
+    }
     return cudaGetLastError();
 }
 

@@ -98,10 +98,14 @@ def test_beamlet_dose_statistically_matches_oracle(ocmc, setup):
         D, S = e.dose()
     r = O.run(ph, beam, B["n_histories"], seed=3, p=O.params(n_batches=50))
     Dr, Sr = r.dose()
-    mask = Dr >= 0.1 * Dr.max()
+    # tissue only: the air around the body (0.0012 g/cm^3) has a huge, noisy dose per mass
+    tissue = ph.density >= 0.1
+    dmax = Dr[tissue].max()
+    mask = tissue & (Dr >= 0.1 * dmax)
     z = np.abs(D - Dr)[mask] / np.sqrt(S ** 2 + Sr ** 2)[mask]
+    assert mask.sum() > 300
     assert np.mean(z <= 3) >= 0.99
-    assert abs((D - Dr)[mask].mean() / Dr.max()) < 0.005
+    assert abs((D - Dr)[mask].mean() / dmax) < 0.005
 
 
 def test_autotune_keeps_the_dose(ocmc):
