@@ -68,6 +68,9 @@ const char* check_params(const ocmc_params* p)
     if (p->stack_capacity != 0 && (p->stack_capacity < 64 || p->stack_capacity > (1 << 20)))
         return "stack_capacity must be 0 or in [64, 2^20]";
     if (p->switch_high < 0 || p->switch_low < 0 || p->switch_low > 32) return "bad switch thresholds";
+    if (p->refill_min < 0 || p->refill_min > 32) return "refill_min must be in [0, 32]";
+    if (p->max_registers != 0 && !transport_nreg_supported(p->max_registers))
+        return "max_registers must be 0, 56, 64 or 80";
     if (!(p->beamlet_capacity_scale >= 0.f && p->beamlet_capacity_scale <= 1e6f))
         return "beamlet_capacity_scale must be in [0, 1e6]";
     return nullptr;
@@ -165,11 +168,12 @@ ocmc_status ensure_tally(ocmc_ctx* c)
     return OCMC_OK;
 }
 
-void launch_shape(const ocmc_ctx* c, int* threads, int* blocks, int* cap)
+void launch_shape(const ocmc_ctx* c, int* threads, int* blocks, int* cap, int* nreg)
 {
-    *threads = c->p.block_threads ? c->p.block_threads : 256;
+    *nreg = c->p.max_registers ? c->p.max_registers : 64;
+    *threads = c->p.block_threads ? c->p.block_threads : (*nreg == 64 ? 512 : *nreg == 56 ? 384 : 256);
     size_t smem = transport_smem_bytes(*threads);
-    int bps = c->p.blocks_per_sm ? c->p.blocks_per_sm : transport_max_blocks_per_sm(*threads, smem);
+    int bps = c->p.blocks_per_sm ? c->p.blocks_per_sm : transport_max_blocks_per_sm(*threads, smem, *nreg);
     if (bps < 1) bps = 1;
     *blocks = c->sms * bps;
     *cap = c->p.stack_capacity ? c->p.stack_capacity : 1024;
@@ -182,7 +186,10 @@ ocmc_status ctx_fail(ocmc_ctx* c, ocmc_status s, const std::string& msg) { retur
 ocmc_status ctx_cuda_fail(ocmc_ctx* c, cudaError_t e, const char* where) { return cuda_fail(c, e, where); }
 ocmc_status ctx_ensure_tables(ocmc_ctx* c, cudaStream_t s) { return ensure_tables(c, s); }
 void ctx_fill_args(const ocmc_ctx* c, TransportArgs& a) { fill_args(c, a); }
-void ctx_launch_shape(const ocmc_ctx* c, int* threads, int* blocks, int* cap) { launch_shape(c, threads, blocks, cap); }
+void ctx_launch_shape(const ocmc_ctx* c, int* threads, int* blocks, int* cap, int* nreg)
+{
+    launch_shape(c, threads, blocks, cap, nreg);
+}
 
 ocmc_status ctx_ensure_stacks(ocmc_ctx* c, size_t need)
 {
@@ -407,8 +414,8 @@ ocmc_status ocmc_run_range(ocmc_ctx* c, uint64_t first, uint64_t count, uint64_t
     if (st != OCMC_OK) return st;
     st = ensure_tables(c, s);
     if (st != OCMC_OK) return st;
-    int threads, blocks, cap;
-    launch_shape(c, &threads, &blocks, &cap);
+    int threads, blocks, cap, nreg;
+    launch_shape(c, &threads, &blocks, &cap, &nreg);
     size_t need = (size_t)blocks * (threads / 32) * 2 * cap;
     if (need > c->stack_records) {
         if (c->ran || c->last_stream) cudaDeviceSynchronize();
@@ -427,9 +434,10 @@ ocmc_status ocmc_run_range(ocmc_ctx* c, uint64_t first, uint64_t count, uint64_t
     a.cap = cap;
     a.switch_high = c->p.switch_high ? c->p.switch_high : 128;
     a.switch_low = c->p.switch_low ? c->p.switch_low : 8;
+    a.refill_min = c->p.refill_min ? c->p.refill_min : 1;
     CK(cudaMemsetAsync(c->d_counter, 0, sizeof(unsigned long long), s), "counter reset");
     CK(cudaEventRecord(c->ev0, s), "event");
-    CK(launch_transport(a, blocks, threads, transport_smem_bytes(threads), s), "transport launch");
+    CK(launch_transport(a, blocks, threads, transport_smem_bytes(threads), s, nreg), "transport launch");
     CK(cudaEventRecord(c->ev1, s), "event");
     c->timed = true;
     c->last_stream = s;

@@ -79,7 +79,7 @@ ocmc_status upload_beamlets(ocmc_ctx* c, const std::vector<unsigned long long>& 
 
 // Transport arguments of a beamlet launch (tables cleared by the caller's memsets).
 ocmc_status beamlet_args(ocmc_ctx* c, unsigned long long total, uint64_t seed, TransportArgs& a, int* threads,
-                         int* blocks)
+                         int* blocks, int* nreg)
 {
     ctx_fill_args(c, a);
     a.src.particle = c->bl_particle;
@@ -103,24 +103,26 @@ ocmc_status beamlet_args(ocmc_ctx* c, unsigned long long total, uint64_t seed, T
     a.bl_vals = c->d_bl_vals;
     a.bl_overflow = c->d_bl_over;
     int cap;
-    ctx_launch_shape(c, threads, blocks, &cap);
+    ctx_launch_shape(c, threads, blocks, &cap, nreg);
     ocmc_status st = ctx_ensure_stacks(c, (size_t)*blocks * (*threads / 32) * 2 * cap);
     if (st != OCMC_OK) return st;
     a.stacks = c->d_stacks;
     a.cap = cap;
     a.switch_high = c->p.switch_high ? c->p.switch_high : 128;
     a.switch_low = c->p.switch_low ? c->p.switch_low : 8;
+    a.refill_min = c->p.refill_min ? c->p.refill_min : 1;
     return OCMC_OK;
 }
 
 // Clears the tables, flags and counter, then launches the transport (all on stream s).
-cudaError_t enqueue_beamlets(ocmc_ctx* c, const TransportArgs& a, size_t slots, int threads, int blocks, cudaStream_t s)
+cudaError_t enqueue_beamlets(ocmc_ctx* c, const TransportArgs& a, size_t slots, int threads, int blocks, int nreg,
+                             cudaStream_t s)
 {
     cudaError_t e = cudaMemsetAsync(c->d_bl_keys, 0xFF, sizeof(unsigned int) * slots, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->d_bl_vals, 0, sizeof(unsigned long long) * slots, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->d_bl_over, 0, sizeof(unsigned int) * c->bl_n, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->d_counter, 0, sizeof(unsigned long long), s);
-    if (e == cudaSuccess) e = launch_transport(a, blocks, threads, transport_smem_bytes(threads), s);
+    if (e == cudaSuccess) e = launch_transport(a, blocks, threads, transport_smem_bytes(threads), s, nreg);
     return e;
 }
 
@@ -156,10 +158,10 @@ ocmc_status size_tables(ocmc_ctx* c, uint64_t seed, cudaStream_t s)
             ocmc_status st = upload_beamlets(c, cnt, caps, &total, &slots);
             if (st != OCMC_OK) return st;
             TransportArgs a;
-            int threads, blocks;
-            st = beamlet_args(c, total, seed ^ 0x5EEDF00Dull, a, &threads, &blocks);
+            int threads, blocks, nreg;
+            st = beamlet_args(c, total, seed ^ 0x5EEDF00Dull, a, &threads, &blocks, &nreg);
             if (st != OCMC_OK) return st;
-            BCK(enqueue_beamlets(c, a, slots, threads, blocks, s), "pilot launch");
+            BCK(enqueue_beamlets(c, a, slots, threads, blocks, nreg, s), "pilot launch");
             BCK(cudaStreamSynchronize(s), "pilot");
             std::vector<unsigned int> over;
             st = read_overflow(c, over);
@@ -201,14 +203,14 @@ ocmc_status capture_graph(ocmc_ctx* c, uint64_t seed)
     ocmc_status st = upload_beamlets(c, counts, c->bl_cap, &total, &slots);
     if (st != OCMC_OK) return st;
     TransportArgs a;
-    int threads, blocks;
-    st = beamlet_args(c, total, seed, a, &threads, &blocks);
+    int threads, blocks, nreg;
+    st = beamlet_args(c, total, seed, a, &threads, &blocks, &nreg);
     if (st != OCMC_OK) return st;
     if (!c->bl_capture) BCK(cudaStreamCreateWithFlags(&c->bl_capture, cudaStreamNonBlocking), "stream");
-    transport_max_blocks_per_sm(threads, transport_smem_bytes(threads));   // sets the kernel's smem attribute
+    transport_max_blocks_per_sm(threads, transport_smem_bytes(threads), nreg);   // sets the kernels' smem attribute
     cudaGraph_t g = nullptr;
     BCK(cudaStreamBeginCapture(c->bl_capture, cudaStreamCaptureModeRelaxed), "graph capture");
-    cudaError_t e = enqueue_beamlets(c, a, slots, threads, blocks, c->bl_capture);
+    cudaError_t e = enqueue_beamlets(c, a, slots, threads, blocks, nreg, c->bl_capture);
     cudaError_t e2 = cudaStreamEndCapture(c->bl_capture, &g);
     if (e != cudaSuccess || e2 != cudaSuccess) {
         if (g) cudaGraphDestroy(g);
@@ -363,16 +365,18 @@ ocmc_status ocmc_autotune(ocmc_ctx* c, uint64_t pilot, ocmc_params* chosen)
     if (!c) return ctx_fail(c, OCMC_ERR_ARG, "ctx is NULL");
     if (!c->have_phantom || !c->have_source) return ctx_fail(c, OCMC_ERR_STATE, "need a phantom and a source");
     if (pilot < 1) return ctx_fail(c, OCMC_ERR_ARG, "pilot_histories must be > 0");
-    const int threads_c[] = {128, 256, 512};
+    // (register cap, threads per block) pairs that fill an SM, x type-switch thresholds
+    const int shape_c[][2] = {{64, 512}, {80, 256}, {56, 384}, {64, 256}};
     const int high_c[] = {64, 128, 256};
     const int low_c[] = {8, 16};
     ocmc_params base = c->p, best = c->p;
     float best_ms = 3.0e38f;
-    for (int t : threads_c)
+    for (const auto& sh : shape_c)
         for (int hi : high_c)
             for (int lo : low_c) {
                 ocmc_params q = base;
-                q.block_threads = t;
+                q.max_registers = sh[0];
+                q.block_threads = sh[1];
                 q.blocks_per_sm = 0;
                 q.switch_high = hi;
                 q.switch_low = lo;

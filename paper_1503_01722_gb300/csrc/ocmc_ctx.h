@@ -79,7 +79,7 @@ ocmc_status ctx_fail(ocmc_ctx* c, ocmc_status s, const std::string& msg);
 ocmc_status ctx_cuda_fail(ocmc_ctx* c, cudaError_t e, const char* where);
 ocmc_status ctx_ensure_tables(ocmc_ctx* c, cudaStream_t s);
 void ctx_fill_args(const ocmc_ctx* c, TransportArgs& a);
-void ctx_launch_shape(const ocmc_ctx* c, int* threads, int* blocks, int* cap);
+void ctx_launch_shape(const ocmc_ctx* c, int* threads, int* blocks, int* cap, int* nreg);
 ocmc_status ctx_ensure_stacks(ocmc_ctx* c, size_t records);
 void stratify_bins(const float* edges, const float* weights, int n_bins, unsigned long long N, int* order,
                    unsigned long long* bound);

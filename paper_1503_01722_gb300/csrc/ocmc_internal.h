@@ -126,6 +126,7 @@ struct TransportArgs {
     PRec* stacks;               // per warp: 2 stacks of `cap` records
     int cap;
     int switch_high, switch_low;
+    int refill_min;                      // free lanes needed before a warp refills (>= 1)
     unsigned long long* hist_counter;
     unsigned long long* stats;  // ST_COUNT
     int* err;
@@ -143,9 +144,11 @@ struct TransportArgs {
 // kernels / launchers (defined in the .cu files)
 cudaError_t build_tables(const Tables& t, const PhysParams& pp, const float* density, const uint8_t* material,
                          long long nvox, int* d_err, cudaStream_t s);
-cudaError_t launch_transport(const TransportArgs& a, int blocks, int threads, size_t smem, cudaStream_t s);
+cudaError_t launch_transport(const TransportArgs& a, int blocks, int threads, size_t smem, cudaStream_t s,
+                             int nreg);
 size_t transport_smem_bytes(int threads);
-int transport_max_blocks_per_sm(int threads, size_t smem);
+int transport_max_blocks_per_sm(int threads, size_t smem, int nreg);
+bool transport_nreg_supported(int nreg);
 cudaError_t launch_finalize(const long long* tally, const float* density, int B, long long nvox, double voxel_volume,
                             const double* inv_nb, double inv_n, float* dose, float* sigma, cudaStream_t s);
 cudaError_t launch_test_philox(uint32_t key0, uint32_t key1, uint32_t c1, uint32_t c2, uint32_t c3,

@@ -117,7 +117,8 @@ extern "C" ocmc_status ocmc_run_noalloc(int device, int nx, int ny, int nz, cons
     if ((p.block_threads != 0 && (p.block_threads < 32 || p.block_threads > 1024 || p.block_threads % 32)) ||
         p.blocks_per_sm < 0 || p.blocks_per_sm > 32 ||
         (p.stack_capacity != 0 && (p.stack_capacity < 64 || p.stack_capacity > (1 << 20))) || p.switch_high < 0 ||
-        p.switch_low < 0 || p.switch_low > 32)
+        p.switch_low < 0 || p.switch_low > 32 || p.refill_min < 0 || p.refill_min > 32 ||
+        (p.max_registers != 0 && !transport_nreg_supported(p.max_registers)))
         return M.fail(OCMC_ERR_ARG, "invalid execution parameters");
     double W = 0.0;
     for (int i = 0; i < n_bins; ++i) {
@@ -160,7 +161,8 @@ extern "C" ocmc_status ocmc_run_noalloc(int device, int nx, int ny, int nz, cons
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
     size_t smem = transport_smem_bytes(threads);
-    int bps = p.blocks_per_sm ? p.blocks_per_sm : transport_max_blocks_per_sm(threads, smem);
+    const int nreg = p.max_registers ? p.max_registers : 80;
+    int bps = p.blocks_per_sm ? p.blocks_per_sm : transport_max_blocks_per_sm(threads, smem, nreg);
     if (bps < 1) bps = 1;
     size_t per_block = (size_t)(threads / 32) * 2 * cap * sizeof(PRec);
     size_t room = NOALLOC_BYTES - cv.used;
@@ -199,6 +201,7 @@ extern "C" ocmc_status ocmc_run_noalloc(int device, int nx, int ny, int nz, cons
     a.cap = cap;
     a.switch_high = p.switch_high ? p.switch_high : 128;
     a.switch_low = p.switch_low ? p.switch_low : 8;
+    a.refill_min = p.refill_min ? p.refill_min : 1;
     a.hist_counter = counter;
     a.stats = stats;
     a.err = err;
@@ -238,7 +241,7 @@ extern "C" ocmc_status ocmc_run_noalloc(int device, int nx, int ny, int nz, cons
     sd.bound[n_bins] = n_total;
     for (int i = 0; i < n_bins; ++i) { sd.lo[i] = edges[i]; sd.hi[i] = edges[i + 1]; }
 
-    e = launch_transport(a, (int)blocks, threads, smem, s);
+    e = launch_transport(a, (int)blocks, threads, smem, s, nreg);
     if (e != cudaSuccess) return M.cuda(e, "transport launch");
     int flag = 0;
     e = cudaMemcpyAsync(&flag, err, sizeof(int), cudaMemcpyDeviceToHost, s);

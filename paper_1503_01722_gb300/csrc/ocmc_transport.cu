@@ -405,8 +405,10 @@ __device__ __forceinline__ bool charged_step(C& c, Lane& p, unsigned& n_hfict)
     return true;
 }
 
-template <bool BL>
-__global__ void __maxnreg__(80) k_transport(const __grid_constant__ TransportArgs a)
+// NREG: register cap per thread. More registers spill less; fewer registers let more
+// warps share an SM (80: 3 x 256 threads, 64: 2 x 512, 56: 3 x 384 on GB300).
+template <bool BL, int NREG>
+__global__ void __maxnreg__(NREG) k_transport(const __grid_constant__ TransportArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_top[MAX_WARPS][2];
@@ -433,7 +435,9 @@ __global__ void __maxnreg__(80) k_transport(const __grid_constant__ TransportArg
         int top0 = min(c.top[0], a.cap), top1 = min(c.top[1], a.cap);
         unsigned act = __ballot_sync(FULL, active);
         int nfree = 32 - __popc(act);
-        if (nfree > 0) {
+        // refill when enough lanes are free: the refill code runs on the free lanes only,
+        // so waiting for several of them spreads its cost
+        if (nfree >= a.refill_min || nfree == 32) {
             int topm = mode ? top1 : top0;
             int rank = __popc(~act & lt);
             int take = min(nfree, topm);
@@ -532,27 +536,48 @@ __global__ void __maxnreg__(80) k_transport(const __grid_constant__ TransportArg
 
 size_t transport_smem_bytes(int /*threads*/) { return SMEM_TABLE_BYTES; }
 
-int transport_max_blocks_per_sm(int threads, size_t smem)
+namespace {
+template <bool BL, int R>
+cudaError_t launch_variant(const TransportArgs& a, int blocks, int threads, size_t smem, cudaStream_t s)
 {
-    cudaFuncSetAttribute(k_transport<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaFuncSetAttribute(k_transport<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_transport<false>, threads, smem) != cudaSuccess) return 0;
-    return n;
+    cudaError_t e = cudaFuncSetAttribute(k_transport<BL, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_transport<BL, R><<<blocks, threads, smem, s>>>(a);
+    return cudaGetLastError();
 }
 
-cudaError_t launch_transport(const TransportArgs& a, int blocks, int threads, size_t smem, cudaStream_t s)
+template <bool BL, int R>
+int occupancy(int threads, size_t smem)
+{
+    cudaFuncSetAttribute(k_transport<BL, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_transport<BL, R>, threads, smem) != cudaSuccess) return 0;
+    return n;
+}
+}  // namespace
+
+bool transport_nreg_supported(int nreg) { return nreg == 56 || nreg == 64 || nreg == 80; }
+
+int transport_max_blocks_per_sm(int threads, size_t smem, int nreg)
+{
+    occupancy<true, 56>(threads, smem);   // sets the shared-memory attribute of every variant
+    occupancy<true, 64>(threads, smem);
+    occupancy<true, 80>(threads, smem);
+    if (nreg == 56) return occupancy<false, 56>(threads, smem);
+    if (nreg == 64) return occupancy<false, 64>(threads, smem);
+    return occupancy<false, 80>(threads, smem);
+}
+
+cudaError_t launch_transport(const TransportArgs& a, int blocks, int threads, size_t smem, cudaStream_t s, int nreg)
 {
     if (a.beamlets) {
-        cudaError_t e = cudaFuncSetAttribute(k_transport<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        k_transport<true><<<blocks, threads, smem, s>>>(a);
-    } else {
-        cudaError_t e = cudaFuncSetAttribute(k_transport<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        k_transport<false><<<blocks, threads, smem, s>>>(a);
+        if (nreg == 56) return launch_variant<true, 56>(a, blocks, threads, smem, s);
+        if (nreg == 64) return launch_variant<true, 64>(a, blocks, threads, smem, s);
+        return launch_variant<true, 80>(a, blocks, threads, smem, s);
     }
-    return cudaGetLastError();
+    if (nreg == 56) return launch_variant<false, 56>(a, blocks, threads, smem, s);
+    if (nreg == 64) return launch_variant<false, 64>(a, blocks, threads, smem, s);
+    return launch_variant<false, 80>(a, blocks, threads, smem, s);
 }
 
 }  // namespace ocmc
