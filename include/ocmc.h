@@ -78,7 +78,7 @@ typedef struct {
                             /* the run repeated, so any value gives the same dose  */
     int32_t refill_min;     /* free lanes a warp waits for before refilling (0=1)  */
     int32_t max_registers;  /* register cap of the transport kernel: 56, 64 or 80; */
-                            /* 0 = 64 (with 512-thread blocks)                     */
+                            /* 0 = 64 (with 1024-thread blocks)                    */
 } ocmc_params;
 
 /* Run statistics accumulated since the last ocmc_reset_tally(). */

@@ -19,7 +19,10 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include"), "-I", CSRC]
 # FP32 transport code: approximate division/sqrt and flush-to-zero (deterministic for a given
 # binary; the physics tables are built in FP64 in ocmc_tables.cu, which keeps IEEE semantics)
-FAST = ["-ftz=true", "-prec-div=false", "-prec-sqrt=false"]
+# ptxas may fuse a multiply and an add into an FMA differently for different register caps;
+# -fmad=false for ptxas keeps the front end's explicit FMAs only, so every compiled variant of
+# the transport kernel performs the same arithmetic (bit-identical tallies across launch shapes)
+FAST = ["-ftz=true", "-prec-div=false", "-prec-sqrt=false", "-Xptxas", "-fmad=false"]
 FAST_FILES = {"ocmc_transport.cu", "ocmc_aux.cu", "ocmc_noalloc.cu"}
 
 

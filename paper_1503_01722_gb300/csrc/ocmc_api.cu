@@ -171,7 +171,7 @@ ocmc_status ensure_tally(ocmc_ctx* c)
 void launch_shape(const ocmc_ctx* c, int* threads, int* blocks, int* cap, int* nreg)
 {
     *nreg = c->p.max_registers ? c->p.max_registers : 64;
-    *threads = c->p.block_threads ? c->p.block_threads : (*nreg == 64 ? 512 : *nreg == 56 ? 384 : 256);
+    *threads = c->p.block_threads ? c->p.block_threads : (*nreg == 64 ? 1024 : *nreg == 56 ? 384 : 256);
     size_t smem = transport_smem_bytes(*threads);
     int bps = c->p.blocks_per_sm ? c->p.blocks_per_sm : transport_max_blocks_per_sm(*threads, smem, *nreg);
     if (bps < 1) bps = 1;
@@ -432,7 +432,7 @@ ocmc_status ocmc_run_range(ocmc_ctx* c, uint64_t first, uint64_t count, uint64_t
     a.key1 = (uint32_t)(seed >> 32);
     a.stacks = c->d_stacks;
     a.cap = cap;
-    a.switch_high = c->p.switch_high ? c->p.switch_high : 128;
+    a.switch_high = c->p.switch_high ? c->p.switch_high : 256;
     a.switch_low = c->p.switch_low ? c->p.switch_low : 8;
     a.refill_min = c->p.refill_min ? c->p.refill_min : 1;
     CK(cudaMemsetAsync(c->d_counter, 0, sizeof(unsigned long long), s), "counter reset");

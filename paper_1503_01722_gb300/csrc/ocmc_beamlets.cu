@@ -108,7 +108,7 @@ ocmc_status beamlet_args(ocmc_ctx* c, unsigned long long total, uint64_t seed, T
     if (st != OCMC_OK) return st;
     a.stacks = c->d_stacks;
     a.cap = cap;
-    a.switch_high = c->p.switch_high ? c->p.switch_high : 128;
+    a.switch_high = c->p.switch_high ? c->p.switch_high : 256;
     a.switch_low = c->p.switch_low ? c->p.switch_low : 8;
     a.refill_min = c->p.refill_min ? c->p.refill_min : 1;
     return OCMC_OK;
@@ -366,8 +366,8 @@ ocmc_status ocmc_autotune(ocmc_ctx* c, uint64_t pilot, ocmc_params* chosen)
     if (!c->have_phantom || !c->have_source) return ctx_fail(c, OCMC_ERR_STATE, "need a phantom and a source");
     if (pilot < 1) return ctx_fail(c, OCMC_ERR_ARG, "pilot_histories must be > 0");
     // (register cap, threads per block) pairs that fill an SM, x type-switch thresholds
-    const int shape_c[][2] = {{64, 512}, {80, 256}, {56, 384}, {64, 256}};
-    const int high_c[] = {64, 128, 256};
+    const int shape_c[][2] = {{64, 1024}, {64, 512}, {80, 256}, {56, 384}};
+    const int high_c[] = {128, 256, 512};
     const int low_c[] = {8, 16};
     ocmc_params base = c->p, best = c->p;
     float best_ms = 3.0e38f;

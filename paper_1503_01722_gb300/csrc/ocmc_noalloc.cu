@@ -199,7 +199,7 @@ extern "C" ocmc_status ocmc_run_noalloc(int device, int nx, int ny, int nz, cons
     a.tally = reinterpret_cast<unsigned long long*>(tally_dev);
     a.stacks = stacks;
     a.cap = cap;
-    a.switch_high = p.switch_high ? p.switch_high : 128;
+    a.switch_high = p.switch_high ? p.switch_high : 256;
     a.switch_low = p.switch_low ? p.switch_low : 8;
     a.refill_min = p.refill_min ? p.refill_min : 1;
     a.hist_counter = counter;
