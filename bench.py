@@ -31,8 +31,9 @@ import ocmc_inputs as I  # noqa: E402
 # smsp__thread_inst_executed.sum divided by the kernel's own lane-step counter)
 # and DRAM bytes per history, from the ncu capture summarised in
 # profiles/k_transport_photon_slab_120.md (re-measured whenever the kernel changes).
-INST_PER_LANE_STEP = 732.4
-DRAM_BYTES_PER_HISTORY = None
+INST_PER_LANE_STEP = 649.3
+# DRAM bytes of one transport launch measured by ncu on the full default workload
+DRAM_BYTES_PER_LAUNCH = {("photon_slab_120", 100_000_000): 21.547e9}
 
 WORKLOADS = {
     "photon_slab_120": (I.photon_slab_120, 100_000_000,
@@ -352,10 +353,10 @@ def main():
         "achieved": achieved, "peak": peak, "unit": "Tinst/s",
         "frac": None if achieved is None else achieved / peak,
         "peak_basis": f"152 SMs x 128 lanes x median SM clock under load ({sm_mhz:.0f} MHz)",
-        "traffic": None if DRAM_BYTES_PER_HISTORY is None else DRAM_BYTES_PER_HISTORY * n,
+        "traffic": DRAM_BYTES_PER_LAUNCH.get((args.workload, n)),
         "kernel_ms": kern, "lane_steps_per_launch": ls,
-        "hbm_gbs_achieved_if_traffic": None if DRAM_BYTES_PER_HISTORY is None else
-        DRAM_BYTES_PER_HISTORY * n / (kern / 1e3) / 1e9,
+        "hbm_gbs_from_traffic": None if (args.workload, n) not in DRAM_BYTES_PER_LAUNCH else
+        DRAM_BYTES_PER_LAUNCH[(args.workload, n)] / (kern / 1e3) / 1e9,
         "hbm_peak_gbs_measured": peaks.get("hbm_gbs"),
     }
     line = {
