@@ -46,6 +46,18 @@ WORKLOADS = {
                              "6 MV photon beam, 10x10 at SSD 100, half-slab phantom 120^3 at 0.25 cm"),
     "electron_half_slab_120": (I.electron_half_slab_120, 10_000_000,
                                "15 MeV electron beam, 10x10 at SSD 100, half-slab phantom 120^3 at 0.25 cm"),
+    # the paper's own setups (Tables 2-3): 2x2 cm2 at SSD 100, 32 cm cube at 0.25 cm, cutoffs
+    # e 200 keV / gamma 50 keV, hard-event thresholds 200 keV / 50 keV
+    "paper_electron_water": (lambda: I.paper_preset(1, "water"), 5_000_000,
+                             "paper preset: 15 MeV e-, 2x2 cm2 at SSD 100, water 128^3 at 0.25 cm"),
+    "paper_electron_slab": (lambda: I.paper_preset(1, "slab"), 5_000_000,
+                            "paper preset: 15 MeV e-, 2x2 cm2 at SSD 100, slab 128^3 at 0.25 cm"),
+    "paper_photon_water": (lambda: I.paper_preset(0, "water"), 500_000_000,
+                           "paper preset: 6 MV, 2x2 cm2 at SSD 100, water 128^3 at 0.25 cm"),
+    "paper_photon_slab": (lambda: I.paper_preset(0, "slab"), 500_000_000,
+                          "paper preset: 6 MV, 2x2 cm2 at SSD 100, slab 128^3 at 0.25 cm"),
+    "paper_photon_half_slab": (lambda: I.paper_preset(0, "half"), 500_000_000,
+                               "paper preset: 6 MV, 2x2 cm2 at SSD 100, half-slab 128^3 at 0.25 cm"),
     "beamlets_ct": (I.beamlets_ct, 0,
                     "512 6 MV pencil beamlets 0.5x0.5 cm2 at random gantry angles (SAD 100 cm), histories "
                     "10^N(5,0.5) clipped to [1e4,1e6], CT-like phantom 256x256x128 at 0.2 cm, one graph-captured "
@@ -253,12 +265,15 @@ def main():
     from paper_1503_01722_gb300 import sharding
 
     torch.cuda.set_device(local)
+    params = {}
+    if args.workload.startswith("paper_"):
+        params = dict(e_abs_e=0.2, e_abs_g=0.05, w_cc=0.2, w_cb=0.05)
     dist = None
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
     n = args.histories or n_default
-    eng = ocmc.Engine(local)
+    eng = ocmc.Engine(local, **params)
     eng.create_phantom(ph)
     eng.set_source(beam)
     shape = ph.density.shape
@@ -317,7 +332,7 @@ def main():
         mat_h = torch.from_numpy(np.ascontiguousarray(ph.material)).pin_memory()
         dose_h = torch.empty(shape, dtype=torch.float32).pin_memory()
         sig_h = torch.empty(shape, dtype=torch.float32).pin_memory()
-        e2e_eng = ocmc.Engine(local)
+        e2e_eng = ocmc.Engine(local, **params)
         e2e_ms = []
         for k in range(args.warmup + args.steps):
             torch.cuda.synchronize()

@@ -163,6 +163,26 @@ def electron_half_slab_120():
     return ph, beam_on(ph, 1, mono(15.0), (10.0, 10.0), ssd=100.0)
 
 
+def paper_phantom(kind="water"):
+    """Phantoms of the paper's experiments (Sec. 2.2 "Materials"): 32x32x32 cm^3 at 0.25 cm
+    (128^3); slab: water, bone and lung layers of 2 cm each along z (0-2, 2-4, 4-6 cm),
+    then water; half-slab: the bone and lung layers cover half of the x-y plane."""
+    n, v = (128, 128, 128), (0.25, 0.25, 0.25)
+    if kind == "water":
+        return homogeneous(n, v)
+    if kind == "slab":
+        return _layered(n, v, ((2.0, 4.0, BONE), (4.0, 6.0, LUNG)))
+    return _layered(n, v, ((2.0, 4.0, BONE), (4.0, 6.0, LUNG)), half=True)
+
+
+def paper_preset(particle, kind="water"):
+    """The paper's beams: 2x2 cm^2 at the surface, point source at SSD 100 cm,
+    15 MeV electrons or the 6 MV spectrum."""
+    ph = paper_phantom(kind)
+    spec = mono(15.0) if particle == 1 else spectrum_6mv()
+    return ph, beam_on(ph, particle, spec, (2.0, 2.0), 100.0)
+
+
 def scaled(ph: Phantom, factor):
     """Coarsen a phantom by an integer factor (nearest sample) for oracle-sized cases."""
     f = int(factor)
