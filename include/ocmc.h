@@ -233,6 +233,45 @@ ocmc_status ocmc_get_beamlet_dose(ocmc_ctx* ctx, int beamlet, int32_t* idx_host,
  * *chosen if not NULL). Resets the tally. The dose does not depend on the choice. */
 ocmc_status ocmc_autotune(ocmc_ctx* ctx, uint64_t pilot_histories, ocmc_params* chosen);
 
+/* ---- learned dose denoiser ----------------------------------------------------
+ * The paper has no learned component; this is a systems extension. A 3D U-Net
+ * (4 levels, 16/32/64/128 channels, 3x3x3 convolutions with ReLU, 2x2x2 stride-2
+ * down and transposed-up convolutions, concatenated skips, 1x1x1 head adding a
+ * correction to the normalised input) maps a low-history dose plus density to a
+ * converged dose. BF16 activations and weights, FP32 accumulation on the tensor
+ * cores, FP32 master weights trained with Adam. Grid sizes must be multiples of 8
+ * (at most 512). Dose arrays are nx*ny*nz floats on the network's device. */
+typedef struct ocmc_unet ocmc_unet;
+
+/* Create a network with He-normal initial weights drawn from Philox(seed). */
+ocmc_status ocmc_unet_create(ocmc_unet** out, int device, int nx, int ny, int nz, uint64_t seed);
+void ocmc_unet_destroy(ocmc_unet* net);
+const char* ocmc_unet_last_error(ocmc_unet* net);
+/* Number of FP32 parameters; get/set all of them (grads = 1: the last gradients). */
+ocmc_status ocmc_unet_num_params(ocmc_unet* net, int64_t* n);
+ocmc_status ocmc_unet_get_params(ocmc_unet* net, float* host, int grads);
+ocmc_status ocmc_unet_set_params(ocmc_unet* net, const float* host);
+/* Denoised dose (same units as dose_dev) from (dose_dev, density_dev), device arrays. */
+ocmc_status ocmc_unet_forward(ocmc_unet* net, const float* dose_dev, const float* density_dev, float* out_dev,
+                              void* cuda_stream);
+/* One Adam step (learning rate lr; lr <= 0: gradients only) on the mean squared error
+ * between output and target_dev / s over voxels with density >= 0.1 g/cm^3, s the
+ * maximum of dose_dev. *loss_host (may be NULL) receives the loss (synchronises). */
+ocmc_status ocmc_unet_train_step(ocmc_unet* net, const float* dose_dev, const float* density_dev,
+                                 const float* target_dev, float lr, float* loss_host, void* cuda_stream);
+/* One layer through the network's own kernels (for the gradient tests): mode 0 3x3x3
+ * convolution, 1 2x2x2 stride-2 convolution, 2 its transposed form; (nx,ny,nz) is the
+ * fine grid; x, dy, y, dx channels-last FP32 host arrays (inputs rounded to BF16);
+ * w [taps][cin][cout]; y = layer(x) without bias or ReLU; dx, dw the gradients for dy. */
+ocmc_status ocmc_unet_test_layer(int device, int mode, int nx, int ny, int nz, int cin, int cout,
+                                 const float* x_host, const float* w_host, const float* dy_host, float* y_host,
+                                 float* dx_host, float* dw_host);
+/* Denoise the context's current dose with the network; where the denoised value
+ * differs from the plain Monte Carlo value by more than k_sigma of its batch sigma
+ * the plain value is kept and flag_out (may be NULL) is 1. */
+ocmc_status ocmc_denoise(ocmc_ctx* ctx, ocmc_unet* net, float k_sigma, float* dose_out, float* flag_out,
+                         int on_device);
+
 /* ---- test access to the engine's building blocks ---------------------------
  * These run the same device functions the transport kernel uses, so the
  * tests can compare each building block with the CPU oracle. */

@@ -1,0 +1,377 @@
+// ocmc_unet_kernels.cuh -- tensor-core kernels of the 3D U-Net dose denoiser.
+//
+// Activations are BF16, channels-last (NDHWC with x fastest among voxels), stored
+// with a per-voxel channel stride so that convolutions read and write channel
+// slices (the U-Net's concatenations need no copies). Weights are BF16 copies of
+// FP32 master weights, laid out [tap][in channel][out channel]. Every product runs
+// on the tensor cores (mma.sync m16n8k16, BF16 inputs, FP32 accumulation).
+//
+// One implicit-GEMM kernel covers the forward pass and the data gradients of all
+// layer kinds: each output row (voxel) gathers its input voxels per tap:
+//   CONV3 : 3x3x3, stride 1, zero padding 1      (27 taps, src = v + d - 1)
+//   DOWN  : 2x2x2, stride 2 (fine -> coarse)      (8 taps,  src = 2v + d)
+//   UP    : 2x2x2 transposed, stride 2 (coarse -> fine), one launch per output parity:
+//           row = coarse voxel u, out voxel = 2u + p, single tap p.
+// Data gradients use the same kernel with transposed (and, for CONV3, flipped)
+// weights: dgrad(CONV3) = CONV3, dgrad(DOWN) = UP, dgrad(UP) = DOWN.
+// The weight gradient is a second kernel: dW[tap][c][n] = sum over rows of
+// in[src(row, tap)][c] * dy[row][n], split over row chunks into FP32 partials that
+// a third kernel sums in a fixed order (deterministic).
+#pragma once
+#include <cstdint>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+namespace ocmc {
+namespace unet {
+
+enum Mode { CONV3 = 0, DOWN = 1, UP = 2 };
+
+struct Grid3 {
+    int nx, ny, nz;
+    __host__ __device__ long long n() const { return (long long)nx * ny * nz; }
+};
+
+// Channel slice of an activation buffer: element (v, c) at ptr[v * stride + c0 + c].
+struct Slice {
+    __nv_bfloat16* ptr;
+    int stride, c0;
+};
+
+struct ConvArgs {
+    Mode mode;
+    Grid3 gin, gout;             // input and output grids (output = rows, except UP: rows = input grid)
+    Slice in, out;
+    int cin, cout;               // channels read / written
+    const __nv_bfloat16* w;      // [taps][cin][cout]
+    const float* bias;           // [cout] or null
+    int relu;                    // apply max(0, .) to the result
+    int accumulate;              // out = out + result
+    const __nv_bfloat16* mask;   // multiply by (mask(v, c) > 0), mask is a Slice-like buffer
+    int mask_stride, mask_c0;
+    int parity;                  // UP mode: output parity 0..7
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem, bool valid)
+{
+    uint32_t s = smem_u32(smem);
+    int sz = valid ? 16 : 0;                    // 0 source bytes: the 16 destination bytes are zero-filled
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem), "r"(sz));
+}
+
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::); }
+
+__device__ __forceinline__ void ldsm_x4(uint32_t& r0, uint32_t& r1, uint32_t& r2, uint32_t& r3, const void* p)
+{
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(smem_u32(p)));
+}
+
+__device__ __forceinline__ void ldsm_x4_t(uint32_t& r0, uint32_t& r1, uint32_t& r2, uint32_t& r3, const void* p)
+{
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(smem_u32(p)));
+}
+
+__device__ __forceinline__ void ldsm_x2_t(uint32_t& r0, uint32_t& r1, const void* p)
+{
+    asm volatile("ldmatrix.sync.aligned.m8n8.x2.trans.shared.b16 {%0,%1}, [%2];\n"
+                 : "=r"(r0), "=r"(r1)
+                 : "r"(smem_u32(p)));
+}
+
+// D = A (16x16, row) * B (16x8, col) + D, BF16 in, FP32 accumulate
+__device__ __forceinline__ void mma_bf16(float* d, uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3, uint32_t b0,
+                                         uint32_t b1)
+{
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ int num_taps(Mode m) { return m == CONV3 ? 27 : (m == DOWN ? 8 : 1); }
+
+// Input voxel of output row r for tap t (-1: zero padding). For UP the row is the
+// coarse voxel itself.
+__device__ __forceinline__ long long src_voxel(const ConvArgs& a, long long r, int t)
+{
+    if (a.mode == UP) return r;
+    const Grid3& go = a.gout;
+    int x = (int)(r % go.nx);
+    long long q = r / go.nx;
+    int y = (int)(q % go.ny);
+    int z = (int)(q / go.ny);
+    int sx, sy, sz;
+    if (a.mode == CONV3) {
+        sx = x + (t % 3) - 1;
+        sy = y + (t / 3) % 3 - 1;
+        sz = z + t / 9 - 1;
+    } else {
+        sx = 2 * x + (t & 1);
+        sy = 2 * y + ((t >> 1) & 1);
+        sz = 2 * z + (t >> 2);
+    }
+    const Grid3& gi = a.gin;
+    if (sx < 0 || sy < 0 || sz < 0 || sx >= gi.nx || sy >= gi.ny || sz >= gi.nz) return -1;
+    return sx + (long long)gi.nx * (sy + (long long)gi.ny * sz);
+}
+
+// Output voxel of row r.
+__device__ __forceinline__ long long dst_voxel(const ConvArgs& a, long long r)
+{
+    if (a.mode != UP) return r;
+    const Grid3& gi = a.gin;   // coarse
+    int x = (int)(r % gi.nx);
+    long long q = r / gi.nx;
+    int y = (int)(q % gi.ny);
+    int z = (int)(q / gi.ny);
+    int p = a.parity;
+    int ox = 2 * x + (p & 1), oy = 2 * y + ((p >> 1) & 1), oz = 2 * z + (p >> 2);
+    const Grid3& go = a.gout;
+    if (ox >= go.nx || oy >= go.ny || oz >= go.nz) return -1;
+    return ox + (long long)go.nx * (oy + (long long)go.ny * oz);
+}
+
+constexpr int BM = 128;        // rows per block
+constexpr int THREADS = 256;   // 8 warps, 16 rows each
+
+// Implicit-GEMM convolution. BK: input channels per K chunk (16 or 32); BN: output
+// channels per block (16, 32, 64 or 128; gridDim.y covers cout / BN).
+template <int BK, int BN>
+__global__ void __launch_bounds__(THREADS) k_conv(const ConvArgs a)
+{
+    constexpr int AST = BK + 8;        // smem row strides (bf16), +16 B against bank conflicts
+    constexpr int BST = BN + 8;
+    __shared__ __align__(16) __nv_bfloat16 sA[2][BM * AST];
+    __shared__ __align__(16) __nv_bfloat16 sB[2][BK * BST];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const long long rows = a.mode == UP ? a.gin.n() : a.gout.n();
+    const long long r0 = (long long)blockIdx.x * BM;
+    const int n0 = blockIdx.y * BN;
+    const int T = num_taps(a.mode);
+    const int KC = a.cin / BK;                    // chunks per tap
+    const int steps = T * KC;
+
+    auto load = [&](int step, int buf) {
+        const int t = a.mode == UP ? a.parity : step / KC;
+        const int wt = a.mode == UP ? 0 : t;     // UP passes the parity's weights as a 1-tap tensor
+        const int c0 = (step % KC) * BK;
+        constexpr int CH_A = BK / 8;             // 16-byte chunks per A row
+        for (int i = tid; i < BM * CH_A; i += THREADS) {
+            int r = i / CH_A, ch = i % CH_A;
+            long long row = r0 + r;
+            long long s = row < rows ? src_voxel(a, row, t) : -1;
+            const __nv_bfloat16* g = a.in.ptr + (s >= 0 ? s : 0) * a.in.stride + a.in.c0 + c0 + ch * 8;
+            cp_async16(&sA[buf][r * AST + ch * 8], g, s >= 0);
+        }
+        constexpr int CH_B = BN / 8;
+        for (int i = tid; i < BK * CH_B; i += THREADS) {
+            int k = i / CH_B, ch = i % CH_B;
+            const __nv_bfloat16* g = a.w + ((long long)wt * a.cin + c0 + k) * a.cout + n0 + ch * 8;
+            cp_async16(&sB[buf][k * BST + ch * 8], g, true);
+        }
+        cp_async_commit();
+    };
+
+    float acc[BN / 8][4];
+#pragma unroll
+    for (int j = 0; j < BN / 8; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
+
+    load(0, 0);
+    for (int s = 0; s < steps; ++s) {
+        const int buf = s & 1;
+        cp_async_wait_all();
+        __syncthreads();
+        if (s + 1 < steps) load(s + 1, buf ^ 1);
+#pragma unroll
+        for (int kk = 0; kk < BK; kk += 16) {
+            uint32_t a0, a1, a2, a3;
+            {
+                int row = warp * 16 + (lane & 7) + 8 * ((lane >> 3) & 1);
+                int col = kk + 8 * (lane >> 4);
+                ldsm_x4(a0, a1, a2, a3, &sA[buf][row * AST + col]);
+            }
+#pragma unroll
+            for (int j = 0; j < BN / 8; j += 2) {
+                if (j + 1 < BN / 8) {
+                    uint32_t b0, b1, b2, b3;
+                    int k = kk + (lane & 7) + 8 * ((lane >> 3) & 1);
+                    int n = j * 8 + 8 * (lane >> 4);
+                    ldsm_x4_t(b0, b1, b2, b3, &sB[buf][k * BST + n]);
+                    mma_bf16(acc[j], a0, a1, a2, a3, b0, b1);
+                    mma_bf16(acc[j + 1], a0, a1, a2, a3, b2, b3);
+                } else {
+                    uint32_t b0, b1;
+                    int k = kk + (lane & 7) + 8 * ((lane >> 3) & 1);
+                    ldsm_x2_t(b0, b1, &sB[buf][k * BST + j * 8]);
+                    mma_bf16(acc[j], a0, a1, a2, a3, b0, b1);
+                }
+            }
+        }
+    }
+    // epilogue: rows g and g+8 of the warp's 16, columns 2t, 2t+1 of each n-tile
+    const int g = lane >> 2, t4 = lane & 3;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        long long row = r0 + warp * 16 + g + 8 * h;
+        if (row >= rows) continue;
+        long long v = dst_voxel(a, row);
+        if (v < 0) continue;
+#pragma unroll
+        for (int j = 0; j < BN / 8; ++j) {
+            int n = n0 + j * 8 + 2 * t4;
+            float x0 = acc[j][2 * h], x1 = acc[j][2 * h + 1];
+            if (a.bias) { x0 += a.bias[n]; x1 += a.bias[n + 1]; }
+            __nv_bfloat162* o = reinterpret_cast<__nv_bfloat162*>(a.out.ptr + v * a.out.stride + a.out.c0 + n);
+            if (a.accumulate) {
+                float2 old = __bfloat1622float2(*o);
+                x0 += old.x;
+                x1 += old.y;
+            }
+            if (a.relu) { x0 = fmaxf(x0, 0.f); x1 = fmaxf(x1, 0.f); }
+            if (a.mask) {
+                __nv_bfloat162 mk = *reinterpret_cast<const __nv_bfloat162*>(a.mask + v * a.mask_stride + a.mask_c0 + n);
+                float2 m = __bfloat1622float2(mk);
+                if (!(m.x > 0.f)) x0 = 0.f;
+                if (!(m.y > 0.f)) x1 = 0.f;
+            }
+            *o = __floats2bfloat162_rn(x0, x1);
+        }
+    }
+}
+
+struct WgradArgs {
+    Mode mode;
+    Grid3 gin, gout;
+    Slice in;                    // layer input x
+    Slice dy;                    // gradient of the layer output (rows = output voxels; UP: fine grid)
+    int cin, cout;
+    long long rows_per_chunk;
+    float* partial;              // [chunks][taps][cin][cout]
+};
+
+// Row r's input voxel for the weight gradient: for UP the rows are output (fine)
+// voxels whose single source is their coarse parent, and the tap is their parity.
+__device__ __forceinline__ long long wsrc(const WgradArgs& a, long long r, int t)
+{
+    const Grid3& go = a.gout;
+    int x = (int)(r % go.nx);
+    long long q = r / go.nx;
+    int y = (int)(q % go.ny);
+    int z = (int)(q / go.ny);
+    int sx, sy, sz;
+    if (a.mode == CONV3) {
+        sx = x + (t % 3) - 1; sy = y + (t / 3) % 3 - 1; sz = z + t / 9 - 1;
+    } else if (a.mode == DOWN) {
+        sx = 2 * x + (t & 1); sy = 2 * y + ((t >> 1) & 1); sz = 2 * z + (t >> 2);
+    } else {
+        int p = (x & 1) | ((y & 1) << 1) | ((z & 1) << 2);
+        if (p != t) return -1;
+        sx = x >> 1; sy = y >> 1; sz = z >> 1;
+    }
+    const Grid3& gi = a.gin;
+    if (sx < 0 || sy < 0 || sz < 0 || sx >= gi.nx || sy >= gi.ny || sz >= gi.nz) return -1;
+    return sx + (long long)gi.nx * (sy + (long long)gi.ny * sz);
+}
+
+// Weight-gradient partials: block (chunk, tap) computes the [BC x BN] tile
+// sum_{rows in chunk} x[src(row, tap)][c] * dy[row][n]; rows are the GEMM's K.
+// gridDim.z covers (cin / BC) x (cout / BN) tiles.
+template <int BC, int BN>
+__global__ void __launch_bounds__(THREADS) k_wgrad(const WgradArgs a)
+{
+    constexpr int KR = 32;                 // rows per K step
+    constexpr int XST = BC + 8, YST = BN + 8;
+    __shared__ __align__(16) __nv_bfloat16 sX[2][KR * XST];
+    __shared__ __align__(16) __nv_bfloat16 sY[2][KR * YST];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int t = blockIdx.y;
+    const int tiles_n = a.cout / BN;
+    const int c0 = (blockIdx.z / tiles_n) * BC, n0 = (blockIdx.z % tiles_n) * BN;
+    const long long rows = a.gout.n();
+    const long long rb = (long long)blockIdx.x * a.rows_per_chunk;
+    const long long re = rb + a.rows_per_chunk < rows ? rb + a.rows_per_chunk : rows;
+    const int steps = (int)((re - rb + KR - 1) / KR);
+    constexpr int MT = BC / 16, NT = BN / 8, TILES = MT * NT;
+    constexpr int PER_WARP = (TILES + 7) / 8;
+    float acc[PER_WARP][4];
+#pragma unroll
+    for (int i = 0; i < PER_WARP; ++i) acc[i][0] = acc[i][1] = acc[i][2] = acc[i][3] = 0.f;
+
+    auto load = [&](int s, int buf) {
+        long long base = rb + (long long)s * KR;
+        for (int i = tid; i < KR * (BC / 8); i += THREADS) {
+            int r = i / (BC / 8), ch = i % (BC / 8);
+            long long row = base + r;
+            long long sv = row < re ? wsrc(a, row, t) : -1;
+            const __nv_bfloat16* g = a.in.ptr + (sv >= 0 ? sv : 0) * a.in.stride + a.in.c0 + c0 + ch * 8;
+            cp_async16(&sX[buf][r * XST + ch * 8], g, sv >= 0);
+        }
+        for (int i = tid; i < KR * (BN / 8); i += THREADS) {
+            int r = i / (BN / 8), ch = i % (BN / 8);
+            long long row = base + r;
+            bool ok = row < re;
+            const __nv_bfloat16* g = a.dy.ptr + (ok ? row : 0) * a.dy.stride + a.dy.c0 + n0 + ch * 8;
+            cp_async16(&sY[buf][r * YST + ch * 8], g, ok);
+        }
+        cp_async_commit();
+    };
+
+    if (steps > 0) load(0, 0);
+    for (int s = 0; s < steps; ++s) {
+        const int buf = s & 1;
+        cp_async_wait_all();
+        __syncthreads();
+        if (s + 1 < steps) load(s + 1, buf ^ 1);
+#pragma unroll
+        for (int kk = 0; kk < KR; kk += 16) {
+#pragma unroll
+            for (int i = 0; i < PER_WARP; ++i) {
+                int tile = warp + 8 * i;
+                if (tile >= TILES) break;
+                int mt = tile / NT, nt = tile % NT;
+                // A (M = channel, K = row) from sX[row][c]: transposed 8x8 loads
+                uint32_t a0, a1, a2, a3;
+                {
+                    int j = lane >> 3;
+                    int row = kk + (lane & 7) + 8 * (j >> 1);
+                    int col = mt * 16 + 8 * (j & 1);
+                    ldsm_x4_t(a0, a1, a2, a3, &sX[buf][row * XST + col]);
+                }
+                uint32_t b0, b1;
+                {
+                    int row = kk + (lane & 7) + 8 * ((lane >> 3) & 1);
+                    ldsm_x2_t(b0, b1, &sY[buf][row * YST + nt * 8]);
+                }
+                mma_bf16(acc[i], a0, a1, a2, a3, b0, b1);
+            }
+        }
+    }
+    const int g = lane >> 2, t4 = lane & 3;
+    const int taps = a.mode == CONV3 ? 27 : 8;
+    float* P = a.partial + ((long long)blockIdx.x * taps + t) * a.cin * a.cout;
+#pragma unroll
+    for (int i = 0; i < PER_WARP; ++i) {
+        int tile = warp + 8 * i;
+        if (tile >= TILES) break;
+        int mt = tile / NT, nt = tile % NT;
+        int c = c0 + mt * 16 + g, n = n0 + nt * 8 + 2 * t4;
+        P[(long long)c * a.cout + n] = acc[i][0];
+        P[(long long)c * a.cout + n + 1] = acc[i][1];
+        P[(long long)(c + 8) * a.cout + n] = acc[i][2];
+        P[(long long)(c + 8) * a.cout + n + 1] = acc[i][3];
+    }
+}
+
+}  // namespace unet
+}  // namespace ocmc

@@ -80,6 +80,17 @@ def _load():
         "ocmc_run_beamlets": (C.c_int, [P, C.c_uint64, P]),
         "ocmc_get_beamlet_dose": (C.c_int, [P, C.c_int, P, P, P, C.c_int64, C.POINTER(C.c_int64)]),
         "ocmc_autotune": (C.c_int, [P, C.c_uint64, C.POINTER(Params)]),
+        "ocmc_unet_create": (C.c_int, [C.POINTER(P), C.c_int, C.c_int, C.c_int, C.c_int, C.c_uint64]),
+        "ocmc_unet_destroy": (None, [P]),
+        "ocmc_unet_last_error": (C.c_char_p, [P]),
+        "ocmc_unet_num_params": (C.c_int, [P, C.POINTER(C.c_int64)]),
+        "ocmc_unet_get_params": (C.c_int, [P, P, C.c_int]),
+        "ocmc_unet_set_params": (C.c_int, [P, P]),
+        "ocmc_unet_forward": (C.c_int, [P, P, P, P, P]),
+        "ocmc_unet_train_step": (C.c_int, [P, P, P, P, C.c_float, C.POINTER(C.c_float), P]),
+        "ocmc_unet_test_layer": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
+                                           P, P, P, P, P, P]),
+        "ocmc_denoise": (C.c_int, [P, P, C.c_float, P, P, C.c_int]),
         "ocmc_run_noalloc": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, P, P, C.c_float, C.c_float, C.c_float,
                                        C.c_int, C.c_int, P, P, C.c_float, C.c_float, C.c_float,
                                        C.POINTER(C.c_float), C.POINTER(C.c_float), C.POINTER(Params),
@@ -345,3 +356,78 @@ def run_noalloc(density, material, voxel, beam, tally, first, count, n_total, se
                               int(seed), pt, _stream_ptr(stream), msg, 256)
     if st != OK:
         raise OcmcError(st, msg.value.decode())
+
+
+class UNet:
+    """The 3D U-Net dose denoiser (ocmc_unet). Dose/density/target arguments are
+    CUDA tensors of the network's grid shape (nz, ny, nx), float32."""
+
+    def __init__(self, shape, device=0, seed=1):
+        nz, ny, nx = shape
+        self._u = C.c_void_p()
+        st = lib.ocmc_unet_create(C.byref(self._u), device, nx, ny, nz, int(seed))
+        if st != OK:
+            raise OcmcError(st, "ocmc_unet_create failed")
+        self.shape = tuple(shape)
+        n = C.c_int64()
+        self._check(lib.ocmc_unet_num_params(self._u, C.byref(n)))
+        self.num_params = n.value
+
+    def _check(self, st):
+        if st != OK:
+            raise OcmcError(st, lib.ocmc_unet_last_error(self._u).decode())
+
+    def close(self):
+        if getattr(self, "_u", None) and self._u.value:
+            lib.ocmc_unet_destroy(self._u)
+            self._u = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def params(self, grads=False):
+        out = np.empty(self.num_params, np.float32)
+        self._check(lib.ocmc_unet_get_params(self._u, C.c_void_p(out.ctypes.data), 1 if grads else 0))
+        return out
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, np.float32)
+        self._check(lib.ocmc_unet_set_params(self._u, C.c_void_p(p.ctypes.data)))
+
+    def forward(self, dose, density, out, stream=None):
+        self._check(lib.ocmc_unet_forward(self._u, _ptr(dose)[0], _ptr(density)[0], _ptr(out)[0],
+                                          _stream_ptr(stream)))
+        return out
+
+    def train_step(self, dose, density, target, lr, stream=None):
+        loss = C.c_float()
+        self._check(lib.ocmc_unet_train_step(self._u, _ptr(dose)[0], _ptr(density)[0], _ptr(target)[0],
+                                             float(lr), C.byref(loss), _stream_ptr(stream)))
+        return loss.value
+
+
+def unet_test_layer(mode, fine_shape, cin, cout, x, w, dy, device=0):
+    """One layer through the denoiser's kernels: returns (y, dx, dw)."""
+    nz, ny, nx = fine_shape
+    x = np.ascontiguousarray(x, np.float32)
+    w = np.ascontiguousarray(w, np.float32)
+    dy = np.ascontiguousarray(dy, np.float32)
+    y = np.empty(dy.shape, np.float32)
+    dx = np.empty(x.shape, np.float32)
+    dw = np.empty(w.shape, np.float32)
+    st = lib.ocmc_unet_test_layer(device, mode, nx, ny, nz, cin, cout, *(C.c_void_p(a.ctypes.data)
+                                                                        for a in (x, w, dy, y, dx, dw)))
+    if st != OK:
+        raise OcmcError(st, "ocmc_unet_test_layer failed")
+    return y, dx, dw
+
+
+def denoise(engine, net, k_sigma, out, flag=None):
+    """ocmc_denoise: denoised dose of the engine's current tally with plain-MC fallback."""
+    po, dev = _ptr(out)
+    pf = _ptr(flag)[0] if flag is not None else None
+    engine._check(lib.ocmc_denoise(engine._c, net._u, float(k_sigma), po, pf, dev))
+    return out, flag

@@ -1,0 +1,117 @@
+"""The tensor-core denoiser against its numpy oracle (oracle/unet.py): every layer kind's
+forward, data gradient and weight gradient, the whole network's output and parameter
+gradients, training progress, and the plain-Monte-Carlo fallback."""
+import numpy as np
+import pytest
+
+from oracle import unet as U
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ocmc():
+    from paper_1503_01722_gb300 import build
+    build.build()
+    from paper_1503_01722_gb300 import ocmc as m
+    return m
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(np.ravel(a) - np.ravel(b)) / max(np.linalg.norm(np.ravel(b)), 1e-30))
+
+
+CASES = [(0, 16, 16), (0, 32, 16), (0, 16, 32), (0, 64, 128), (0, 128, 64),
+         (1, 16, 32), (1, 32, 64), (1, 64, 128), (2, 128, 64), (2, 64, 32), (2, 32, 16)]
+
+
+@pytest.mark.parametrize("mode,cin,cout", CASES)
+def test_layer_matches_oracle(ocmc, mode, cin, cout):
+    rng = np.random.default_rng(mode * 1000 + cin + cout)
+    fine = (10, 12, 14)                       # 1680 voxels: several 128-row tiles and a ragged tail
+    coarse = tuple(s // 2 for s in fine)
+    gin = coarse if mode == 2 else fine
+    gout = coarse if mode == 1 else fine
+    taps = 27 if mode == 0 else 8
+    x = U.bf16(rng.standard_normal(gin + (cin,)))
+    W = U.bf16(rng.standard_normal((taps, cin, cout)) / np.sqrt(taps * cin))
+    dy = U.bf16(rng.standard_normal(gout + (cout,)))
+    y, dx, dw = ocmc.unet_test_layer(mode, fine, cin, cout, x, W, dy)
+    if mode == 0:
+        yr, dxr, dwr = U.conv3(x, W), U.conv3_dx(dy, W), U.conv3_dw(x, dy)
+    elif mode == 1:
+        yr, dxr, dwr = U.down(x, W), U.down_dx(dy, W, x.shape), U.down_dw(x, dy)
+    else:
+        yr, dxr, dwr = U.up(x, W), U.up_dx(dy, W), U.up_dw(x, dy)
+    # y and dx are stored in BF16 (relative rounding 2^-9); dW is FP32
+    assert np.allclose(y, yr, rtol=8e-3, atol=1e-2 * np.abs(yr).max())
+    assert np.allclose(dx, dxr, rtol=8e-3, atol=1e-2 * np.abs(dxr).max())
+    assert rel_l2(y, yr) < 4e-3 and rel_l2(dx, dxr) < 4e-3
+    assert np.allclose(dw, dwr, rtol=1e-4, atol=1e-4 * np.abs(dwr).max())
+
+
+def random_case(shape, seed):
+    rng = np.random.default_rng(seed)
+    z, y, x = np.meshgrid(*[np.linspace(-1, 1, n) for n in shape], indexing="ij")
+    target = np.exp(-4 * (x ** 2 + y ** 2)) * np.exp(-0.5 * (z + 1))
+    dose = np.maximum(target * (1 + 0.3 * rng.standard_normal(shape)), 0)
+    dens = np.where(rng.random(shape) < 0.1, 0.05, rng.uniform(0.3, 1.8, shape))
+    return dose.astype(np.float32), dens.astype(np.float32), target.astype(np.float32)
+
+
+def test_network_output_and_gradients_match_oracle(ocmc):
+    import torch
+    shape = (16, 16, 16)
+    net = ocmc.UNet(shape, seed=3)
+    p = net.params().astype(np.float64)
+    p[-17:-1] = np.random.default_rng(5).standard_normal(16) * 0.2     # a head that passes signal
+    net.set_params(p)
+    dose, dens, target = random_case(shape, 7)
+    td, tr, tt = (torch.from_numpy(a).cuda() for a in (dose, dens, target))
+    out = torch.empty_like(td)
+    net.forward(td, tr, out)
+    ref = U.UNet(p.astype(np.float32).astype(np.float64), bf16_storage=True)
+    assert rel_l2(out.cpu().numpy(), ref.forward(dose, dens)) < 1e-2
+    loss = net.train_step(td, tr, tt, lr=0.0)
+    G = net.params(grads=True)
+    lr_, Gr = ref.loss_and_grads(dose, dens, target)
+    assert abs(loss - lr_) < 1e-2 * lr_
+    lay, hw, hb = U.param_layout()
+    for i, (off, shp, boff, cout) in enumerate(lay):
+        n = int(np.prod(shp))
+        assert rel_l2(G[off:off + n], Gr[off:off + n]) < 5e-2, i
+        assert rel_l2(G[boff:boff + cout], Gr[boff:boff + cout]) < 5e-2, i
+    assert rel_l2(G[hw:hw + 17], Gr[hw:hw + 17]) < 2e-2
+
+
+def test_training_reduces_loss(ocmc):
+    import torch
+    shape = (32, 32, 32)
+    net = ocmc.UNet(shape, seed=1)
+    dose, dens, target = random_case(shape, 9)
+    td, tr, tt = (torch.from_numpy(a).cuda() for a in (dose, dens, target))
+    losses = [net.train_step(td, tr, tt, lr=1e-3) for _ in range(60)]
+    assert losses[-1] < 0.5 * losses[0], (losses[0], losses[-1])
+
+
+def test_denoise_fallback(ocmc):
+    import torch
+    import ocmc_inputs as I
+    ph = I.homogeneous((16, 16, 16), (1.0, 1.0, 1.0))
+    net = ocmc.UNet(ph.density.shape, seed=2)
+    with ocmc.Engine(0) as e:
+        e.create_phantom(ph)
+        e.set_source(I.beam_on(ph, 0, I.mono(2.0), (6, 6), 100.0))
+        e.run(200_000, seed=1)
+        D, S = e.dose()
+        out = torch.empty(ph.density.shape, dtype=torch.float32, device="cuda")
+        flag = torch.empty_like(out)
+        # tiny k: every voxel whose network value differs from plain MC keeps the plain value
+        ocmc.denoise(e, net, 1e-6, out, flag)
+        o, f = out.cpu().numpy(), flag.cpu().numpy()
+        assert np.array_equal(o[f == 1], D[f == 1]) and f.mean() > 0.5
+        # huge k: the network output
+        ocmc.denoise(e, net, 1e30, out, flag)
+        ref = torch.empty_like(out)
+        net.forward(torch.from_numpy(D).cuda(), torch.from_numpy(ph.density).cuda(), ref)
+        assert flag.sum().item() == 0 and torch.equal(out, ref)
