@@ -247,7 +247,8 @@ typedef struct ocmc_unet ocmc_unet;
 ocmc_status ocmc_unet_create(ocmc_unet** out, int device, int nx, int ny, int nz, uint64_t seed);
 void ocmc_unet_destroy(ocmc_unet* net);
 const char* ocmc_unet_last_error(ocmc_unet* net);
-/* Number of FP32 parameters; get/set all of them (grads = 1: the last gradients). */
+/* Number of FP32 parameters; get/set all of them (grads = 1: the last gradients).
+ * Setting the parameters also restarts Adam (zero moments, step count 0). */
 ocmc_status ocmc_unet_num_params(ocmc_unet* net, int64_t* n);
 ocmc_status ocmc_unet_get_params(ocmc_unet* net, float* host, int grads);
 ocmc_status ocmc_unet_set_params(ocmc_unet* net, const float* host);

@@ -230,6 +230,24 @@ def beamlets_ct():
     return ph, spectrum_6mv(), beamlets(ph)
 
 
+def denoiser_case(seed, n=(128, 128, 128), voxel=(0.25, 0.25, 0.25)):
+    """One random case for training or judging the dose denoiser: the CT-like phantom
+    generator at 128^3 x 0.25 cm with this seed, and a random beam: 6 MV photons or
+    mono-energetic electrons with E ~ U(6, 20) MeV (equal odds), field sides U(2, 20) cm each
+    in the plane through the phantom centre, gantry angle U(0, 2 pi) about the y axis through
+    the centre, point source at SAD 100 cm."""
+    ph = ct_like(n, voxel, seed)
+    rng = np.random.default_rng([int(seed), 5])
+    particle = int(rng.integers(0, 2))
+    edges, w = spectrum_6mv() if particle == 0 else mono(float(rng.uniform(6.0, 20.0)))
+    fx, fy = (float(v) for v in rng.uniform(2.0, 20.0, 2))
+    th = float(rng.uniform(0.0, 2.0 * math.pi))
+    lx, ly, lz = ph.size_cm
+    beam = Beam(particle, edges, w, (fx, fy), 100.0, (lx / 2, ly / 2, lz / 2),
+                (math.sin(th), 0.0, math.cos(th)))
+    return ph, beam
+
+
 def pencil(ph: Phantom, particle, E, direction=(0.0, 0.0, 1.0)):
     """Infinitely thin parallel beam along +z through the x-y centre."""
     lx, ly, _ = ph.size_cm

@@ -248,6 +248,7 @@ struct ocmc_unet {
     float* gout = nullptr;
     unsigned int* smax = nullptr;
     double* lacc = nullptr;
+    float* fb = nullptr;            // denoise scratch: plain dose, sigma, output, flags (4 x nvox)
     std::string err;
 };
 
@@ -600,6 +601,7 @@ void ocmc_unet_destroy(ocmc_unet* u)
     cudaFree(u->params); cudaFree(u->grads); cudaFree(u->adam_m); cudaFree(u->adam_v); cudaFree(u->part);
     cudaFree(u->tmpw); cudaFree(u->bpart);
     cudaFree(u->x0f); cudaFree(u->outf); cudaFree(u->gout); cudaFree(u->smax); cudaFree(u->lacc);
+    cudaFree(u->fb);
     delete u;
 }
 
@@ -625,6 +627,9 @@ ocmc_status ocmc_unet_set_params(ocmc_unet* u, const float* host)
     if (!u || !host) return OCMC_ERR_ARG;
     UCK(cudaSetDevice(u->device), "device");
     UCK(cudaMemcpy(u->params, host, u->nparams * sizeof(float), cudaMemcpyHostToDevice), "copy");
+    UCK(cudaMemset(u->adam_m, 0, u->nparams * sizeof(float)), "adam");
+    UCK(cudaMemset(u->adam_v, 0, u->nparams * sizeof(float)), "adam");
+    u->step = 0;
     UCK(refresh_bf16(u, nullptr), "weights");
     UCK(cudaDeviceSynchronize(), "sync");
     return OCMC_OK;
@@ -766,31 +771,29 @@ ocmc_status ocmc_denoise(ocmc_ctx* c, ocmc_unet* u, float k_sigma, float* dose_o
     if (!c || !u || !dose_out) return ctx_fail(c, OCMC_ERR_ARG, "NULL argument");
     if (!c->have_phantom || c->nvox != u->nvox) return ctx_fail(c, OCMC_ERR_ARG, "network grid differs from phantom");
     if (!(k_sigma > 0.f)) return ctx_fail(c, OCMC_ERR_ARG, "k_sigma must be > 0");
-    float *dd = nullptr, *ds = nullptr, *dout = nullptr, *dflag = nullptr;
     cudaError_t e = cudaSetDevice(c->device);
     long long n = c->nvox;
-    if (e == cudaSuccess) e = cudaMalloc(&dd, n * 4);
-    if (e == cudaSuccess) e = cudaMalloc(&ds, n * 4);
-    if (e == cudaSuccess) e = cudaMalloc(&dout, n * 4);
-    if (e == cudaSuccess) e = cudaMalloc(&dflag, n * 4);
-    if (e != cudaSuccess) {
-        cudaFree(dd); cudaFree(ds); cudaFree(dout); cudaFree(dflag);
-        return ctx_cuda_fail(c, e, "allocation");
+    if (e == cudaSuccess && !u->fb) e = cudaMalloc(&u->fb, 4 * n * sizeof(float));
+    if (e != cudaSuccess) return ctx_cuda_fail(c, e, "allocation");
+    float *dd = u->fb, *ds = dd + n, *dout = ds + n, *dflag = dout + n;
+    if (on_device) {
+        dout = dose_out;
+        if (flag_out) dflag = flag_out;
     }
     ocmc_status st = ocmc_get_dose(c, dd, ds, 1);
     if (st == OCMC_OK || st == OCMC_ERR_OVERFLOW || st == OCMC_ERR_TIMEOUT) {
         ocmc_status s2 = ocmc_unet_forward(u, dd, c->d_density, dout, nullptr);
         if (s2 == OCMC_OK) {
             k_fallback<<<grid_for(n), 256>>>(dd, ds, dout, dflag, k_sigma, n);
-            cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
-            e = cudaMemcpy(dose_out, dout, n * 4, k);
-            if (e == cudaSuccess && flag_out) e = cudaMemcpy(flag_out, dflag, n * 4, k);
-            if (e != cudaSuccess) st = ctx_cuda_fail(c, e, "copy");
+            e = cudaGetLastError();
+            if (e == cudaSuccess && !on_device) e = cudaMemcpy(dose_out, dout, n * 4, cudaMemcpyDeviceToHost);
+            if (e == cudaSuccess && !on_device && flag_out) e = cudaMemcpy(flag_out, dflag, n * 4, cudaMemcpyDeviceToHost);
+            if (e == cudaSuccess) e = cudaDeviceSynchronize();
+            if (e != cudaSuccess) st = ctx_cuda_fail(c, e, "denoise");
         } else {
             st = ctx_fail(c, s2, std::string("network: ") + u->err);
         }
     }
-    cudaFree(dd); cudaFree(ds); cudaFree(dout); cudaFree(dflag);
     return st;
 }
 
