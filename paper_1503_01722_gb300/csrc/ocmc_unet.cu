@@ -9,9 +9,11 @@
 // over voxels of density >= 0.1 g/cm^3; Adam on FP32 master weights with BF16 copies.
 #include "ocmc_ctx.h"
 #include "ocmc_unet_kernels.cuh"
+#include "ocmc_unet_tc.h"
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -221,6 +223,8 @@ struct Layer {
     size_t woff, boff;              // offsets in the flat parameter vector
     __nv_bfloat16* wf = nullptr;    // forward BF16 weights
     __nv_bfloat16* wt = nullptr;    // transposed / flipped BF16 weights
+    __nv_bfloat16* wtc_f = nullptr; // wf packed for the tensor-memory convolution (CONV3), or null
+    __nv_bfloat16* wtc_t = nullptr; // wt packed likewise, for the data gradient
     bool grad_accumulate = false;   // the input's gradient slice was already written
 };
 
@@ -249,6 +253,8 @@ struct ocmc_unet {
     unsigned int* smax = nullptr;
     double* lacc = nullptr;
     float* fb = nullptr;            // denoise scratch: plain dose, sigma, output, flags (4 x nvox)
+    int* kerr = nullptr;            // device flag: a tensor-memory kernel timed out
+    bool tc = true;                 // 3x3x3 convolutions on tcgen05 where the kernel covers them
     std::string err;
 };
 
@@ -270,6 +276,17 @@ ocmc_status ufail(ocmc_unet* u, ocmc_status s, const std::string& m)
 
 int grid_for(long long n) { return (int)std::max<long long>(1, std::min<long long>((n + 255) / 256, 152 * 16)); }
 
+// A tensor-memory kernel that timed out has set u->kerr; report it once and clear it.
+ocmc_status take_kernel_flag(ocmc_unet* u, cudaStream_t s)
+{
+    int f = 0;
+    UCK(cudaMemcpyAsync(&f, u->kerr, sizeof(int), cudaMemcpyDeviceToHost, s), "flag");
+    UCK(cudaStreamSynchronize(s), "sync");
+    if (!f) return OCMC_OK;
+    UCK(cudaMemsetAsync(u->kerr, 0, sizeof(int), s), "flag");
+    return ufail(u, OCMC_ERR_TIMEOUT, "a tensor-memory convolution timed out waiting for its data");
+}
+
 template <int BK>
 cudaError_t launch_conv_bk(const ConvArgs& a, cudaStream_t s)
 {
@@ -287,6 +304,7 @@ cudaError_t launch_conv_bk(const ConvArgs& a, cudaStream_t s)
 
 cudaError_t launch_conv(const ConvArgs& a, cudaStream_t s)
 {
+    if (a.mode == CONV3 && a.wtc && conv3_tc_supported(a.cin, a.cout)) return launch_conv3_tc(a, a.wtc, a.err, s);
     return a.cin % 32 == 0 ? launch_conv_bk<32>(a, s) : launch_conv_bk<16>(a, s);
 }
 
@@ -358,8 +376,10 @@ cudaError_t layer_fwd(ocmc_unet* u, const Layer& L, cudaStream_t s)
     a.cout = L.cout;
     a.bias = u->params + L.boff;
     a.relu = 1;
+    a.err = u->kerr;
     if (L.mode != UP) {
         a.w = L.wf;
+        a.wtc = u->tc ? L.wtc_f : nullptr;
         return launch_conv(a, s);
     }
     for (int p = 0; p < 8; ++p) {
@@ -411,6 +431,8 @@ cudaError_t layer_bwd(ocmc_unet* u, const Layer& L, bool need_dx, cudaStream_t s
         a.gin = u->g[L.lout];
         a.gout = u->g[L.lin];
         a.w = L.wt;
+        a.wtc = u->tc ? L.wtc_t : nullptr;
+        a.err = u->kerr;
         return launch_conv(a, s);
     }
     if (L.mode == DOWN) {           // fine <- coarse: UP over parities with W'[p][n][c]
@@ -438,6 +460,10 @@ cudaError_t refresh_bf16(ocmc_unet* u, cudaStream_t s)
         long long m = (long long)L.taps * L.cin * L.cout;
         k_weights_bf16<<<grid_for(m), 256, 0, s>>>(u->params + L.woff, L.taps, L.cin, L.cout, L.mode == CONV3,
                                                    L.wf, L.wt);
+        cudaError_t e = cudaSuccess;
+        if (L.wtc_f) e = pack_conv3_tc(L.wf, L.cin, L.cout, L.wtc_f, s);
+        if (e == cudaSuccess && L.wtc_t) e = pack_conv3_tc(L.wt, L.cout, L.cin, L.wtc_t, s);
+        if (e != cudaSuccess) return e;
     }
     return cudaGetLastError();
 }
@@ -550,6 +576,14 @@ ocmc_status ocmc_unet_create(ocmc_unet** out, int device, int nx, int ny, int nz
         size_t m = (size_t)L.taps * L.cin * L.cout * sizeof(__nv_bfloat16);
         if (e == cudaSuccess) e = cudaMalloc(&L.wf, m);
         if (e == cudaSuccess) e = cudaMalloc(&L.wt, m);
+        if (L.mode == CONV3 && conv3_tc_supported(L.cin, L.cout) && e == cudaSuccess) e = cudaMalloc(&L.wtc_f, m);
+        if (L.mode == CONV3 && conv3_tc_supported(L.cout, L.cin) && e == cudaSuccess) e = cudaMalloc(&L.wtc_t, m);
+    }
+    if (e == cudaSuccess) e = cudaMalloc(&u->kerr, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(u->kerr, 0, sizeof(int));
+    {
+        const char* k = std::getenv("OCMC_UNET_KERNELS");
+        u->tc = !(k && std::strcmp(k, "mma") == 0);
     }
     size_t pbytes = u->nparams * sizeof(float);
     if (e == cudaSuccess) e = cudaMalloc(&u->params, pbytes);
@@ -597,11 +631,11 @@ void ocmc_unet_destroy(ocmc_unet* u)
     cudaSetDevice(u->device);
     cudaDeviceSynchronize();
     for (Act& A : u->acts) { cudaFree(A.x); cudaFree(A.g); }
-    for (Layer& L : u->layers) { cudaFree(L.wf); cudaFree(L.wt); }
+    for (Layer& L : u->layers) { cudaFree(L.wf); cudaFree(L.wt); cudaFree(L.wtc_f); cudaFree(L.wtc_t); }
     cudaFree(u->params); cudaFree(u->grads); cudaFree(u->adam_m); cudaFree(u->adam_v); cudaFree(u->part);
     cudaFree(u->tmpw); cudaFree(u->bpart);
     cudaFree(u->x0f); cudaFree(u->outf); cudaFree(u->gout); cudaFree(u->smax); cudaFree(u->lacc);
-    cudaFree(u->fb);
+    cudaFree(u->fb); cudaFree(u->kerr);
     delete u;
 }
 
@@ -682,6 +716,8 @@ ocmc_status ocmc_unet_train_step(ocmc_unet* u, const float* dose, const float* d
         UCK(refresh_bf16(u, s), "weights");
     }
     if (loss_host) {
+        ocmc_status fs = take_kernel_flag(u, s);
+        if (fs != OCMC_OK) return fs;
         double acc[2];
         UCK(cudaMemcpyAsync(acc, u->lacc, sizeof(acc), cudaMemcpyDeviceToHost, s), "loss");
         UCK(cudaStreamSynchronize(s), "sync");
@@ -715,16 +751,26 @@ ocmc_status ocmc_unet_test_layer(int device, int mode, int nx, int ny, int nz, i
     A((void**)&dX, ni * cin * 2); A((void**)&dY, no * cout * 2); A((void**)&dDY, no * cout * 2);
     A((void**)&dDX, ni * cin * 2); A((void**)&wf, nw * 2); A((void**)&wt, nw * 2); A((void**)&w32, nw * 4);
     A((void**)&part, part_n * 4); A((void**)&dW, nw * 4); A((void**)&dW2, nw * 4);
+    __nv_bfloat16 *pf = nullptr, *pt = nullptr;
+    int* kerr = nullptr;
+    const bool tcf = m == CONV3 && conv3_tc_supported(cin, cout), tct = m == CONV3 && conv3_tc_supported(cout, cin);
+    if (tcf) A((void**)&pf, nw * 2);
+    if (tct) A((void**)&pt, nw * 2);
+    A((void**)&kerr, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(kerr, 0, sizeof(int));
     if (e == cudaSuccess) e = cudaMemcpy(dX, hx.data(), ni * cin * 2, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(dDY, hdy.data(), no * cout * 2, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(w32, w, nw * 4, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) {
         k_weights_bf16<<<grid_for(nw), 256>>>(w32, taps, cin, cout, m == CONV3, wf, wt);
+        if (tcf) e = pack_conv3_tc(wf, cin, cout, pf, nullptr);
+        if (tct && e == cudaSuccess) e = pack_conv3_tc(wt, cout, cin, pt, nullptr);
         ConvArgs a;
         std::memset(&a, 0, sizeof(a));
         a.mode = m; a.gin = gi; a.gout = go; a.in = Slice{dX, cin, 0}; a.out = Slice{dY, cout, 0};
         a.cin = cin; a.cout = cout;
-        if (m != UP) { a.w = wf; e = launch_conv(a, nullptr); }
+        a.wtc = pf; a.err = kerr;
+        if (m != UP && e == cudaSuccess) { a.w = wf; e = launch_conv(a, nullptr); }
         else for (int p = 0; p < 8 && e == cudaSuccess; ++p) { a.parity = p; a.w = wf + (size_t)p * cin * cout; e = launch_conv(a, nullptr); }
     }
     if (e == cudaSuccess) {
@@ -732,6 +778,7 @@ ocmc_status ocmc_unet_test_layer(int device, int mode, int nx, int ny, int nz, i
         std::memset(&a, 0, sizeof(a));
         a.in = Slice{dDY, cout, 0}; a.out = Slice{dDX, cin, 0}; a.cin = cout; a.cout = cin;
         a.gin = go; a.gout = gi;
+        a.wtc = pt; a.err = kerr;
         if (m == CONV3) { a.mode = CONV3; a.w = wt; e = launch_conv(a, nullptr); }
         else if (m == DOWN) {
             a.mode = UP;
@@ -750,6 +797,8 @@ ocmc_status ocmc_unet_test_layer(int device, int mode, int nx, int ny, int nz, i
         }
     }
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    int flag = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&flag, kerr, sizeof(int), cudaMemcpyDeviceToHost);
     std::vector<__nv_bfloat16> hy(no * cout), hdx(ni * cin);
     if (e == cudaSuccess) e = cudaMemcpy(hy.data(), dY, no * cout * 2, cudaMemcpyDeviceToHost);
     if (e == cudaSuccess) e = cudaMemcpy(hdx.data(), dDX, ni * cin * 2, cudaMemcpyDeviceToHost);
@@ -759,8 +808,9 @@ ocmc_status ocmc_unet_test_layer(int device, int mode, int nx, int ny, int nz, i
         for (long long i = 0; i < ni * cin; ++i) dx[i] = __bfloat162float(hdx[i]);
     }
     cudaFree(dX); cudaFree(dY); cudaFree(dDY); cudaFree(dDX); cudaFree(wf); cudaFree(wt); cudaFree(w32);
-    cudaFree(part); cudaFree(dW); cudaFree(dW2);
-    return e == cudaSuccess ? OCMC_OK : OCMC_ERR_CUDA;
+    cudaFree(part); cudaFree(dW); cudaFree(dW2); cudaFree(pf); cudaFree(pt); cudaFree(kerr);
+    if (e != cudaSuccess) return OCMC_ERR_CUDA;
+    return flag ? OCMC_ERR_TIMEOUT : OCMC_OK;
 }
 
 // Denoise the context's current dose: the network maps (dose, density) to a converged
@@ -790,6 +840,7 @@ ocmc_status ocmc_denoise(ocmc_ctx* c, ocmc_unet* u, float k_sigma, float* dose_o
             if (e == cudaSuccess && !on_device && flag_out) e = cudaMemcpy(flag_out, dflag, n * 4, cudaMemcpyDeviceToHost);
             if (e == cudaSuccess) e = cudaDeviceSynchronize();
             if (e != cudaSuccess) st = ctx_cuda_fail(c, e, "denoise");
+            else if (take_kernel_flag(u, nullptr) != OCMC_OK) st = ctx_fail(c, OCMC_ERR_TIMEOUT, u->err);
         } else {
             st = ctx_fail(c, s2, std::string("network: ") + u->err);
         }

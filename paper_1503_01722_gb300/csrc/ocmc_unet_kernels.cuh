@@ -50,6 +50,8 @@ struct ConvArgs {
     const __nv_bfloat16* mask;   // multiply by (mask(v, c) > 0), mask is a Slice-like buffer
     int mask_stride, mask_c0;
     int parity;                  // UP mode: output parity 0..7
+    const __nv_bfloat16* wtc;    // CONV3: weights packed for the tensor-memory kernel, or null
+    int* err;                    // device error flag for the tensor-memory kernel (may be null)
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p)

@@ -1,0 +1,370 @@
+// ocmc_unet_tc.cu -- 3x3x3 convolutions of the denoiser on the 5th-generation tensor cores
+// (tcgen05.mma, accumulators in tensor memory, operands staged by TMA).
+//
+// Output tile: 8 (x) x 16 (y) x TZ (z) voxels. For one z-slice the 128 voxels are the M = 128
+// rows of an MMA (row m = x + 8 y). The block loads, per 16-channel input chunk, the halo
+// of its tile, 10 x 18 x (TZ + 2) voxels, as two planes of 8 channels (16 bytes per voxel) in
+// the order z, y, x: TMA writes exactly that from a 5-D view of the channels-last activation
+// (8 channels, channel group, x, y, z) and zero-fills outside the grid, which is the
+// convolution's padding. Because every halo row of 10 voxels is contiguous, the A operand of
+// tap (dx, dy, dz) for slice s is a no-swizzle K-major matrix starting at halo voxel
+// (dx, dy, s + dz): 8 rows 16 bytes apart (x), next 8-row group 160 bytes on (y), second
+// 8 channels one plane on (K). No data is copied per tap.
+// The layer's weights stay in shared memory for the whole kernel, packed [tap][channel group]
+// [out channel][8 channels] so that B (N = out channels, K = 16 input channels) is K-major too.
+// Each (tap, slice) is one MMA of M = 128, N = cout, K = 16, accumulating in FP32 in tensor
+// memory; two accumulator sets let the epilogue of one tile overlap the MMAs of the next.
+//
+// Warp roles (192 threads): warp 0 issues the TMA copies, warp 1 owns tensor memory and one of
+// its lanes issues the MMAs, warps 2-5 read the accumulators (each warp its 32-lane quarter of
+// tensor memory), add bias / previous value, apply ReLU and mask, and store BF16. Every wait
+// gives up after two seconds, sets the error flag, lets its copies in flight land and frees
+// tensor memory before the block exits.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <mutex>
+
+#include "ocmc_umma.cuh"
+#include "ocmc_unet_kernels.cuh"
+#include "ocmc_unet_tc.h"
+
+namespace ocmc {
+namespace unet {
+namespace {
+
+using namespace ocmc::umma;
+
+constexpr int TX = 8, TY = 16, HX = TX + 2, HY = TY + 2;
+constexpr int TC_THREADS = 192;
+constexpr uint64_t WAIT_NS = 2000000000ull;
+
+struct TcArgs {
+    Grid3 g;
+    Slice out;
+    const __nv_bfloat16* wpack;
+    const float* bias;
+    int relu, accumulate;
+    const __nv_bfloat16* mask;
+    int mask_stride, mask_c0;
+    int tiles_x, tiles_y, ntiles;
+    int* err;
+};
+
+template <int CIN, int COUT, int TZ>
+struct Cfg {
+    static constexpr int NS = 2;                                         // halo stages
+    static constexpr int G = CIN / 8;
+    static constexpr int CHUNKS = CIN / 16;
+    static constexpr uint32_t W_BYTES = 27u * CIN * COUT * 2;
+    static constexpr uint32_t PLANE = (uint32_t)(TZ + 2) * HY * HX * 16;
+    static constexpr uint32_t STAGE = 2 * PLANE;
+    static constexpr uint32_t BAR_OFF = W_BYTES + NS * STAGE;
+    static constexpr uint32_t SMEM = BAR_OFF + 256;
+    static constexpr uint32_t COLS = 2 * TZ * COUT;
+    static constexpr uint32_t NCOLS = COLS <= 32 ? 32 : COLS <= 64 ? 64 : COLS <= 128 ? 128 : COLS <= 256 ? 256 : 512;
+    static_assert(COLS <= 512, "tensor memory holds 512 columns");
+    static_assert(CIN % 16 == 0 && COUT % 16 == 0 && COUT <= 256, "MMA shape");
+    static_assert(W_BYTES % 128 == 0 && PLANE % 128 == 0, "TMA destinations 128-byte aligned");
+    static_assert(SMEM <= 232448, "shared memory per block");
+};
+
+__device__ __forceinline__ bool wait_bounded(uint64_t* bar, uint32_t parity)
+{
+    int dummy = 0;
+    return mbar_wait(bar, parity, &dummy, WAIT_NS);
+}
+
+template <int CIN, int COUT, int TZ>
+__global__ void __launch_bounds__(TC_THREADS, 1) k_conv3_tc(const __grid_constant__ CUtensorMap tmap, const TcArgs a)
+{
+    using C = Cfg<CIN, COUT, TZ>;
+    constexpr int NS = C::NS;
+    extern __shared__ __align__(1024) uint8_t smem[];
+    uint8_t* sw = smem;
+    uint8_t* sh = smem + C::W_BYTES;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + C::BAR_OFF);
+    uint64_t* w_full = bars;
+    uint64_t* h_full = bars + 1;
+    uint64_t* h_empty = bars + 1 + NS;
+    uint64_t* t_full = bars + 1 + 2 * NS;
+    uint64_t* t_empty = bars + 3 + 2 * NS;
+    uint64_t* drain = bars + 5 + 2 * NS;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 6 + 2 * NS);
+    volatile int* abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    if (threadIdx.x == 0) {
+        mbar_init(w_full, 1);
+        for (int i = 0; i < NS; ++i) {
+            mbar_init(&h_full[i], 1);
+            mbar_init(&h_empty[i], 1);
+        }
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&t_full[i], 1);
+            mbar_init(&t_empty[i], 4);
+        }
+        mbar_init(drain, 1);
+        *abort = 0;
+        fence_mbar_init();
+    }
+    if (warp == 1) tmem_alloc(tmem_slot, C::NCOLS);
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        // ---- producer: weights once, then one halo chunk per (tile, chunk) ----
+        if (lane == 0) {
+            mbar_expect_tx(w_full, C::W_BYTES);
+            for (uint32_t off = 0; off < C::W_BYTES; off += 32768u)
+                bulk_load(sw + off, reinterpret_cast<const uint8_t*>(a.wpack) + off, min(32768u, C::W_BYTES - off),
+                          w_full);
+            int it = 0;
+            int last[NS];
+#pragma unroll
+            for (int i = 0; i < NS; ++i) last[i] = -1;
+            for (int tile = blockIdx.x; tile < a.ntiles && !*abort; tile += gridDim.x) {
+                const int tx = tile % a.tiles_x, r = tile / a.tiles_x;
+                const int x0 = tx * TX, y0 = (r % a.tiles_y) * TY, z0 = (r / a.tiles_y) * TZ;
+                for (int c = 0; c < C::CHUNKS; ++c, ++it) {
+                    const int st = it % NS, u = it / NS;
+                    if (!mbar_wait(&h_empty[st], (u & 1) ^ 1, abort, WAIT_NS)) break;
+                    uint8_t* dst = sh + st * C::STAGE;
+                    mbar_expect_tx(&h_full[st], C::STAGE);
+                    tma_load_5d(dst, &tmap, 0, 2 * c, x0 - 1, y0 - 1, z0 - 1, &h_full[st]);
+                    tma_load_5d(dst + C::PLANE, &tmap, 0, 2 * c + 1, x0 - 1, y0 - 1, z0 - 1, &h_full[st]);
+                    last[st] = u;
+                }
+            }
+            if (*abort) {   // copies in flight must land before the block exits
+                wait_bounded(w_full, 0);
+                for (int i = 0; i < NS; ++i)
+                    if (last[i] >= 0) wait_bounded(&h_full[i], last[i] & 1);
+            }
+        }
+    } else if (warp == 1) {
+        // ---- MMA issue ----
+        if (lane == 0) {
+            bool issued = false;
+            if (mbar_wait(w_full, 0, abort, WAIT_NS)) {
+                fence_after_sync();
+                constexpr uint32_t idesc = idesc_bf16_f32(128, COUT);
+                const uint32_t sw_addr = saddr(sw), sh_addr = saddr(sh);
+                int it = 0, lt = 0;
+                for (int tile = blockIdx.x; tile < a.ntiles && !*abort; tile += gridDim.x, ++lt) {
+                    const int acc = lt & 1, ua = lt >> 1;
+                    if (!mbar_wait(&t_empty[acc], (ua & 1) ^ 1, abort, WAIT_NS)) break;
+                    fence_after_sync();
+                    const uint32_t d0 = tmem + (uint32_t)(acc * TZ * COUT);
+                    for (int c = 0; c < C::CHUNKS; ++c, ++it) {
+                        const int st = it % NS, u = it / NS;
+                        if (!mbar_wait(&h_full[st], u & 1, abort, WAIT_NS)) break;
+                        fence_after_sync();
+                        const uint32_t hb = sh_addr + (uint32_t)st * C::STAGE;
+                        const uint32_t wb = sw_addr + (uint32_t)(2 * c) * COUT * 16;
+#pragma unroll 1
+                        for (int t = 0; t < 27; ++t) {
+                            const int dx = t % 3, dy = (t / 3) % 3, dz = t / 9;
+                            const uint64_t bd = sdesc(wb + (uint32_t)t * C::G * COUT * 16, COUT * 16, 128);
+#pragma unroll
+                            for (int s = 0; s < TZ; ++s) {
+                                const uint32_t ao = (uint32_t)(((s + dz) * HY + dy) * HX + dx) * 16;
+                                mma_f16(d0 + (uint32_t)(s * COUT), sdesc(hb + ao, C::PLANE, HX * 16), bd, idesc,
+                                        (c | t) != 0);
+                            }
+                        }
+                        mma_commit(&h_empty[st]);
+                        issued = true;
+                    }
+                    if (*abort) break;
+                    mma_commit(&t_full[acc]);
+                }
+            }
+            if (*abort && issued) {   // MMAs in flight must finish before tensor memory is freed
+                mma_commit(drain);
+                wait_bounded(drain, 0);
+            }
+        }
+        __syncwarp();
+    } else {
+        // ---- epilogue: tensor memory -> bias / accumulate / ReLU / mask -> BF16 ----
+        const int q = warp & 3;                       // the tensor-memory lane quarter of this warp
+        const int row = 32 * q + lane;
+        int lt = 0;
+        for (int tile = blockIdx.x; tile < a.ntiles && !*abort; tile += gridDim.x, ++lt) {
+            const int acc = lt & 1, ua = lt >> 1;
+            if (!mbar_wait(&t_full[acc], ua & 1, abort, WAIT_NS)) break;
+            fence_after_sync();
+            const int tx = tile % a.tiles_x, r = tile / a.tiles_x;
+            const int x = tx * TX + (row & 7), y = (r % a.tiles_y) * TY + (row >> 3), z0 = (r / a.tiles_y) * TZ;
+            const uint32_t tbase = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(acc * TZ * COUT);
+#pragma unroll 1
+            for (int s = 0; s < TZ; ++s) {
+                float v[COUT];
+#pragma unroll
+                for (int j = 0; j < COUT / 16; ++j) tmem_ld16(tbase + (uint32_t)(s * COUT + 16 * j), v + 16 * j);
+                const int z = z0 + s;
+                if (x < a.g.nx && y < a.g.ny && z < a.g.nz) {
+                    const long long vox = x + (long long)a.g.nx * (y + (long long)a.g.ny * z);
+                    __nv_bfloat16* o = a.out.ptr + vox * a.out.stride + a.out.c0;
+                    const __nv_bfloat16* mk = a.mask ? a.mask + vox * a.mask_stride + a.mask_c0 : nullptr;
+#pragma unroll
+                    for (int j = 0; j < COUT / 8; ++j) {
+                        float f[8];
+#pragma unroll
+                        for (int e = 0; e < 8; ++e) f[e] = v[8 * j + e] + (a.bias ? __ldg(a.bias + 8 * j + e) : 0.f);
+                        if (a.accumulate) {
+                            uint4 old = *reinterpret_cast<const uint4*>(o + 8 * j);
+                            const __nv_bfloat162* ob = reinterpret_cast<const __nv_bfloat162*>(&old);
+#pragma unroll
+                            for (int e = 0; e < 4; ++e) {
+                                float2 p = __bfloat1622float2(ob[e]);
+                                f[2 * e] += p.x;
+                                f[2 * e + 1] += p.y;
+                            }
+                        }
+                        if (a.relu) {
+#pragma unroll
+                            for (int e = 0; e < 8; ++e) f[e] = fmaxf(f[e], 0.f);
+                        }
+                        if (mk) {
+                            uint4 mv = *reinterpret_cast<const uint4*>(mk + 8 * j);
+                            const __nv_bfloat162* mb = reinterpret_cast<const __nv_bfloat162*>(&mv);
+#pragma unroll
+                            for (int e = 0; e < 4; ++e) {
+                                float2 p = __bfloat1622float2(mb[e]);
+                                if (!(p.x > 0.f)) f[2 * e] = 0.f;
+                                if (!(p.y > 0.f)) f[2 * e + 1] = 0.f;
+                            }
+                        }
+                        uint4 w;
+                        __nv_bfloat162* wb2 = reinterpret_cast<__nv_bfloat162*>(&w);
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) wb2[e] = __floats2bfloat162_rn(f[2 * e], f[2 * e + 1]);
+                        *reinterpret_cast<uint4*>(o + 8 * j) = w;
+                    }
+                }
+            }
+            fence_before_sync();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&t_empty[acc]);
+        }
+    }
+    fence_before_sync();
+    __syncthreads();
+    if (warp == 1) {
+        fence_after_sync();
+        tmem_dealloc(tmem, C::NCOLS);
+    }
+    if (threadIdx.x == 0 && *abort && a.err) atomicExch(a.err, 1);
+}
+
+// [taps][K][N] -> [taps][K/8][N][8]
+__global__ void k_pack_tc(const __nv_bfloat16* src, int taps, int K, int N, __nv_bfloat16* dst)
+{
+    long long total = (long long)taps * K * N;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+        int kk = (int)(i & 7);
+        long long q = i >> 3;
+        int n = (int)(q % N);
+        q /= N;
+        int g = (int)(q % (K / 8));
+        int t = (int)(q / (K / 8));
+        dst[i] = src[((long long)t * K + 8 * g + kk) * N + n];
+    }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            p = nullptr;
+        return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }();
+    return fn;
+}
+
+template <int CIN, int COUT, int TZ>
+cudaError_t launch_cfg(const ConvArgs& a, const __nv_bfloat16* wpack, int* err, cudaStream_t s)
+{
+    using C = Cfg<CIN, COUT, TZ>;
+    static std::once_flag once;
+    static cudaError_t attr = cudaSuccess;
+    std::call_once(once, [] {
+        attr = cudaFuncSetAttribute(k_conv3_tc<CIN, COUT, TZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+    });
+    if (attr != cudaSuccess) return attr;
+    auto enc = encode_fn();
+    if (!enc) return cudaErrorNotSupported;
+    const Grid3 g = a.gin;
+    CUtensorMap m;
+    cuuint64_t dims[5] = {8, (cuuint64_t)(CIN / 8), (cuuint64_t)g.nx, (cuuint64_t)g.ny, (cuuint64_t)g.nz};
+    const cuuint64_t vb = (cuuint64_t)a.in.stride * 2;
+    cuuint64_t strides[4] = {16, vb, vb * g.nx, vb * g.nx * g.ny};
+    cuuint32_t box[5] = {8, 1, HX, HY, (cuuint32_t)(TZ + 2)};
+    cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+    CUresult r = enc(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, (void*)(a.in.ptr + a.in.c0), dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+    TcArgs t;
+    t.g = g;
+    t.out = a.out;
+    t.wpack = wpack;
+    t.bias = a.bias;
+    t.relu = a.relu;
+    t.accumulate = a.accumulate;
+    t.mask = a.mask;
+    t.mask_stride = a.mask_stride;
+    t.mask_c0 = a.mask_c0;
+    t.tiles_x = (g.nx + TX - 1) / TX;
+    t.tiles_y = (g.ny + TY - 1) / TY;
+    const int tiles_z = (g.nz + TZ - 1) / TZ;
+    t.ntiles = t.tiles_x * t.tiles_y * tiles_z;
+    t.err = err;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int blocks = std::max(1, std::min(t.ntiles, sms));
+    k_conv3_tc<CIN, COUT, TZ><<<blocks, TC_THREADS, C::SMEM, s>>>(m, t);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+bool conv3_tc_supported(int cin, int cout)
+{
+    return (cin == 16 && (cout == 16 || cout == 32)) || (cin == 32 && (cout == 16 || cout == 32 || cout == 64)) ||
+           (cin == 64 && cout == 32);
+}
+
+cudaError_t pack_conv3_tc(const __nv_bfloat16* w, int cin, int cout, __nv_bfloat16* wpack, cudaStream_t s)
+{
+    long long n = 27LL * cin * cout;
+    k_pack_tc<<<(unsigned)std::min<long long>((n + 255) / 256, 4096), 256, 0, s>>>(w, 27, cin, cout, wpack);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_conv3_tc(const ConvArgs& a, const __nv_bfloat16* wpack, int* err, cudaStream_t s)
+{
+    if (a.mode != CONV3 || a.in.c0 % 8 || a.in.stride % 8 || a.out.c0 % 8 || a.out.stride % 8 ||
+        (a.mask && (a.mask_c0 % 8 || a.mask_stride % 8)))
+        return cudaErrorInvalidValue;
+    if (a.cin == 16 && a.cout == 16) return launch_cfg<16, 16, 8>(a, wpack, err, s);
+    if (a.cin == 16 && a.cout == 32) return launch_cfg<16, 32, 8>(a, wpack, err, s);
+    if (a.cin == 32 && a.cout == 16) return launch_cfg<32, 16, 8>(a, wpack, err, s);
+    if (a.cin == 32 && a.cout == 32) return launch_cfg<32, 32, 8>(a, wpack, err, s);
+    if (a.cin == 64 && a.cout == 32) return launch_cfg<64, 32, 8>(a, wpack, err, s);
+    if (a.cin == 32 && a.cout == 64) return launch_cfg<32, 64, 4>(a, wpack, err, s);
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace unet
+}  // namespace ocmc

@@ -1,0 +1,23 @@
+// ocmc_unet_tc.h -- host entry points of the tcgen05 3x3x3 convolution (ocmc_unet_tc.cu).
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include "ocmc_unet_kernels.cuh"
+
+namespace ocmc {
+namespace unet {
+
+// Channel counts the tensor-memory kernel covers (its layer weights fit in shared memory).
+bool conv3_tc_supported(int cin, int cout);
+
+// Repack BF16 weights [27][cin][cout] into the kernel's layout [27][cin/8][cout][8].
+cudaError_t pack_conv3_tc(const __nv_bfloat16* w, int cin, int cout, __nv_bfloat16* wpack, cudaStream_t s);
+
+// CONV3 convolution (forward, or data gradient with flipped transposed weights) with the same
+// epilogue semantics as k_conv; the input and output grids are a.gin. err (device int, may be
+// null) is set to 1 if a wait inside the kernel timed out.
+cudaError_t launch_conv3_tc(const ConvArgs& a, const __nv_bfloat16* wpack, int* err, cudaStream_t s);
+
+}  // namespace unet
+}  // namespace ocmc

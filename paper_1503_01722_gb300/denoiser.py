@@ -123,3 +123,158 @@ def time_to_error(engine, net, ph, beam, ref, target=0.01, n0=10_000, factor=mat
             res["denoised"] = {"n": N, "time_s": t_mc + t_dn, "err": e_dn}
         n *= factor
     return res
+
+
+# ---- layer shapes and work ----------------------------------------------------------------
+CHANNELS = (16, 32, 64, 128)
+
+
+def layer_shapes(shape):
+    """(kind, cin, cout, output voxels) of every layer, in the network's order: per encoder
+    level two 3x3x3 convolutions and a 2x2x2 stride-2 convolution, then per decoder level a
+    transposed 2x2x2 convolution and two 3x3x3 convolutions (the first over the concatenated
+    skip). The input has 16 channels (dose, density, zero padding)."""
+    nz, ny, nx = shape
+    vox = [(nz >> l) * (ny >> l) * (nx >> l) for l in range(len(CHANNELS))]
+    out, cin = [], 16
+    for l, c in enumerate(CHANNELS):
+        out += [("conv3", cin, c, vox[l]), ("conv3", c, c, vox[l])]
+        if l < len(CHANNELS) - 1:
+            out.append(("down", c, CHANNELS[l + 1], vox[l + 1]))
+            cin = CHANNELS[l + 1]
+    for l in range(len(CHANNELS) - 2, -1, -1):
+        c = CHANNELS[l]
+        out += [("up", CHANNELS[l + 1], c, vox[l]), ("conv3", 2 * c, c, vox[l]), ("conv3", c, c, vox[l])]
+    return out
+
+
+def forward_flops(shape):
+    """Multiply-add work of one forward pass (2 FLOP per MAC): 27 taps for 3x3x3
+    convolutions, 8 for stride-2 convolutions per coarse voxel, 1 per fine voxel for the
+    transposed convolution, plus the 16-weight head."""
+    taps = {"conv3": 27, "down": 8, "up": 1}
+    f = sum(2 * taps[k] * ci * co * v for k, ci, co, v in layer_shapes(shape))
+    return f + 2 * 16 * shape[0] * shape[1] * shape[2]
+
+
+# ---- the full study -------------------------------------------------------------------------
+def _cases(seeds, shape, voxel, workers=8):
+    import ocmc_inputs as inputs
+    from concurrent.futures import ThreadPoolExecutor
+    with ThreadPoolExecutor(workers) as ex:
+        return list(ex.map(lambda s: inputs.denoiser_case(s, shape, voxel), seeds))
+
+
+def run_study(n_train=200, n_eval=8, lows=(10**5, 10**6, 10**7), n_high=10**8,
+              n_ref=(2 * 10**9, 3 * 10**8), steps=4000, lr=1e-3, shape=(128, 128, 128),
+              voxel=(0.25, 0.25, 0.25), target=0.01, k_sigma=4.0, device=0, seed=1, log=print,
+              weights_out=None):
+    """Generate training pairs on random cases, train the network, then on held-out cases
+    compare plain and denoised Monte Carlo by the wall time each needs to reach `target`
+    against a reference of n_ref histories (photon, electron beams). Returns a report dict."""
+    dev = torch.device("cuda", device)
+    t0 = time.perf_counter()
+    train_cases = _cases([100_000 + seed * 10_000 + k for k in range(n_train)], shape, voxel)
+    eval_cases = _cases([900_000 + seed * 10_000 + k for k in range(n_eval)], shape, voxel)
+    t_cases = time.perf_counter() - t0
+    eng = ocmc.Engine(device)
+    net = ocmc.UNet(shape, device=device, seed=seed)
+    rep = {"shape": list(shape), "voxel_cm": list(voxel), "n_train": n_train, "n_eval": n_eval,
+           "lows": list(lows), "n_high": n_high, "n_ref": list(n_ref), "steps": steps, "target": target,
+           "k_sigma": k_sigma, "t_case_generation_s": t_cases}
+    try:
+        # training data: several input noise levels per case, one target
+        t0 = time.perf_counter()
+        pairs = []
+        for k, (ph, beam) in enumerate(train_cases):
+            eng.create_phantom(ph)
+            eng.set_source(beam)
+            dens = torch.from_numpy(np.ascontiguousarray(ph.density)).to(dev)
+            eng.reset()
+            eng.run(n_high, seed=7 * k + seed)
+            high = _dose(eng, shape, dev)
+            for j, n in enumerate(lows):
+                eng.reset()
+                eng.run(n, seed=7 * k + seed + 1 + j)
+                pairs.append((_dose(eng, shape, dev), dens, high))
+            if (k + 1) % 25 == 0:
+                log(f"pairs: case {k + 1}/{n_train} ({time.perf_counter() - t0:.0f} s)")
+        torch.cuda.synchronize()
+        rep["t_pairs_s"] = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        losses = train(net, pairs, steps, lr=lr, seed=seed, log_every=max(steps // 10, 1), log=log)
+        torch.cuda.synchronize()
+        rep["t_train_s"] = time.perf_counter() - t0
+        rep["loss_first_100"] = float(np.mean(losses[:100]))
+        rep["loss_last_100"] = float(np.mean(losses[-100:]))
+        del pairs
+        if weights_out:
+            np.save(weights_out, net.params())
+        # evaluation on held-out cases
+        rows = []
+        for k, (ph, beam) in enumerate(eval_cases):
+            eng.create_phantom(ph)
+            eng.set_source(beam)
+            eng.reset()
+            nr = n_ref[0] if beam.particle == 0 else n_ref[1]
+            t1 = time.perf_counter()
+            eng.run(nr, seed=99_991 + k)
+            ref = _dose(eng, shape, dev)
+            sig = torch.empty_like(ref)
+            eng.dose(out=(ref, sig))
+            m = ref.max()
+            sel = ref >= 0.1 * m
+            ref_err = float(sig[sel].mean() / m * math.sqrt(2 / math.pi))
+            t_ref = time.perf_counter() - t1
+            r = time_to_error(eng, net, ph, beam, ref, target=target, k_sigma=k_sigma, seed=31 + k,
+                              device=device)
+            row = {"particle": "photon" if beam.particle == 0 else "electron",
+                   "energy_MeV": float(beam.edges[0]) if beam.particle == 1 else "6MV",
+                   "field_cm": [round(v, 2) for v in beam.field], "n_ref": nr, "t_ref_s": t_ref,
+                   "ref_err_est": ref_err, "plain": r["plain"], "denoised": r["denoised"],
+                   "curve": r["curve"]}
+            if r["plain"] and r["denoised"]:
+                row["speedup"] = r["plain"]["time_s"] / r["denoised"]["time_s"]
+            rows.append(row)
+            log(f"eval {k}: {row['particle']} field {row['field_cm']} plain {r['plain']} denoised {r['denoised']}")
+        rep["cases"] = rows
+        tp = [r["plain"]["time_s"] for r in rows if r["plain"]]
+        td = [r["denoised"]["time_s"] for r in rows if r["denoised"]]
+        rep["median_time_plain_s"] = float(np.median(tp)) if tp else None
+        rep["median_time_denoised_s"] = float(np.median(td)) if td else None
+        sp = [r["speedup"] for r in rows if "speedup" in r]
+        rep["median_speedup"] = float(np.median(sp)) if sp else None
+    finally:
+        net.close()
+        eng.close()
+    return rep
+
+
+def main(argv=None):
+    import argparse
+    import json
+    ap = argparse.ArgumentParser(description="train the dose denoiser on engine-made pairs and compare "
+                                             "plain and denoised Monte Carlo by time to a target error")
+    ap.add_argument("--train", type=int, default=200)
+    ap.add_argument("--eval", type=int, default=8)
+    ap.add_argument("--steps", type=int, default=4000)
+    ap.add_argument("--n-high", type=float, default=1e8)
+    ap.add_argument("--grid", type=int, default=128)
+    ap.add_argument("--voxel", type=float, default=0.25)
+    ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--weights-out", default=None)
+    ap.add_argument("--report", default=None)
+    a = ap.parse_args(argv)
+    g = a.grid
+    rep = run_study(n_train=a.train, n_eval=a.eval, n_high=int(a.n_high), steps=a.steps, lr=a.lr,
+                    shape=(g, g, g), voxel=(a.voxel,) * 3, weights_out=a.weights_out,
+                    log=lambda m: print(m, flush=True))
+    s = json.dumps(rep)
+    if a.report:
+        with open(a.report, "w") as f:
+            f.write(s)
+    print(json.dumps({k: v for k, v in rep.items() if k != "cases"}))
+
+
+if __name__ == "__main__":
+    main()

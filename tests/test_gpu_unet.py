@@ -21,7 +21,7 @@ def rel_l2(a, b):
     return float(np.linalg.norm(np.ravel(a) - np.ravel(b)) / max(np.linalg.norm(np.ravel(b)), 1e-30))
 
 
-CASES = [(0, 16, 16), (0, 32, 16), (0, 16, 32), (0, 64, 128), (0, 128, 64),
+CASES = [(0, 16, 16), (0, 32, 16), (0, 16, 32), (0, 32, 32), (0, 64, 32), (0, 32, 64), (0, 64, 128), (0, 128, 64),
          (1, 16, 32), (1, 32, 64), (1, 64, 128), (2, 128, 64), (2, 64, 32), (2, 32, 16)]
 
 
@@ -48,6 +48,48 @@ def test_layer_matches_oracle(ocmc, mode, cin, cout):
     assert np.allclose(dx, dxr, rtol=8e-3, atol=1e-2 * np.abs(dxr).max())
     assert rel_l2(y, yr) < 4e-3 and rel_l2(dx, dxr) < 4e-3
     assert np.allclose(dw, dwr, rtol=1e-4, atol=1e-4 * np.abs(dwr).max())
+
+
+@pytest.mark.parametrize("cin,cout", [(16, 16), (32, 64), (64, 32)])
+def test_conv3_large_grid(ocmc, cin, cout):
+    """A grid of 480+ output tiles, so every block of the persistent tensor-memory kernel runs
+    several tiles (both accumulator sets, every halo stage reused)."""
+    rng = np.random.default_rng(cin * 7 + cout)
+    fine = (48, 80, 128)
+    x = U.bf16(rng.standard_normal(fine + (cin,)))
+    W = U.bf16(rng.standard_normal((27, cin, cout)) / np.sqrt(27 * cin))
+    dy = U.bf16(rng.standard_normal(fine + (cout,)))
+    y, dx, dw = ocmc.unet_test_layer(0, fine, cin, cout, x, W, dy)
+    yr, dxr = U.conv3(x, W), U.conv3_dx(dy, W)
+    assert np.allclose(y, yr, rtol=8e-3, atol=1e-2 * np.abs(yr).max())
+    assert np.allclose(dx, dxr, rtol=8e-3, atol=1e-2 * np.abs(dxr).max())
+    dwr = U.conv3_dw(x, dy)
+    assert np.allclose(dw, dwr, rtol=1e-4, atol=1e-4 * np.abs(dwr).max())
+
+
+def test_tensor_memory_path_matches_mma_path(ocmc, monkeypatch):
+    """The network with its 3x3x3 convolutions on tcgen05 and with every layer on mma.sync:
+    the same arithmetic in a different summation order (outputs and gradients agree to BF16
+    rounding)."""
+    import torch
+    shape = (32, 32, 32)
+    dose, dens, target = random_case(shape, 13)
+    td, tr, tt = (torch.from_numpy(a).cuda() for a in (dose, dens, target))
+    res = []
+    for mode in ("tc", "mma"):
+        if mode == "mma":
+            monkeypatch.setenv("OCMC_UNET_KERNELS", "mma")
+        net = ocmc.UNet(shape, seed=21)
+        p = net.params()
+        p[-17:-1] = np.random.default_rng(5).standard_normal(16) * 0.2
+        net.set_params(p)
+        out = torch.empty_like(td)
+        net.forward(td, tr, out)
+        net.train_step(td, tr, tt, lr=0.0)
+        res.append((out.cpu().numpy(), net.params(grads=True)))
+        net.close()
+    assert rel_l2(res[0][0], res[1][0]) < 1e-2
+    assert rel_l2(res[0][1], res[1][1]) < 0.1
 
 
 def random_case(shape, seed):
