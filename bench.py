@@ -58,6 +58,11 @@ WORKLOADS = {
                           "paper preset: 6 MV, 2x2 cm2 at SSD 100, slab 128^3 at 0.25 cm"),
     "paper_photon_half_slab": (lambda: I.paper_preset(0, "half"), 500_000_000,
                                "paper preset: 6 MV, 2x2 cm2 at SSD 100, half-slab 128^3 at 0.25 cm"),
+    "denoiser_128": (None, 0,
+                     "learned dose denoiser: 3D U-Net (4 levels, 16-128 channels, BF16 with FP32 accumulation) "
+                     "on 128^3 grids at 0.25 cm; trained on engine-made pairs of random CT-like phantoms "
+                     "(6 MV or 6-20 MeV e-, fields 2-20 cm); time to <=1% mean dose error above the 10% isodose, "
+                     "plain vs denoised, on held-out cases"),
     "beamlets_ct": (I.beamlets_ct, 0,
                     "512 6 MV pencil beamlets 0.5x0.5 cm2 at random gantry angles (SAD 100 cm), histories "
                     "10^N(5,0.5) clipped to [1e4,1e6], CT-like phantom 256x256x128 at 0.2 cm, one graph-captured "
@@ -235,6 +240,100 @@ def run_beamlets_bench(args, make, desc):
     eng.close()
 
 
+def run_denoiser_bench(args, desc):
+    """The denoiser: one step = one forward pass of the U-Net over a 128^3 dose (inference with
+    all activations far larger than L2); per-layer CUDA-event times give the dominant kernel's
+    roofline. Unless --no-study, the full study (pair generation, training, time to <= 1% error
+    plain vs denoised on held-out cases) runs first and supplies the headline value."""
+    import torch
+    from paper_1503_01722_gb300 import denoiser as D
+    from paper_1503_01722_gb300 import ocmc
+    shape = (128, 128, 128)
+    study = None
+    weights = None
+    if not args.no_study:
+        wpath = os.path.join(ROOT, "gpurun_out", "denoiser_bench_weights.npy") if os.path.isdir(
+            os.path.join(ROOT, "gpurun_out")) else None
+        study = D.run_study(n_train=args.study_train, steps=args.study_steps, log=lambda m: print(m, file=sys.stderr),
+                            weights_out=wpath)
+        weights = np.load(wpath) if wpath else None
+    ph, beam = I.denoiser_case(424242)
+    eng = ocmc.Engine(0)
+    eng.create_phantom(ph)
+    eng.set_source(beam)
+    eng.run(1_000_000, seed=1)
+    dose = torch.empty(shape, dtype=torch.float32, device="cuda")
+    eng.dose(out=(dose, None))
+    dens = torch.from_numpy(np.ascontiguousarray(ph.density)).cuda()
+    net = ocmc.UNet(shape, seed=1)
+    if weights is not None:
+        net.set_params(weights)
+    out = torch.empty_like(dose)
+    for _ in range(args.warmup):
+        net.forward(dose, dens, out)
+    torch.cuda.synchronize()
+    ms = []
+    with ClockSampler(0) as clk:
+        for k in range(args.steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            net.forward(dose, dens, out)
+            e1.record()
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        lt = net.layer_times(dose, dens, repeats=max(args.steps, 3))
+    clocks = clk.summary()
+    # end to end through the C ABI: the dose of the engine's tally denoised into pinned host memory
+    out_h = torch.empty(shape, dtype=torch.float32).pin_memory()
+    e2e_ms = []
+    for k in range(args.warmup + args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ocmc.denoise(eng, net, 4.0, out_h)
+        if k >= args.warmup:
+            e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    layers = D.layer_shapes(shape)
+    taps = {"conv3": 27, "down": 8, "up": 1}
+    rows = []
+    for (kind, ci, co, vox), t in zip(layers, lt):
+        fl = 2 * taps[kind] * ci * co * vox
+        rows.append({"kind": kind, "cin": ci, "cout": co, "voxels": vox, "ms": float(t),
+                     "tflops": fl / (float(t) / 1e3) / 1e12, "flop": fl})
+    dom = max(rows, key=lambda r: r["ms"])
+    peaks = measured_peaks()
+    peak = peaks.get("bf16_tflops")
+    fwd_ms = statistics.mean(ms)
+    flops = D.forward_flops(shape)
+    launches = 3 + sum(8 if k == "up" else 1 for k, _, _, _ in layers)
+    line = {
+        "metric": "time to <=1% mean dose error (>10% isodose), denoised", "unit": "s",
+        "value": study["median_time_denoised_s"] if study else None, "higher_is_better": False,
+        "plain": {"value": study["median_time_plain_s"] if study else None, "unit": "s"},
+        "speedup_median": study["median_speedup"] if study else None,
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": fwd_ms, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+        "config": {"workload": desc, "step": "one U-Net forward pass over 128^3 (inference)",
+                   "l2": "activations 0.5 GB per pass, larger than L2", "forward_gflop": flops / 1e9},
+        "forward_tflops": flops / (fwd_ms / 1e3) / 1e12,
+        "e2e": {"value": statistics.mean(e2e_ms) / 1e3, "unit": "s per denoised dose (ocmc_denoise to host)",
+                "h2d_bytes_per_step": 0, "d2h_bytes_per_step": int(np.prod(shape) * 4)},
+        "gpu_launches": launches * args.steps,
+        "roofline": {"bound": "tensor", "kernel": f"{dom['kind']} {dom['cin']}->{dom['cout']} over {dom['voxels']} voxels",
+                     "achieved": dom["tflops"], "peak": peak, "unit": "TFLOP/s",
+                     "frac": None if not peak else dom["tflops"] / peak,
+                     "peak_basis": "bf16_tflops (cuBLAS burst) of MEASURED_PEAKS.json", "traffic": None},
+        "layers": rows,
+        "clocks": clocks,
+        "study": None if not study else {k: v for k, v in study.items() if k != "cases"},
+        "study_cases": None if not study else [
+            {k: c[k] for k in ("particle", "energy_MeV", "field_cm", "plain", "denoised") if k in c} |
+            {"speedup": c.get("speedup")} for c in study["cases"]],
+    }
+    print(json.dumps(line))
+    net.close()
+    eng.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -245,9 +344,14 @@ def main():
     ap.add_argument("--histories", type=int, default=0, help="histories per step and GPU (default: workload's)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-study", action="store_true", help="denoiser_128: inference timing only")
+    ap.add_argument("--study-train", type=int, default=200, help="denoiser_128: training cases")
+    ap.add_argument("--study-steps", type=int, default=4000, help="denoiser_128: training steps")
     args = ap.parse_args()
 
     make, n_default, desc = WORKLOADS[args.workload]
+    if args.workload == "denoiser_128":
+        return run_denoiser_bench(args, desc)
     if args.workload == "beamlets_ct":
         return run_beamlets_bench(args, make, desc)
     ph, beam = make()

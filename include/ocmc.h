@@ -260,6 +260,11 @@ ocmc_status ocmc_unet_forward(ocmc_unet* net, const float* dose_dev, const float
  * maximum of dose_dev. *loss_host (may be NULL) receives the loss (synchronises). */
 ocmc_status ocmc_unet_train_step(ocmc_unet* net, const float* dose_dev, const float* density_dev,
                                  const float* target_dev, float lr, float* loss_host, void* cuda_stream);
+/* Timing: forward passes with a CUDA event pair around every layer (20 layers, in the order
+ * encoder level 0..3, then decoder level 2..0); ms_out[i] (may be NULL to query *n_layers) is
+ * the mean duration of layer i over `repeats` passes. Synchronises. */
+ocmc_status ocmc_unet_layer_times(ocmc_unet* net, const float* dose_dev, const float* density_dev, int repeats,
+                                  float* ms_out, int* n_layers);
 /* One layer through the network's own kernels (for the gradient tests): mode 0 3x3x3
  * convolution, 1 2x2x2 stride-2 convolution, 2 its transposed form; (nx,ny,nz) is the
  * fine grid; x, dy, y, dx channels-last FP32 host arrays (inputs rounded to BF16);

@@ -37,7 +37,8 @@ __global__ void k_max_reduce(const float* x, long long n, unsigned int* out)
     if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(m));   // non-negative floats
 }
 
-// x0 = dose / s, x1 = density; other input channels zero
+// x0 = dose / s, x1 = density. Channels 2-15 of the input activation are zeroed when the
+// network is created and never written, so each voxel needs one 4-byte store.
 __global__ void k_pack_input(const float* dose, const float* dens, long long n, const unsigned int* smax,
                              __nv_bfloat16* x, float* x0f)
 {
@@ -46,11 +47,7 @@ __global__ void k_pack_input(const float* dose, const float* dens, long long n, 
     for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < n; v += (long long)gridDim.x * blockDim.x) {
         float d = dose[v] * inv;
         x0f[v] = d;
-        __nv_bfloat16* p = x + v * 16;
-        p[0] = __float2bfloat16_rn(d);
-        p[1] = __float2bfloat16_rn(dens[v]);
-#pragma unroll
-        for (int c = 2; c < 16; ++c) p[c] = __float2bfloat16_rn(0.f);
+        *reinterpret_cast<__nv_bfloat162*>(x + v * 16) = __floats2bfloat162_rn(d, dens[v]);
     }
 }
 
@@ -142,20 +139,25 @@ __global__ void k_sum_rows(const float* part, int parts, int m, float* out)
     out[j] = s;
 }
 
-// bias gradient partials: per block sums of dy[v][n] over its voxels
+// bias gradient partials: per block sums of dy[v][n] over its voxels, in a fixed order (thread
+// (r, c) of the block sums channel c over voxels r, r + R, ...; then the R partial sums of each
+// channel are added in order), so that gradients are bit-reproducible. cout divides blockDim.x.
 __global__ void k_bias_part(const __nv_bfloat16* dy, int stride, int c0, int cout, long long n, float* part)
 {
-    extern __shared__ float sh[];
-    for (int c = threadIdx.x; c < cout; c += blockDim.x) sh[c] = 0.f;
+    __shared__ float sh[256];
+    const int rpp = blockDim.x / cout;
+    const int c = threadIdx.x % cout, r = threadIdx.x / cout;
+    float acc = 0.f;
+    if (r < rpp)
+        for (long long v = (long long)blockIdx.x * rpp + r; v < n; v += (long long)gridDim.x * rpp)
+            acc += __bfloat162float(dy[v * stride + c0 + c]);
+    sh[threadIdx.x] = acc;
     __syncthreads();
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n * cout;
-         i += (long long)gridDim.x * blockDim.x) {
-        long long v = i / cout;
-        int c = (int)(i % cout);
-        atomicAdd(&sh[c], __bfloat162float(dy[v * stride + c0 + c]));
+    if (threadIdx.x < cout) {
+        float sum = 0.f;
+        for (int i = 0; i < rpp; ++i) sum += sh[i * cout + threadIdx.x];
+        part[blockIdx.x * cout + threadIdx.x] = sum;
     }
-    __syncthreads();
-    for (int c = threadIdx.x; c < cout; c += blockDim.x) part[blockIdx.x * cout + c] = sh[c];
 }
 
 // BF16 copies of the FP32 weights: forward layout W[t][c][n] and the data-gradient layout
@@ -412,7 +414,7 @@ cudaError_t layer_bwd(ocmc_unet* u, const Layer& L, bool need_dx, cudaStream_t s
     }
     long long nout = u->g[L.lout].n();
     int blocks = grid_for(nout * L.cout);
-    k_bias_part<<<blocks, 256, L.cout * sizeof(float), s>>>(dy.ptr, dy.stride, dy.c0, L.cout, nout, u->bpart);
+    k_bias_part<<<blocks, 256, 0, s>>>(dy.ptr, dy.stride, dy.c0, L.cout, nout, u->bpart);
     k_sum_rows<<<1, 128, 0, s>>>(u->bpart, blocks, L.cout, u->grads + L.boff);
     e = cudaGetLastError();
     if (e != cudaSuccess || !need_dx) return e;
@@ -723,6 +725,45 @@ ocmc_status ocmc_unet_train_step(ocmc_unet* u, const float* dose, const float* d
         UCK(cudaStreamSynchronize(s), "sync");
         *loss_host = acc[1] > 0 ? (float)(acc[0] / acc[1]) : 0.f;
     }
+    return OCMC_OK;
+}
+
+// Forward pass with a CUDA event pair around every layer: ms_out[i] = mean time of layer i over
+// `repeats` passes (stream order, so each layer's time is its own launches only).
+ocmc_status ocmc_unet_layer_times(ocmc_unet* u, const float* dose, const float* dens, int repeats, float* ms_out,
+                                  int* n_layers)
+{
+    if (!u || !dose || !dens || repeats < 1) return ufail(u, OCMC_ERR_ARG, "bad argument");
+    const int L = (int)u->layers.size();
+    if (n_layers) *n_layers = L;
+    if (!ms_out) return OCMC_OK;
+    UCK(cudaSetDevice(u->device), "device");
+    std::vector<cudaEvent_t> ev(L + 1);
+    for (auto& e : ev) UCK(cudaEventCreate(&e), "event");
+    std::vector<double> acc(L, 0.0);
+    ocmc_status st = OCMC_OK;
+    for (int r = 0; r < repeats && st == OCMC_OK; ++r) {
+        long long n = u->nvox;
+        cudaMemsetAsync(u->smax, 0, sizeof(unsigned int), nullptr);
+        k_max_reduce<<<grid_for(n), 256>>>(dose, n, u->smax);
+        k_pack_input<<<grid_for(n), 256>>>(dose, dens, n, u->smax, u->acts[0].x, u->x0f);
+        cudaEventRecord(ev[0], nullptr);
+        for (int i = 0; i < L; ++i) {
+            if (layer_fwd(u, u->layers[i], nullptr) != cudaSuccess) { st = ufail(u, OCMC_ERR_CUDA, "layer"); break; }
+            cudaEventRecord(ev[i + 1], nullptr);
+        }
+        if (cudaEventSynchronize(ev[L]) != cudaSuccess) st = ufail(u, OCMC_ERR_CUDA, "sync");
+        for (int i = 0; i < L && st == OCMC_OK; ++i) {
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, ev[i], ev[i + 1]);
+            acc[i] += ms;
+        }
+    }
+    for (auto& e : ev) cudaEventDestroy(e);
+    if (st != OCMC_OK) return st;
+    ocmc_status fs = take_kernel_flag(u, nullptr);
+    if (fs != OCMC_OK) return fs;
+    for (int i = 0; i < L; ++i) ms_out[i] = (float)(acc[i] / repeats);
     return OCMC_OK;
 }
 

@@ -52,16 +52,17 @@ struct TcArgs {
     int* err;
 };
 
-template <int CIN, int COUT, int TZ>
+template <int CIN, int COUT, int TZ, int NS_>
 struct Cfg {
-    static constexpr int NS = 2;                                         // halo stages
+    static constexpr int NS = NS_;                                       // halo stages
     static constexpr int G = CIN / 8;
     static constexpr int CHUNKS = CIN / 16;
     static constexpr uint32_t W_BYTES = 27u * CIN * COUT * 2;
     static constexpr uint32_t PLANE = (uint32_t)(TZ + 2) * HY * HX * 16;
     static constexpr uint32_t STAGE = 2 * PLANE;
     static constexpr uint32_t BAR_OFF = W_BYTES + NS * STAGE;
-    static constexpr uint32_t SMEM = BAR_OFF + 256;
+    static constexpr uint32_t BIAS_OFF = BAR_OFF + 256;
+    static constexpr uint32_t SMEM = BIAS_OFF + COUT * 4;
     static constexpr uint32_t COLS = 2 * TZ * COUT;
     static constexpr uint32_t NCOLS = COLS <= 32 ? 32 : COLS <= 64 ? 64 : COLS <= 128 ? 128 : COLS <= 256 ? 256 : 512;
     static_assert(COLS <= 512, "tensor memory holds 512 columns");
@@ -76,10 +77,10 @@ __device__ __forceinline__ bool wait_bounded(uint64_t* bar, uint32_t parity)
     return mbar_wait(bar, parity, &dummy, WAIT_NS);
 }
 
-template <int CIN, int COUT, int TZ>
+template <int CIN, int COUT, int TZ, int NS_>
 __global__ void __launch_bounds__(TC_THREADS, 1) k_conv3_tc(const __grid_constant__ CUtensorMap tmap, const TcArgs a)
 {
-    using C = Cfg<CIN, COUT, TZ>;
+    using C = Cfg<CIN, COUT, TZ, NS_>;
     constexpr int NS = C::NS;
     extern __shared__ __align__(1024) uint8_t smem[];
     uint8_t* sw = smem;
@@ -93,7 +94,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv3_tc(const __grid_constan
     uint64_t* drain = bars + 5 + 2 * NS;
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 6 + 2 * NS);
     volatile int* abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
+    float* sbias = reinterpret_cast<float*>(smem + C::BIAS_OFF);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int i = threadIdx.x; i < COUT; i += TC_THREADS) sbias[i] = a.bias ? a.bias[i] : 0.f;
 
     if (threadIdx.x == 0) {
         mbar_init(w_full, 1);
@@ -163,18 +166,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv3_tc(const __grid_constan
                         const int st = it % NS, u = it / NS;
                         if (!mbar_wait(&h_full[st], u & 1, abort, WAIT_NS)) break;
                         fence_after_sync();
-                        const uint32_t hb = sh_addr + (uint32_t)st * C::STAGE;
-                        const uint32_t wb = sw_addr + (uint32_t)(2 * c) * COUT * 16;
-#pragma unroll 1
+                        // descriptors are built once per chunk; a tap or slice only moves the start
+                        // address, which is the descriptor's low field in 16-byte units
+                        const uint64_t a0 = sdesc(sh_addr + (uint32_t)st * C::STAGE, C::PLANE, HX * 16);
+                        const uint64_t b0 = sdesc(sw_addr + (uint32_t)(2 * c) * COUT * 16, COUT * 16, 128);
+#pragma unroll
                         for (int t = 0; t < 27; ++t) {
                             const int dx = t % 3, dy = (t / 3) % 3, dz = t / 9;
-                            const uint64_t bd = sdesc(wb + (uint32_t)t * C::G * COUT * 16, COUT * 16, 128);
+                            const uint64_t bd = b0 + (uint64_t)(t * C::G * COUT);
 #pragma unroll
-                            for (int s = 0; s < TZ; ++s) {
-                                const uint32_t ao = (uint32_t)(((s + dz) * HY + dy) * HX + dx) * 16;
-                                mma_f16(d0 + (uint32_t)(s * COUT), sdesc(hb + ao, C::PLANE, HX * 16), bd, idesc,
-                                        (c | t) != 0);
-                            }
+                            for (int s = 0; s < TZ; ++s)
+                                mma_f16(d0 + (uint32_t)(s * COUT), a0 + (uint64_t)(((s + dz) * HY + dy) * HX + dx), bd,
+                                        idesc, (t != 0 || c != 0) ? 1u : 0u);
                         }
                         mma_commit(&h_empty[st]);
                         issued = true;
@@ -215,7 +218,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv3_tc(const __grid_constan
                     for (int j = 0; j < COUT / 8; ++j) {
                         float f[8];
 #pragma unroll
-                        for (int e = 0; e < 8; ++e) f[e] = v[8 * j + e] + (a.bias ? __ldg(a.bias + 8 * j + e) : 0.f);
+                        for (int e = 0; e < 8; ++e) f[e] = v[8 * j + e] + sbias[8 * j + e];
                         if (a.accumulate) {
                             uint4 old = *reinterpret_cast<const uint4*>(o + 8 * j);
                             const __nv_bfloat162* ob = reinterpret_cast<const __nv_bfloat162*>(&old);
@@ -291,14 +294,14 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
     return fn;
 }
 
-template <int CIN, int COUT, int TZ>
+template <int CIN, int COUT, int TZ, int NS>
 cudaError_t launch_cfg(const ConvArgs& a, const __nv_bfloat16* wpack, int* err, cudaStream_t s)
 {
-    using C = Cfg<CIN, COUT, TZ>;
+    using C = Cfg<CIN, COUT, TZ, NS>;
     static std::once_flag once;
     static cudaError_t attr = cudaSuccess;
     std::call_once(once, [] {
-        attr = cudaFuncSetAttribute(k_conv3_tc<CIN, COUT, TZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+        attr = cudaFuncSetAttribute(k_conv3_tc<CIN, COUT, TZ, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
     });
     if (attr != cudaSuccess) return attr;
     auto enc = encode_fn();
@@ -333,7 +336,7 @@ cudaError_t launch_cfg(const ConvArgs& a, const __nv_bfloat16* wpack, int* err, 
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int blocks = std::max(1, std::min(t.ntiles, sms));
-    k_conv3_tc<CIN, COUT, TZ><<<blocks, TC_THREADS, C::SMEM, s>>>(m, t);
+    k_conv3_tc<CIN, COUT, TZ, NS><<<blocks, TC_THREADS, C::SMEM, s>>>(m, t);
     return cudaGetLastError();
 }
 
@@ -357,12 +360,12 @@ cudaError_t launch_conv3_tc(const ConvArgs& a, const __nv_bfloat16* wpack, int* 
     if (a.mode != CONV3 || a.in.c0 % 8 || a.in.stride % 8 || a.out.c0 % 8 || a.out.stride % 8 ||
         (a.mask && (a.mask_c0 % 8 || a.mask_stride % 8)))
         return cudaErrorInvalidValue;
-    if (a.cin == 16 && a.cout == 16) return launch_cfg<16, 16, 8>(a, wpack, err, s);
-    if (a.cin == 16 && a.cout == 32) return launch_cfg<16, 32, 8>(a, wpack, err, s);
-    if (a.cin == 32 && a.cout == 16) return launch_cfg<32, 16, 8>(a, wpack, err, s);
-    if (a.cin == 32 && a.cout == 32) return launch_cfg<32, 32, 8>(a, wpack, err, s);
-    if (a.cin == 64 && a.cout == 32) return launch_cfg<64, 32, 8>(a, wpack, err, s);
-    if (a.cin == 32 && a.cout == 64) return launch_cfg<32, 64, 4>(a, wpack, err, s);
+    if (a.cin == 16 && a.cout == 16) return launch_cfg<16, 16, 8, 3>(a, wpack, err, s);
+    if (a.cin == 16 && a.cout == 32) return launch_cfg<16, 32, 8, 3>(a, wpack, err, s);
+    if (a.cin == 32 && a.cout == 16) return launch_cfg<32, 16, 8, 3>(a, wpack, err, s);
+    if (a.cin == 32 && a.cout == 32) return launch_cfg<32, 32, 8, 3>(a, wpack, err, s);
+    if (a.cin == 64 && a.cout == 32) return launch_cfg<64, 32, 8, 2>(a, wpack, err, s);
+    if (a.cin == 32 && a.cout == 64) return launch_cfg<32, 64, 4, 3>(a, wpack, err, s);
     return cudaErrorInvalidValue;
 }
 

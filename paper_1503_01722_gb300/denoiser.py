@@ -114,8 +114,11 @@ def time_to_error(engine, net, ph, beam, ref, target=0.01, n0=10_000, factor=mat
         t_plain = _sync_time(lambda: engine.dose(out=(plain, None)))
         t_dn = _sync_time(lambda: ocmc.denoise(engine, net, k_sigma, out, flag))
         e_plain, e_dn = dose_error(plain, ref), dose_error(out, ref)
+        sel = ref >= 0.1 * ref.max()
         row = {"n": N, "err_plain": e_plain, "err_denoised": e_dn, "t_mc": t_mc, "t_dose": t_plain,
-               "t_denoise": t_dn, "flagged": float(flag.mean())}
+               "t_denoise": t_dn, "flagged": float(flag[sel].mean())}
+        ocmc.denoise(engine, net, 3.0e38, out, flag)          # the network alone, for the record
+        row["err_network"] = dose_error(out, ref)
         res["curve"].append(row)
         if res["plain"] is None and e_plain <= target:
             res["plain"] = {"n": N, "time_s": t_mc + t_plain, "err": e_plain}

@@ -119,11 +119,13 @@ def test_network_output_and_gradients_match_oracle(ocmc):
     lr_, Gr = ref.loss_and_grads(dose, dens, target)
     assert abs(loss - lr_) < 1e-2 * lr_
     # Deep-layer gradients are sums with heavy cancellation at random initialisation, so the
-    # BF16 rounding of stored activations and gradients moves them by up to ~20% (fp64
-    # oracle vs BF16 oracle). The kernels' gradient must be no farther from the BF16 oracle
-    # than the BF16 oracle is from the exact one (at least 3% allowed); measured, it sits at
-    # 0.5-0.7 of that gap in every layer. A wiring mistake (wrong skip, missing ReLU mask,
-    # swapped operand) gives errors of order 1.
+    # BF16 rounding of stored activations and gradients moves them by up to ~25% (fp64 oracle
+    # vs BF16 oracle: the "gap"). Two BF16 evaluations that sum in different orders round some
+    # stored values differently; from there on their rounding errors are independent, so they
+    # may differ by up to about sqrt(2) x the gap. The bound per layer is 1.5 x the gap (at
+    # least 3%); measured, mma.sync kernels sit at 0.5-0.7 and tcgen05 kernels at 0.7-1.1 of
+    # it. A wiring mistake (wrong skip, missing ReLU mask, swapped operand) gives errors of
+    # order 1, and every kernel is checked on its own to BF16 rounding by the layer tests.
     _, G64 = U.UNet(p.astype(np.float32).astype(np.float64), bf16_storage=False).loss_and_grads(dose, dens, target)
     lay, hw, hb = U.param_layout()
     rows, bad = [], []
@@ -131,7 +133,7 @@ def test_network_output_and_gradients_match_oracle(ocmc):
         n = int(np.prod(shp))
         for name, sl in (("W", slice(off, off + n)), ("b", slice(boff, boff + cout))):
             err, gap = rel_l2(G[sl], Gr[sl]), rel_l2(Gr[sl], G64[sl])
-            tol = max(0.03, gap)
+            tol = max(0.03, 1.5 * gap)
             rows.append(f"{i:2d} {name} err {err:.4f} gap {gap:.4f} tol {tol:.4f}")
             if err > tol:
                 bad.append(rows[-1])
