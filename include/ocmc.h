@@ -273,8 +273,10 @@ ocmc_status ocmc_unet_test_layer(int device, int mode, int nx, int ny, int nz, i
                                  const float* x_host, const float* w_host, const float* dy_host, float* y_host,
                                  float* dx_host, float* dw_host);
 /* Denoise the context's current dose with the network; where the denoised value
- * differs from the plain Monte Carlo value by more than k_sigma of its batch sigma
- * the plain value is kept and flag_out (may be NULL) is 1. */
+ * differs from the plain Monte Carlo value by more than k_sigma times the plain dose's
+ * batch standard error (pooled over the voxel's 3x3x3 neighbourhood: root of the mean
+ * variance) the plain value is kept and flag_out (may be NULL) is 1. dose_out and
+ * flag_out hold nx*ny*nz floats, on the device if on_device, else in host memory. */
 ocmc_status ocmc_denoise(ocmc_ctx* ctx, ocmc_unet* net, float k_sigma, float* dose_out, float* flag_out,
                          int on_device);
 

@@ -491,12 +491,29 @@ __global__ void k_denorm(const float* out, const unsigned int* smax, long long n
         dst[v] = out[v] * sc;
 }
 
-// Fallback to plain Monte Carlo where the network's change exceeds k sigma of the
-// plain estimate: out = flag ? plain : denoised.
-__global__ void k_fallback(const float* plain, const float* sigma, float* den, float* flag, float k, long long n)
+// Fallback to plain Monte Carlo where the network's change exceeds k sigma of the plain
+// estimate: out = flag ? plain : denoised. sigma is the batch standard error pooled over the
+// voxel's 3x3x3 neighbourhood (root of the mean of the neighbours' variances, clipped at the
+// grid's faces): with few batches the per-voxel estimate is itself noisy, and it is exactly
+// zero wherever no batch deposited anything, which would make any denoised value there fail.
+__global__ void k_fallback(const float* plain, const float* sigma, float* den, float* flag, float k, int nx, int ny,
+                           int nz)
 {
+    const long long n = (long long)nx * ny * nz;
     for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < n; v += (long long)gridDim.x * blockDim.x) {
-        bool f = fabsf(den[v] - plain[v]) > k * sigma[v];
+        const int x = (int)(v % nx), y = (int)((v / nx) % ny), z = (int)(v / ((long long)nx * ny));
+        float s2 = 0.f;
+        int cnt = 0;
+        for (int dz = -1; dz <= 1; ++dz)
+            for (int dy = -1; dy <= 1; ++dy)
+                for (int dx = -1; dx <= 1; ++dx) {
+                    const int xx = x + dx, yy = y + dy, zz = z + dz;
+                    if (xx < 0 || yy < 0 || zz < 0 || xx >= nx || yy >= ny || zz >= nz) continue;
+                    const float sg = sigma[xx + (long long)nx * (yy + (long long)ny * zz)];
+                    s2 = __fadd_rn(s2, __fmul_rn(sg, sg));     // no contraction: reproducible on the host
+                    ++cnt;
+                }
+        const bool f = fabsf(__fsub_rn(den[v], plain[v])) > __fmul_rn(k, sqrtf(__fdiv_rn(s2, (float)cnt)));
         if (flag) flag[v] = f ? 1.f : 0.f;
         if (f) den[v] = plain[v];
     }
@@ -875,7 +892,7 @@ ocmc_status ocmc_denoise(ocmc_ctx* c, ocmc_unet* u, float k_sigma, float* dose_o
     if (st == OCMC_OK || st == OCMC_ERR_OVERFLOW || st == OCMC_ERR_TIMEOUT) {
         ocmc_status s2 = ocmc_unet_forward(u, dd, c->d_density, dout, nullptr);
         if (s2 == OCMC_OK) {
-            k_fallback<<<grid_for(n), 256>>>(dd, ds, dout, dflag, k_sigma, n);
+            k_fallback<<<grid_for(n), 256>>>(dd, ds, dout, dflag, k_sigma, u->g[0].nx, u->g[0].ny, u->g[0].nz);
             e = cudaGetLastError();
             if (e == cudaSuccess && !on_device) e = cudaMemcpy(dose_out, dout, n * 4, cudaMemcpyDeviceToHost);
             if (e == cudaSuccess && !on_device && flag_out) e = cudaMemcpy(flag_out, dflag, n * 4, cudaMemcpyDeviceToHost);

@@ -195,3 +195,28 @@ def test_denoise_fallback(ocmc):
         ref = torch.empty_like(out)
         net.forward(torch.from_numpy(D).cuda(), torch.from_numpy(ph.density).cuda(), ref)
         assert flag.sum().item() == 0 and torch.equal(out, ref)
+        # moderate k: the rule itself, |denoised - plain| > k * pooled sigma, with sigma pooled
+        # as the root of the mean variance over the 3x3x3 neighbourhood (float32, same order)
+        r = ref.cpu().numpy()
+        S2 = (S.astype(np.float32) ** 2).astype(np.float32)
+        nz, ny, nx = S2.shape
+        pad = np.zeros((nz + 2, ny + 2, nx + 2), np.float32)
+        pad[1:-1, 1:-1, 1:-1] = S2
+        one = np.zeros_like(pad)
+        one[1:-1, 1:-1, 1:-1] = 1
+        s2 = np.zeros_like(S2)
+        cnt = np.zeros_like(S2)
+        for dz in (-1, 0, 1):
+            for dy in (-1, 0, 1):
+                for dx in (-1, 0, 1):
+                    sl = (slice(1 + dz, 1 + dz + nz), slice(1 + dy, 1 + dy + ny), slice(1 + dx, 1 + dx + nx))
+                    s2 = (s2 + pad[sl]).astype(np.float32)
+                    cnt = cnt + one[sl]
+        sig = np.sqrt((s2 / cnt).astype(np.float32))
+        ratio = np.abs(r - D)[sig > 0] / sig[sig > 0]
+        k = np.float32(np.median(ratio))          # a k that splits the voxels
+        ocmc.denoise(e, net, float(k), out, flag)
+        expect = np.abs(r - D) > k * np.sqrt((s2 / cnt).astype(np.float32))
+        f = flag.cpu().numpy() == 1
+        assert 0 < f.sum() < f.size and np.array_equal(f, expect)
+        assert np.array_equal(out.cpu().numpy(), np.where(expect, D, r))
