@@ -99,6 +99,9 @@ def lib():
                                           C.POINTER(d)]),
                 ("orc_run", i, [C.POINTER(_Phantom), C.POINTER(_Source), C.POINTER(Params), u64, u64, u64,
                                 u64, C.POINTER(C.c_int64), C.POINTER(d), C.POINTER(u64)]),
+                ("orc_ps_sample", i, [C.POINTER(_Phantom), C.c_void_p, u64, u64, u64, C.POINTER(d)]),
+                ("orc_run_ps", i, [C.POINTER(_Phantom), C.c_void_p, u64, C.POINTER(Params), u64, u64, u64,
+                                   C.POINTER(C.c_int64), C.POINTER(d), C.POINTER(u64)]),
             ]:
                 f = getattr(L, name)
                 f.restype = res
@@ -296,3 +299,65 @@ def run(ph, beam, n_hist, seed=1, p=None, first=0, count=None, threads=None, n_t
     ledger = sum(p_[1] for p_ in parts)
     cnt = sum(p_[2] for p_ in parts)
     return Result(tally, ledger, cnt, count, ph)
+
+
+# ---- phase-space source (Sec. 2.2 "Materials": particles from a file or a user's model) -----
+def _ps_records(records):
+    r = np.ascontiguousarray(records)
+    if r.dtype.itemsize != 32 or len(r) == 0:
+        raise ValueError("records: 32-byte structured array (x, y, z, u, v, w, E float32; type int32)")
+    return r
+
+
+def ps_sample(ph, records, first=0, count=None):
+    """Entry state of histories [first, first+count) of a phase-space source: rows
+    (x, y, z, u, v, w, E, entered)."""
+    r = _ps_records(records)
+    count = len(r) - first if count is None else count
+    k = _Keep(ph, _NoBeam)
+    out = np.empty((count, 8), np.float64)
+    rc = lib().orc_ps_sample(C.byref(k.ph), C.c_void_p(r.ctypes.data), len(r), first, count,
+                             _ptr(out, C.c_double))
+    if rc != 0:
+        raise ValueError("orc_ps_sample failed (invalid records)")
+    return out
+
+
+def run_ps(ph, records, n_hist, seed=1, p=None, first=0, count=None, threads=None):
+    """Transport histories [first, first+count) of a phase-space source (history h starts
+    from record h mod len(records))."""
+    p = p or params()
+    r = _ps_records(records)
+    count = n_hist - first if count is None else count
+    threads = threads or os.cpu_count() or 1
+    threads = max(1, min(threads, count if count > 0 else 1))
+    k = _Keep(ph, _NoBeam)
+    nvox = ph.density.size
+    B = p.n_batches
+    chunks = np.linspace(first, first + count, threads + 1).astype(np.int64)
+    L = lib()
+
+    def work(t):
+        tally = np.zeros(B * nvox, np.int64)
+        ledger = np.zeros(N_LEDGER, np.float64)
+        cnt = np.zeros(N_COUNTERS, np.uint64)
+        a, b = int(chunks[t]), int(chunks[t + 1])
+        if b > a:
+            rc = L.orc_run_ps(C.byref(k.ph), C.c_void_p(r.ctypes.data), len(r), C.byref(p), seed, a, b - a,
+                              _ptr(tally, C.c_int64), _ptr(ledger, C.c_double), _ptr(cnt, C.c_uint64))
+            if rc != 0:
+                raise ValueError(f"orc_run_ps failed ({rc})")
+        return tally, ledger, cnt
+
+    with ThreadPoolExecutor(threads) as ex:
+        parts = list(ex.map(work, range(threads)))
+    tally = sum(p_[0] for p_ in parts).reshape((B,) + ph.density.shape)
+    ledger = sum(p_[1] for p_ in parts)
+    cnt = sum(p_[2] for p_ in parts)
+    return Result(tally, ledger, cnt, count, ph)
+
+
+class _NoBeam:
+    """Placeholder beam for the phantom-only ctypes structure of the phase-space calls."""
+    particle, edges, weights = 0, np.zeros(2, np.float32), np.ones(1, np.float32)
+    field, ssd, iso, direction = (0.0, 0.0), 0.0, (0.0, 0.0, 0.0), (0.0, 0.0, 1.0)

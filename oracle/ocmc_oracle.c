@@ -871,6 +871,102 @@ int orc_run(const orc_phantom* ph, const orc_source* src, const orc_params* p,
     return 0;
 }
 
+/* Phase-space primary of history h: record h mod n_ps, moved along its direction through
+ * vacuum to the phantom box (t >= 0, so a particle inside starts where it is). Returns 1 if
+ * it enters. No random numbers are drawn here. */
+static int make_primary_ps(const run_ctx* c, const orc_ps_particle* ps, uint64_t n_ps, uint64_t seed,
+                           uint64_t h, particle* q)
+{
+    const orc_ps_particle* rec = ps + (h % n_ps);
+    memset(q, 0, sizeof(*q));
+    q->rs.key[0] = (uint32_t)seed; q->rs.key[1] = (uint32_t)(seed >> 32);
+    q->rs.hist = h; q->rs.sub = 0; q->rs.n = 0;
+    q->type = rec->type == 0 ? PHOTON : (rec->type == 1 ? ELECTRON : POSITRON);
+    q->E = rec->E;
+    double O[3] = { rec->x, rec->y, rec->z }, d[3] = { rec->u, rec->v, rec->w };
+    normalize3(d);
+    double tmin = 0.0, tmax = INFINITY;
+    for (int k = 0; k < 3; ++k) {
+        if (fabs(d[k]) < 1e-300) {
+            if (O[k] < 0.0 || O[k] > c->L[k]) return 0;
+            continue;
+        }
+        double t1 = (0.0 - O[k]) / d[k], t2 = (c->L[k] - O[k]) / d[k];
+        tmin = fmax(tmin, fmin(t1, t2));
+        tmax = fmin(tmax, fmax(t1, t2));
+    }
+    if (!(tmax > tmin)) return 0;
+    for (int k = 0; k < 3; ++k) { q->r[k] = O[k] + tmin * d[k]; q->d[k] = d[k]; }
+    index_of(c, q->r, q->i);
+    return 1;
+}
+
+static int ps_valid(const orc_ps_particle* ps, uint64_t n_ps)
+{
+    if (n_ps == 0) return 0;
+    for (uint64_t i = 0; i < n_ps; ++i) {
+        const orc_ps_particle* r = ps + i;
+        double n2 = (double)r->u * r->u + (double)r->v * r->v + (double)r->w * r->w;
+        if (r->type < 0 || r->type > 2 || !(r->E > 0.0) || !(n2 > 0.0) || !isfinite(r->E) ||
+            !isfinite(r->x) || !isfinite(r->y) || !isfinite(r->z))
+            return 0;
+    }
+    return 1;
+}
+
+int orc_ps_sample(const orc_phantom* ph, const orc_ps_particle* ps, uint64_t n_ps,
+                  uint64_t first, uint64_t count, double* out)
+{
+    static const orc_params dummy = { 0.2, 0.01, 0.2, 0.01, 0.5, 0.05, 1e-4, 1, 0 };
+    if (!ps_valid(ps, n_ps)) return -1;
+    run_ctx* c = (run_ctx*)calloc(1, sizeof(run_ctx));
+    if (!c || setup_ctx(c, ph, &dummy) != 0) { free(c); return -1; }
+    for (uint64_t j = 0; j < count; ++j) {
+        particle q;
+        int hit = make_primary_ps(c, ps, n_ps, 0, first + j, &q);
+        double* o = out + 8 * j;
+        o[0] = q.r[0]; o[1] = q.r[1]; o[2] = q.r[2];
+        o[3] = q.d[0]; o[4] = q.d[1]; o[5] = q.d[2];
+        o[6] = q.E; o[7] = hit;
+    }
+    free(c);
+    return 0;
+}
+
+int orc_run_ps(const orc_phantom* ph, const orc_ps_particle* ps, uint64_t n_ps,
+               const orc_params* p, uint64_t seed, uint64_t first, uint64_t count,
+               int64_t* tally, double* ledger, uint64_t* counters)
+{
+    if (p->n_batches < 1 || !ps_valid(ps, n_ps)) return -1;
+    run_ctx* c = (run_ctx*)calloc(1, sizeof(run_ctx));
+    if (!c) return -2;
+    if (setup_ctx(c, ph, p) != 0) { free(c); return -1; }
+    c->tally = tally; c->ledger = ledger; c->cnt = counters;
+    for (uint64_t j = 0; j < count; ++j) {
+        uint64_t h = first + j;
+        c->hist = h;
+        particle q;
+        if (!make_primary_ps(c, ps, n_ps, seed, h, &q)) {
+            c->ledger[ORC_L_EMISS] += q.E;
+            c->cnt[ORC_C_MISSED]++;
+            continue;
+        }
+        c->ledger[ORC_L_EIN] += q.E;
+        if (q.type == PHOTON) {
+            if (q.E >= p->e_abs_g) push(c, &q); else deposit(c, q.i, q.E);
+        } else {
+            emit_charged(c, &q);
+        }
+        while (c->top > 0) {
+            particle r = c->stack[--c->top];
+            if (r.type == PHOTON) transport_photon(c, &r);
+            else transport_charged(c, &r);
+        }
+    }
+    free(c);
+    return 0;
+}
+
 /* ---- sampler access for distribution tests ------------------------------ */
 int orc_sample(int kind, int m, double E, double aux, uint64_t n, uint64_t seed,
                const orc_params* p, double* out)

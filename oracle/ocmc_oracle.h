@@ -54,6 +54,15 @@ typedef struct {
     double iso[3], dir[3];
 } orc_source;
 
+/* One source particle of a phase-space source (Sec. 2.2 "Materials": source particles may be
+ * loaded from a phase-space file or made by a user's own source model). Position in the
+ * phantom frame (cm, origin at the outer corner of voxel (0,0,0)), direction (any length > 0),
+ * kinetic energy (MeV), type 0 photon, 1 electron, 2 positron. */
+typedef struct {
+    float x, y, z, u, v, w, E;
+    int32_t type;
+} orc_ps_particle;
+
 /* counters[] layout (uint64) */
 enum {
     ORC_C_FLIGHTS = 0, ORC_C_FICTITIOUS, ORC_C_COMPTON, ORC_C_PHOTO, ORC_C_PAIR,
@@ -101,6 +110,14 @@ int    orc_source_sample(const orc_phantom* ph, const orc_source* src, uint64_t 
 int    orc_run(const orc_phantom* ph, const orc_source* src, const orc_params* p,
                uint64_t seed, uint64_t n_total, uint64_t first, uint64_t count,
                int64_t* tally, double* ledger, uint64_t* counters);
+/* Phase-space source: history h starts from record h mod n_ps, moved forward in vacuum to
+ * the phantom (or starting where it is when inside); it draws no random numbers before its
+ * first transport step. */
+int    orc_ps_sample(const orc_phantom* ph, const orc_ps_particle* ps, uint64_t n_ps,
+                     uint64_t first, uint64_t count, double* out);
+int    orc_run_ps(const orc_phantom* ph, const orc_ps_particle* ps, uint64_t n_ps,
+                  const orc_params* p, uint64_t seed, uint64_t first, uint64_t count,
+                  int64_t* tally, double* ledger, uint64_t* counters);
 
 #ifdef __cplusplus
 }
