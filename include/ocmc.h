@@ -143,6 +143,32 @@ ocmc_status ocmc_set_source(ocmc_ctx* ctx, int particle, int n_bins,
                             float field_x, float field_y, float ssd,
                             const float iso[3], const float dir[3]);
 
+/* ---- phase-space source ---------------------------------------------------------
+ * Sec. 2.2 "Materials" leaves source generation open: source particles may come from a
+ * phase-space file or from a user's own CPU/GPU source model. A record is one source
+ * particle: position (cm, phantom frame: origin at the outer corner of voxel (0,0,0)),
+ * direction (any non-zero length; normalised by the engine), kinetic energy (MeV) and type
+ * (0 photon, 1 electron, 2 positron). History h of a run starts from record h mod n and moves
+ * forward in vacuum to the phantom (a record inside the phantom starts where it is); records
+ * are thus recycled when a run has more histories than records, each use with its own random
+ * stream. The dose stays per source history (MeV/g per history). */
+typedef struct {
+    float x, y, z;
+    float u, v, w;
+    float E;
+    int32_t type;
+} ocmc_ps_particle;
+
+/* Use n records (host memory, or device memory of the context's GPU if on_device) as the
+ * source until the next ocmc_set_source / ocmc_set_phase_space. The records are copied.
+ * OCMC_ERR_ARG if any record has another type, E outside (0, 1e4) MeV, a non-finite
+ * position or a zero direction (the previous source is then unset). */
+ocmc_status ocmc_set_phase_space(ocmc_ctx* ctx, const ocmc_ps_particle* records, uint64_t n, int on_device);
+
+/* The same from a file: 8 bytes "OCMCPS01", uint64 record count (little endian), then the
+ * 32-byte records above (little endian). OCMC_ERR_ARG on a missing, short or foreign file. */
+ocmc_status ocmc_load_phase_space(ocmc_ctx* ctx, const char* path);
+
 /* Transport histories 0..n_histories-1 with the Philox key `seed` and add the
  * deposited energy to the tally (Sec. 2.2.1, Table 1 loop). Asynchronous on
  * cuda_stream (a cudaStream_t, NULL = the legacy default stream); the call

@@ -139,8 +139,10 @@ void fill_args(const ocmc_ctx* c, TransportArgs& a)
     a.stats = c->d_stats;
     a.err = c->d_err;
     a.hist_counter = c->d_counter;
-    a.src.particle = c->particle;
+    a.src.particle = c->src_kind == 1 ? 0 : c->particle;
     a.src.n_bins = c->n_bins;
+    a.ps = c->src_kind == 1 ? c->d_ps : nullptr;
+    a.ps_n = c->src_kind == 1 ? c->ps_n : 0;
     a.src.fx = c->fx; a.src.fy = c->fy; a.src.ssd = c->ssd;
     for (int k = 0; k < 3; ++k) {
         a.src.iso[k] = c->iso[k]; a.src.e1[k] = c->e1[k]; a.src.e2[k] = c->e2[k]; a.src.dir[k] = c->dir[k];
@@ -397,7 +399,66 @@ ocmc_status ocmc_set_source(ocmc_ctx* c, int particle, int n_bins, const float* 
         c->e2[k] = (float)b[k];
     }
     c->have_source = true;
+    c->src_kind = 0;
     return OCMC_OK;
+}
+
+ocmc_status ocmc_set_phase_space(ocmc_ctx* c, const ocmc_ps_particle* records, uint64_t n, int on_device)
+{
+    if (!c) return fail(c, OCMC_ERR_ARG, "ctx is NULL");
+    if (!records || n == 0) return fail(c, OCMC_ERR_ARG, "need at least one record");
+    static_assert(sizeof(ocmc_ps_particle) == sizeof(PsRec), "record layout");
+    CK(cudaSetDevice(c->device), "cudaSetDevice");
+    if (n > c->ps_cap) {
+        cudaDeviceSynchronize();
+        CK(dalloc(&c->d_ps, (size_t)n), "phase-space allocation");
+        c->ps_cap = n;
+    }
+    CK(cudaMemcpy(c->d_ps, records, sizeof(PsRec) * (size_t)n, on_device ? cudaMemcpyDeviceToDevice
+                                                                           : cudaMemcpyHostToDevice),
+       "phase-space copy");
+    CK(launch_ps_validate(c->d_ps, n, c->d_sum, nullptr), "phase-space check");
+    unsigned long long bad = 0;
+    CK(cudaMemcpy(&bad, c->d_sum, sizeof(bad), cudaMemcpyDeviceToHost), "phase-space check");
+    if (bad) {
+        if (c->src_kind == 1) c->have_source = false;
+        return fail(c, OCMC_ERR_ARG, std::to_string(bad) + " phase-space record(s) invalid (type 0/1/2, 0 < E < "
+                                     "1e4 MeV, finite position, non-zero direction)");
+    }
+    c->ps_n = n;
+    c->src_kind = 1;
+    c->have_source = true;
+    return OCMC_OK;
+}
+
+ocmc_status ocmc_load_phase_space(ocmc_ctx* c, const char* path)
+{
+    if (!c) return fail(c, OCMC_ERR_ARG, "ctx is NULL");
+    if (!path) return fail(c, OCMC_ERR_ARG, "path is NULL");
+    FILE* f = std::fopen(path, "rb");
+    if (!f) return fail(c, OCMC_ERR_ARG, std::string("cannot open ") + path);
+    unsigned char hdr[16];
+    if (std::fread(hdr, 1, 16, f) != 16 || std::memcmp(hdr, "OCMCPS01", 8) != 0) {
+        std::fclose(f);
+        return fail(c, OCMC_ERR_ARG, "not a phase-space file (magic OCMCPS01)");
+    }
+    uint64_t n = 0;
+    for (int i = 0; i < 8; ++i) n |= (uint64_t)hdr[8 + i] << (8 * i);      // little endian
+    if (n == 0 || n > (1ull << 36)) {
+        std::fclose(f);
+        return fail(c, OCMC_ERR_ARG, "bad record count");
+    }
+    std::vector<ocmc_ps_particle> recs;
+    try {
+        recs.resize((size_t)n);
+    } catch (...) {
+        std::fclose(f);
+        return fail(c, OCMC_ERR_OOM, "host memory for the phase space");
+    }
+    size_t got = std::fread(recs.data(), sizeof(ocmc_ps_particle), (size_t)n, f);
+    std::fclose(f);
+    if (got != (size_t)n) return fail(c, OCMC_ERR_ARG, "phase-space file shorter than its record count");
+    return ocmc_set_phase_space(c, recs.data(), n, 0);
 }
 
 ocmc_status ocmc_run_range(ocmc_ctx* c, uint64_t first, uint64_t count, uint64_t n_total, uint64_t seed,
@@ -424,7 +485,7 @@ ocmc_status ocmc_run_range(ocmc_ctx* c, uint64_t first, uint64_t count, uint64_t
     }
     TransportArgs a;
     fill_args(c, a);
-    stratify(c, n_total, a.src);
+    if (c->src_kind == 0) stratify(c, n_total, a.src);
     a.first = first;
     a.count = count;
     a.n_total = n_total;
@@ -611,7 +672,7 @@ void ocmc_destroy(ocmc_ctx* c)
     dfree(&c->t.rmeta); dfree(&c->t.msc); dfree(&c->t.scratch); dfree(&c->t.rho_max);
     dfree(&c->d_bl); dfree(&c->d_bl_prefix); dfree(&c->d_bl_offs); dfree(&c->d_bl_caps); dfree(&c->d_bl_nnz);
     dfree(&c->d_bl_over); dfree(&c->d_bl_keys); dfree(&c->d_bl_vals); dfree(&c->d_dense); dfree(&c->d_chunks);
-    dfree(&c->d_oidx); dfree(&c->d_odose); dfree(&c->d_oraw);
+    dfree(&c->d_oidx); dfree(&c->d_odose); dfree(&c->d_oraw); dfree(&c->d_ps);
     if (c->bl_exec) cudaGraphExecDestroy(c->bl_exec);
     if (c->bl_capture) cudaStreamDestroy(c->bl_capture);
     if (c->ev0) cudaEventDestroy(c->ev0);
@@ -642,7 +703,7 @@ ocmc_status ocmc_test_source(ocmc_ctx* c, uint64_t n_total, uint64_t first, uint
     CK(cudaSetDevice(c->device), "cudaSetDevice");
     TransportArgs a;
     fill_args(c, a);
-    stratify(c, n_total, a.src);
+    if (c->src_kind == 0) stratify(c, n_total, a.src);
     a.key0 = (uint32_t)seed;
     a.key1 = (uint32_t)(seed >> 32);
     float* d = nullptr;

@@ -59,7 +59,7 @@ __global__ void k_test_source(const TransportArgs a, unsigned long long first, u
     unsigned long long j = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x;
     if (j >= count) return;
     Lane p;
-    bool in = init_primary(a, first + j, p);
+    bool in = a.ps ? init_phase_space(a, first + j, p) : init_primary(a, first + j, p);
     float* o = out + 8 * j;
     o[0] = in ? p.x : 0.f; o[1] = in ? p.y : 0.f; o[2] = in ? p.z : 0.f;
     o[3] = in ? p.u : 0.f; o[4] = in ? p.v : 0.f; o[5] = in ? p.w : 0.f;
@@ -226,6 +226,31 @@ __global__ void k_compact(const long long* dense, long long nvox, const unsigned
 }
 
 }  // namespace
+
+// Count phase-space records that cannot be transported: unknown type, energy not in
+// (0, 1e4) MeV, non-finite position, zero or non-finite direction.
+__global__ void k_ps_validate(const PsRec* ps, unsigned long long n, unsigned long long* bad)
+{
+    unsigned long long nb = 0;
+    for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
+         i += (unsigned long long)gridDim.x * blockDim.x) {
+        const PsRec r = ps[i];
+        const float d2 = r.u * r.u + r.v * r.v + r.w * r.w;
+        const bool ok = r.type >= 0 && r.type <= 2 && r.E > 0.f && r.E < 1e4f && isfinite(r.x) && isfinite(r.y) &&
+                        isfinite(r.z) && d2 > 0.f && isfinite(d2);
+        nb += ok ? 0 : 1;
+    }
+    if (nb) atomicAdd(bad, nb);
+}
+
+cudaError_t launch_ps_validate(const PsRec* ps, unsigned long long n, unsigned long long* bad, cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(bad, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return e;
+    unsigned blocks = (unsigned)std::min<unsigned long long>((n + 255) / 256, 4096);
+    k_ps_validate<<<blocks, 256, 0, s>>>(ps, n, bad);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_bl_count(const unsigned int* keys, const unsigned long long* offs, const unsigned int* caps, int n,
                             unsigned long long* nnz, cudaStream_t s)

@@ -23,6 +23,9 @@ struct ocmc_ctx {
     int particle = 0, n_bins = 0;
     std::vector<float> edges, weights;
     float fx = 0.f, fy = 0.f, ssd = 0.f, iso[3] = {0, 0, 0}, dir[3] = {0, 0, 1}, e1[3], e2[3];
+    int src_kind = 0;                        // 0 analytic beam (ocmc_set_source), 1 phase space
+    ocmc::PsRec* d_ps = nullptr;             // phase-space records on the device
+    unsigned long long ps_n = 0, ps_cap = 0;
     // tables
     ocmc::Tables t{};
     bool tables_valid = false;

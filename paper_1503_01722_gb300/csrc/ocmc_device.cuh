@@ -319,6 +319,39 @@ __device__ __forceinline__ int batch_of(uint32_t h0, uint32_t h1, int B)
     return (int)(h % (unsigned long long)B);
 }
 
+// Move a particle starting at O with unit direction d (line parameter t >= tmin) through
+// vacuum to the phantom box; sets position, direction and voxel. False if it misses.
+__device__ __forceinline__ bool enter_box(const TransportArgs& a, const float* O, const float* d, float tmin, Lane& p)
+{
+    const float Lb[3] = {a.nx * a.dx, a.ny * a.dy, a.nz * a.dz};
+    float tmax = 3.0e38f;
+    int ent = -1;
+    for (int k = 0; k < 3; ++k) {
+        if (fabsf(d[k]) < 1e-30f) {
+            if (O[k] < 0.f || O[k] > Lb[k]) return false;
+            continue;
+        }
+        float t1 = (0.f - O[k]) / d[k], t2 = (Lb[k] - O[k]) / d[k];
+        float tn = fminf(t1, t2), tx = fmaxf(t1, t2);
+        if (tn > tmin) { tmin = tn; ent = k * 2 + (t1 < t2 ? 0 : 1); }
+        tmax = fminf(tmax, tx);
+    }
+    if (!(tmax > tmin)) return false;
+    p.x = O[0] + tmin * d[0];
+    p.y = O[1] + tmin * d[1];
+    p.z = O[2] + tmin * d[2];
+    if (ent >= 0) {                              // put the entry point exactly on its face
+        float f = (ent & 1) ? Lb[ent >> 1] : 0.f;
+        if ((ent >> 1) == 0) p.x = f; else if ((ent >> 1) == 1) p.y = f; else p.z = f;
+    }
+    p.u = d[0]; p.v = d[1]; p.w = d[2];
+    p.ix = min(max((int)floorf(p.x / a.dx), 0), a.nx - 1);
+    p.iy = min(max((int)floorf(p.y / a.dy), 0), a.ny - 1);
+    p.iz = min(max((int)floorf(p.z / a.dz), 0), a.nz - 1);
+    return true;
+}
+
+
 // Source particle of history h of a beam with geometry g (Sec. 2.2 "Materials": point
 // source at SSD with the field defined at the surface, or a parallel beam; energy
 // bins in decreasing energy, Sec. 2.2.1). Draws: energy within the bin, then the
@@ -357,32 +390,7 @@ __device__ __forceinline__ bool init_source(const TransportArgs& a, const G& g, 
         for (int k = 0; k < 3; ++k) { O[k] = P[k]; d[k] = g.dir[k]; }
         tmin = -3.0e38f;
     }
-    const float Lb[3] = {a.nx * a.dx, a.ny * a.dy, a.nz * a.dz};
-    float tmax = 3.0e38f;
-    int ent = -1;
-    for (int k = 0; k < 3; ++k) {
-        if (fabsf(d[k]) < 1e-30f) {
-            if (O[k] < 0.f || O[k] > Lb[k]) return false;
-            continue;
-        }
-        float t1 = (0.f - O[k]) / d[k], t2 = (Lb[k] - O[k]) / d[k];
-        float tn = fminf(t1, t2), tx = fmaxf(t1, t2);
-        if (tn > tmin) { tmin = tn; ent = k * 2 + (t1 < t2 ? 0 : 1); }
-        tmax = fminf(tmax, tx);
-    }
-    if (!(tmax > tmin)) return false;
-    p.x = O[0] + tmin * d[0];
-    p.y = O[1] + tmin * d[1];
-    p.z = O[2] + tmin * d[2];
-    if (ent >= 0) {                              // put the entry point exactly on its face
-        float f = (ent & 1) ? Lb[ent >> 1] : 0.f;
-        if ((ent >> 1) == 0) p.x = f; else if ((ent >> 1) == 1) p.y = f; else p.z = f;
-    }
-    p.u = d[0]; p.v = d[1]; p.w = d[2];
-    p.ix = min(max((int)floorf(p.x / a.dx), 0), a.nx - 1);
-    p.iy = min(max((int)floorf(p.y / a.dy), 0), a.ny - 1);
-    p.iz = min(max((int)floorf(p.z / a.dz), 0), a.nz - 1);
-    return true;
+    return enter_box(a, O, d, tmin, p);
 }
 
 // Single-beam source: history h of the run, batch = h mod B.
@@ -390,6 +398,27 @@ __device__ __forceinline__ bool init_primary(const TransportArgs& a, unsigned lo
 {
     p.batch = batch_of((uint32_t)h, (uint32_t)(h >> 32), a.pp.n_batches);
     return init_source(a, a.src, a.src.bound, h, a.stream_tag, p);
+}
+
+// Phase-space source: history h starts from record h mod ps_n, moved forward through vacuum to
+// the phantom (a record inside starts where it is); no random number is drawn before the first
+// transport step. Stream (history lo, history hi ^ stream tag, sub-stream 0), batch h mod B.
+__device__ __forceinline__ bool init_phase_space(const TransportArgs& a, unsigned long long h, Lane& p)
+{
+    const PsRec r = a.ps[h % a.ps_n];
+    p.batch = batch_of((uint32_t)h, (uint32_t)(h >> 32), a.pp.n_batches);
+    p.r.h0 = (uint32_t)h;
+    p.r.h1 = (uint32_t)(h >> 32) ^ a.stream_tag;
+    p.r.sub = 0u;
+    p.r.n = 0u;
+    p.r.blk = 0xFFFFFFFFu;
+    p.type = r.type == 0 ? PHOTON : (r.type == 1 ? ELECTRON : POSITRON);
+    p.steps = 0;
+    p.E = r.E;
+    float O[3] = {r.x, r.y, r.z}, d[3] = {r.u, r.v, r.w};
+    const float inv = rsqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+    for (int k = 0; k < 3; ++k) d[k] *= inv;
+    return enter_box(a, O, d, 0.f, p);
 }
 
 // Batched beamlets: global history g -> (beamlet b, its history h); stream high word

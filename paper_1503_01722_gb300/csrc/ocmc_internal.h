@@ -108,6 +108,13 @@ struct BeamletDev {
     unsigned long long bound[MAX_BL_BINS + 1]; // energy-bin stratification of its histories
 };
 
+// Phase-space source record (Sec. 2.2 "Materials": particles from a phase-space file or a
+// user's source model); the same 32-byte layout as ocmc_ps_particle of the C ABI.
+struct PsRec {
+    float x, y, z, u, v, w, E;
+    int type;                            // 0 photon, 1 electron, 2 positron
+};
+
 struct TransportArgs {
     // geometry
     int nx, ny, nz;
@@ -132,6 +139,8 @@ struct TransportArgs {
     int* err;
     SourceDev src;
     uint32_t stream_tag;                 // XORed into the high history word (single-beam mode)
+    const PsRec* ps;                     // phase-space source (null: the analytic source src)
+    unsigned long long ps_n;             // its records; history h starts from record h mod ps_n
     // batched beamlets (beamlets == nullptr: single-beam mode with the dense tally)
     const BeamletDev* beamlets;
     const unsigned long long* bl_prefix; // n_beamlets + 1 prefix sums of histories
@@ -161,6 +170,7 @@ cudaError_t launch_test_tables(const TransportArgs& a, int m, const float* E, in
 cudaError_t launch_test_csda(const TransportArgs& a, int m, const float* T, const float* X, int n, float* out,
                              cudaStream_t s);
 void material_defs(MatDef out[NMAT]);
+cudaError_t launch_ps_validate(const PsRec* ps, unsigned long long n, unsigned long long* bad, cudaStream_t s);
 cudaError_t launch_bl_count(const unsigned int* keys, const unsigned long long* offs, const unsigned int* caps, int n,
                             unsigned long long* nnz, cudaStream_t s);
 cudaError_t launch_bl_extract(const unsigned int* keys, const unsigned long long* vals, unsigned long long cap,

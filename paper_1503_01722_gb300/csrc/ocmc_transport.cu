@@ -407,7 +407,9 @@ __device__ __forceinline__ bool charged_step(C& c, Lane& p, unsigned& n_hfict)
 
 // NREG: register cap per thread. More registers spill less; fewer registers let more
 // warps share an SM (80: 3 x 256 threads, 64: 2 x 512, 56: 3 x 384 on GB300).
-template <bool BL, int NREG>
+// PS: the source is a phase space (per-history records of mixed particle types); a separate
+// instantiation, so that the analytic-source kernel carries none of its code.
+template <bool BL, bool PS, int NREG>
 __global__ void __maxnreg__(NREG) k_transport(const __grid_constant__ TransportArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -423,6 +425,9 @@ __global__ void __maxnreg__(NREG) k_transport(const __grid_constant__ TransportA
           1.f / a.dx, 1.f / a.dy, 1.f / a.dz, a.nx * a.dx, a.ny * a.dy, a.nz * a.dz, true};
     const unsigned lt = (1u << lane) - 1u;
     const int src_mode = a.src.particle == 0 ? 0 : 1;
+    // a phase-space source mixes particle types: warps of either type draw from it, and a
+    // primary of the other type goes to that type's stack like a secondary
+    constexpr bool ps_src = PS && !BL;
     int mode = src_mode;
     bool src_done = a.count == 0;
     bool active = false, just_switched = false;
@@ -446,7 +451,7 @@ __global__ void __maxnreg__(NREG) k_transport(const __grid_constant__ TransportA
                 active = true;
             }
             int want = nfree - take;
-            if (want > 0 && mode == src_mode && !src_done) {
+            if (want > 0 && (ps_src || mode == src_mode) && !src_done) {
                 unsigned long long base = 0;
                 if (lane == 0) base = atomicAdd(a.hist_counter, (unsigned long long)want);
                 base = __shfl_sync(FULL, base, 0);
@@ -456,11 +461,23 @@ __global__ void __maxnreg__(NREG) k_transport(const __grid_constant__ TransportA
                     hist++;
                     bool in;
                     if constexpr (BL) in = init_beamlet(a, base + r2, p);
+                    else if constexpr (ps_src) in = init_phase_space(a, a.first + base + r2, p);
                     else in = init_primary(a, a.first + base + r2, p);
                     float ecut = p.type == PHOTON ? a.pp.e_abs_g : a.pp.e_abs_e;
                     if (!in) {
                         missed++;
                         e_miss += fx(p.E);
+                    } else if constexpr (ps_src) {
+                        e_in += fx(p.E);
+                        const bool charged = p.type != PHOTON;
+                        if (p.E >= ecut && !(charged && (a.pp.flags & 8))) {
+                            if ((charged ? 1 : 0) == mode) active = true;
+                            else push_lane(c, charged ? 1 : 0, p);
+                        } else if (charged) {
+                            absorb_charged(c, p);       // positrons annihilate
+                        } else {
+                            deposit(c, p, p.ix, p.iy, p.iz, p.E);
+                        }
                     } else {
                         e_in += fx(p.E);
                         if (p.E >= ecut && !(p.type != PHOTON && (a.pp.flags & 8))) active = true;
@@ -477,8 +494,8 @@ __global__ void __maxnreg__(NREG) k_transport(const __grid_constant__ TransportA
         int nact = __popc(act);
         int other = 1 - mode;
         int topm = mode ? top1 : top0, topo = mode ? top0 : top1;
-        bool m_avail = topm > 0 || (mode == src_mode && !src_done);
-        bool o_avail = topo > 0 || (other == src_mode && !src_done);
+        bool m_avail = topm > 0 || ((ps_src || mode == src_mode) && !src_done);
+        bool o_avail = topo > 0 || ((ps_src || other == src_mode) && !src_done);
         if (nact == 0) {
             if (m_avail) continue;
             if (o_avail) { mode = other; continue; }
@@ -487,7 +504,8 @@ __global__ void __maxnreg__(NREG) k_transport(const __grid_constant__ TransportA
         bool sw = false;
         if (o_avail && !just_switched) {     // at most one switch between two steps
             // the other group must be strictly larger (or the source), so a switch is never undone at once
-            if (!m_avail && nact <= a.switch_low && (topo > nact || (other == src_mode && !src_done))) sw = true;
+            if (!m_avail && nact <= a.switch_low && (topo > nact || (!ps_src && other == src_mode && !src_done)))
+                sw = true;
             else if (topo >= a.switch_high && topo >= 2 * (nact + topm)) sw = true;
         }
         if (sw) {
@@ -537,22 +555,32 @@ __global__ void __maxnreg__(NREG) k_transport(const __grid_constant__ TransportA
 size_t transport_smem_bytes(int /*threads*/) { return SMEM_TABLE_BYTES; }
 
 namespace {
-template <bool BL, int R>
+template <bool BL, bool PS, int R>
 cudaError_t launch_variant(const TransportArgs& a, int blocks, int threads, size_t smem, cudaStream_t s)
 {
-    cudaError_t e = cudaFuncSetAttribute(k_transport<BL, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e =
+        cudaFuncSetAttribute(k_transport<BL, PS, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_transport<BL, R><<<blocks, threads, smem, s>>>(a);
+    k_transport<BL, PS, R><<<blocks, threads, smem, s>>>(a);
     return cudaGetLastError();
 }
 
-template <bool BL, int R>
+template <bool BL, bool PS, int R>
 int occupancy(int threads, size_t smem)
 {
-    cudaFuncSetAttribute(k_transport<BL, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_transport<BL, PS, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_transport<BL, R>, threads, smem) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_transport<BL, PS, R>, threads, smem) != cudaSuccess)
+        return 0;
     return n;
+}
+
+template <bool BL, bool PS>
+cudaError_t launch_source(const TransportArgs& a, int blocks, int threads, size_t smem, cudaStream_t s, int nreg)
+{
+    if (nreg == 56) return launch_variant<BL, PS, 56>(a, blocks, threads, smem, s);
+    if (nreg == 64) return launch_variant<BL, PS, 64>(a, blocks, threads, smem, s);
+    return launch_variant<BL, PS, 80>(a, blocks, threads, smem, s);
 }
 }  // namespace
 
@@ -560,24 +588,22 @@ bool transport_nreg_supported(int nreg) { return nreg == 56 || nreg == 64 || nre
 
 int transport_max_blocks_per_sm(int threads, size_t smem, int nreg)
 {
-    occupancy<true, 56>(threads, smem);   // sets the shared-memory attribute of every variant
-    occupancy<true, 64>(threads, smem);
-    occupancy<true, 80>(threads, smem);
-    if (nreg == 56) return occupancy<false, 56>(threads, smem);
-    if (nreg == 64) return occupancy<false, 64>(threads, smem);
-    return occupancy<false, 80>(threads, smem);
+    occupancy<true, false, 56>(threads, smem);   // sets the shared-memory attribute of every variant
+    occupancy<true, false, 64>(threads, smem);
+    occupancy<true, false, 80>(threads, smem);
+    occupancy<false, true, 56>(threads, smem);
+    occupancy<false, true, 64>(threads, smem);
+    occupancy<false, true, 80>(threads, smem);
+    if (nreg == 56) return occupancy<false, false, 56>(threads, smem);
+    if (nreg == 64) return occupancy<false, false, 64>(threads, smem);
+    return occupancy<false, false, 80>(threads, smem);
 }
 
 cudaError_t launch_transport(const TransportArgs& a, int blocks, int threads, size_t smem, cudaStream_t s, int nreg)
 {
-    if (a.beamlets) {
-        if (nreg == 56) return launch_variant<true, 56>(a, blocks, threads, smem, s);
-        if (nreg == 64) return launch_variant<true, 64>(a, blocks, threads, smem, s);
-        return launch_variant<true, 80>(a, blocks, threads, smem, s);
-    }
-    if (nreg == 56) return launch_variant<false, 56>(a, blocks, threads, smem, s);
-    if (nreg == 64) return launch_variant<false, 64>(a, blocks, threads, smem, s);
-    return launch_variant<false, 80>(a, blocks, threads, smem, s);
+    if (a.beamlets) return launch_source<true, false>(a, blocks, threads, smem, s, nreg);
+    if (a.ps) return launch_source<false, true>(a, blocks, threads, smem, s, nreg);
+    return launch_source<false, false>(a, blocks, threads, smem, s, nreg);
 }
 
 }  // namespace ocmc

@@ -80,6 +80,8 @@ def _load():
         "ocmc_run_beamlets": (C.c_int, [P, C.c_uint64, P]),
         "ocmc_get_beamlet_dose": (C.c_int, [P, C.c_int, P, P, P, C.c_int64, C.POINTER(C.c_int64)]),
         "ocmc_autotune": (C.c_int, [P, C.c_uint64, C.POINTER(Params)]),
+        "ocmc_set_phase_space": (C.c_int, [P, P, C.c_uint64, C.c_int]),
+        "ocmc_load_phase_space": (C.c_int, [P, C.c_char_p]),
         "ocmc_unet_create": (C.c_int, [C.POINTER(P), C.c_int, C.c_int, C.c_int, C.c_int, C.c_uint64]),
         "ocmc_unet_destroy": (None, [P]),
         "ocmc_unet_last_error": (C.c_char_p, [P]),
@@ -207,6 +209,25 @@ class Engine:
         self._check(lib.ocmc_set_source(self._c, int(particle), len(w), C.c_void_p(e.ctypes.data),
                                         C.c_void_p(w.ctypes.data), float(field[0]), float(field[1]),
                                         float(ssd), iso_c, dir_c))
+
+    def set_phase_space(self, records):
+        """Phase-space source: a structured array of 32-byte records (x, y, z, u, v, w, E as
+        float32, type as int32; see ocmc_inputs.PS_DTYPE) in host memory, or a CUDA uint8/
+        int32/float32 tensor holding the same bytes."""
+        if isinstance(records, np.ndarray):
+            r = np.ascontiguousarray(records)
+            if r.dtype.itemsize != 32:
+                raise ValueError("records must be 32-byte structured records")
+            self._check(lib.ocmc_set_phase_space(self._c, C.c_void_p(r.ctypes.data), len(r), 0))
+        else:
+            pt, dev = _ptr(records)
+            nbytes = records.numel() * records.element_size()
+            if nbytes % 32:
+                raise ValueError("tensor size must be a multiple of 32 bytes")
+            self._check(lib.ocmc_set_phase_space(self._c, pt, nbytes // 32, dev))
+
+    def load_phase_space(self, path):
+        self._check(lib.ocmc_load_phase_space(self._c, os.fsencode(str(path))))
 
     def run(self, n_histories: int, seed: int = 1, stream=None):
         self._check(lib.ocmc_run(self._c, int(n_histories), int(seed), _stream_ptr(stream)))
