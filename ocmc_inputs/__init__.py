@@ -21,6 +21,41 @@ import numpy as np
 WATER, BONE, LUNG = 0, 1, 2
 RHO = {WATER: 1.0, BONE: 1.85, LUNG: 0.26}
 
+# Public compositions (ICRU Report 46 / ICRP tissue compositions and common physics materials):
+# elements Z, standard atomic masses A (g/mol), mass fractions w, mean excitation energy I (eV)
+# and nominal density (g/cm^3). Inputs for user-defined material sets; no method arithmetic.
+_A = {1: 1.008, 6: 12.011, 7: 14.007, 8: 15.999, 11: 22.990, 12: 24.305, 13: 26.982, 15: 30.974,
+      16: 32.06, 17: 35.45, 19: 39.098, 20: 40.078, 26: 55.845, 29: 63.546, 30: 65.38, 53: 126.90}
+
+
+def _mat(zw, I, rho):
+    Z = [z for z, _ in zw]
+    return {"Z": Z, "A": [_A[z] for z in Z], "w": [w for _, w in zw], "I": I, "density": rho}
+
+
+MATERIALS = {
+    "water": _mat([(1, 0.111894), (8, 0.888106)], 75.0, 1.0),
+    "bone_cortical": _mat([(1, 0.047234), (6, 0.144330), (7, 0.041990), (8, 0.446096), (12, 0.002200),
+                           (15, 0.104970), (16, 0.003150), (20, 0.209930), (30, 0.000100)], 106.4, 1.85),
+    "lung": _mat([(1, 0.101278), (6, 0.102310), (7, 0.028650), (8, 0.757072), (11, 0.001840), (12, 0.000730),
+                  (15, 0.000800), (16, 0.002250), (17, 0.002660), (19, 0.001940), (20, 0.000090),
+                  (26, 0.000370), (30, 0.000010)], 75.3, 0.26),
+    "adipose": _mat([(1, 0.114), (6, 0.598), (7, 0.007), (8, 0.278), (11, 0.001), (16, 0.001), (17, 0.001)],
+                    63.2, 0.95),
+    "muscle": _mat([(1, 0.102), (6, 0.143), (7, 0.034), (8, 0.710), (11, 0.001), (15, 0.002), (16, 0.003),
+                    (17, 0.001), (19, 0.004)], 75.3, 1.05),
+    "pmma": _mat([(1, 0.080538), (6, 0.599848), (8, 0.319614)], 74.0, 1.19),
+    "aluminium": _mat([(13, 1.0)], 166.0, 2.699),
+    "copper": _mat([(29, 1.0)], 322.0, 8.96),
+    "hydrogen_rich_gel": _mat([(1, 0.14), (6, 0.10), (8, 0.76)], 70.0, 1.02),
+}
+MATERIAL_ORDER = ["water", "bone_cortical", "lung", "adipose", "muscle", "pmma", "aluminium", "copper",
+                  "hydrogen_rich_gel"]
+
+
+def material_set(names):
+    return [MATERIALS[n] for n in names]
+
 
 @dataclasses.dataclass
 class Phantom:

@@ -54,6 +54,14 @@ class Params(C.Structure):
                 ("s_min", C.c_double), ("n_batches", C.c_int32), ("flags", C.c_int32)]
 
 
+MAX_MAT, MAX_ELEM = 16, 16
+
+
+class _Material(C.Structure):
+    _fields_ = [("n_elements", C.c_int32), ("Z", C.c_int32 * MAX_ELEM), ("A", C.c_double * MAX_ELEM),
+                ("mass_fraction", C.c_double * MAX_ELEM), ("I_eV", C.c_double), ("density", C.c_double)]
+
+
 class _Phantom(C.Structure):
     _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32),
                 ("dx", C.c_double), ("dy", C.c_double), ("dz", C.c_double),
@@ -99,6 +107,8 @@ def lib():
                                           C.POINTER(d)]),
                 ("orc_run", i, [C.POINTER(_Phantom), C.POINTER(_Source), C.POINTER(Params), u64, u64, u64,
                                 u64, C.POINTER(C.c_int64), C.POINTER(d), C.POINTER(u64)]),
+                ("orc_set_materials", i, [i, C.c_void_p]),
+                ("orc_reset_materials", None, []), ("orc_n_materials", i, []),
                 ("orc_ps_sample", i, [C.POINTER(_Phantom), C.c_void_p, u64, u64, u64, C.POINTER(d)]),
                 ("orc_run_ps", i, [C.POINTER(_Phantom), C.c_void_p, u64, C.POINTER(Params), u64, u64, u64,
                                    C.POINTER(C.c_int64), C.POINTER(d), C.POINTER(u64)]),
@@ -361,3 +371,34 @@ class _NoBeam:
     """Placeholder beam for the phantom-only ctypes structure of the phase-space calls."""
     particle, edges, weights = 0, np.zeros(2, np.float32), np.ones(1, np.float32)
     field, ssd, iso, direction = (0.0, 0.0), 0.0, (0.0, 0.0, 0.0), (0.0, 0.0, 1.0)
+
+
+# ---- user-defined materials (the paper's material database, generalised) ----------------------
+def _material_array(defs):
+    arr = (_Material * len(defs))()
+    for k, d in enumerate(defs):
+        n = len(d["Z"])
+        arr[k].n_elements = n
+        for i in range(n):
+            arr[k].Z[i] = int(d["Z"][i])
+            arr[k].A[i] = float(d["A"][i])
+            arr[k].mass_fraction[i] = float(d["w"][i])
+        arr[k].I_eV = float(d["I"])
+        arr[k].density = float(d["density"])
+    return arr
+
+
+def set_materials(defs):
+    """Replace the materials (process-wide) by compositions: dicts with Z, A (g/mol), w (mass
+    fractions), I (eV) and density (g/cm^3). Material m of a phantom is defs[m]."""
+    arr = _material_array(defs)
+    if lib().orc_set_materials(len(defs), C.cast(arr, C.c_void_p)) != 0:
+        raise ValueError("bad material definition")
+
+
+def reset_materials():
+    lib().orc_reset_materials()
+
+
+def n_materials():
+    return lib().orc_n_materials()

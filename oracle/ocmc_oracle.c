@@ -45,13 +45,13 @@ static const double TALLY_SCALE = 268435456.0;    /* 2^28 units per MeV */
 /* ---- materials: element mass fractions (ICRU/ICRP compositions) --------- */
 typedef struct { int Z; double A; double w; } elem;
 typedef struct {
-    const char* name; double I_eV; double rho0; int n; elem e[13];
+    const char* name; double I_eV; double rho0; int n; elem e[ORC_MAX_ELEM];
     /* derived per-gram constants (computed once by orc_init) */
     double n_e, photo, pairZ, S1, S2;
     double dC, dX0, dX1, dA;    /* Sternheimer-Peierls density-effect parameters */
 } material;
 
-static material MAT[3] = {
+static material MAT[ORC_MAX_MAT] = {
     { "water", 75.0, 1.0, 2, { {1, 1.008, 0.111894}, {8, 15.999, 0.888106} } },
     { "bone_cortical_icrp", 106.4, 1.85, 9, {
         {1, 1.008, 0.047234}, {6, 12.011, 0.144330}, {7, 14.007, 0.041990},
@@ -65,31 +65,85 @@ static material MAT[3] = {
         {30, 65.38, 0.000010} } },
 };
 
+static int N_MAT = 3;
+static material DEFAULT_MAT[3];
+
+/* Per-gram constants of material M from its composition (the atoms of each element per gram
+ * are N_A w_i / A_i). */
+static void derive_material(material* M)
+{
+    double wsum = 0.0;
+    for (int i = 0; i < M->n; ++i) wsum += M->e[i].w;
+    M->n_e = M->photo = M->pairZ = M->S1 = M->S2 = 0.0;
+    for (int i = 0; i < M->n; ++i) {
+        double Z = M->e[i].Z, atoms = NAV * (M->e[i].w / wsum) / M->e[i].A; /* per g */
+        M->n_e   += atoms * Z;
+        M->photo += atoms * pow(Z, 5.0);
+        M->pairZ += atoms * Z * (Z + 1.0);
+        M->S1    += atoms * Z * (Z + 1.0) * log(183.0 * pow(Z, -1.0 / 3.0));
+        M->S2    += atoms * Z * (Z + 1.0) / 9.0;
+    }
+    /* Sternheimer & Peierls (1971) general density-effect parameters for
+       condensed media, evaluated at the material's nominal density. */
+    double hw = 28.816 * sqrt(M->rho0 * M->n_e / NAV);      /* eV */
+    double C = 2.0 * log(M->I_eV / hw) + 1.0, x0, x1;
+    if (M->I_eV < 100.0) { x1 = 2.0; x0 = (C < 3.681) ? 0.2 : 0.326 * C - 1.0; }
+    else                 { x1 = 3.0; x0 = (C < 5.215) ? 0.2 : 0.326 * C - 1.5; }
+    M->dC = C; M->dX0 = x0; M->dX1 = x1;
+    M->dA = (C - 2.0 * log(10.0) * x0) / pow(x1 - x0, 3.0);
+}
+
 void orc_init(void)
 {
+    static int done = 0;
+    if (done) return;
+    done = 1;
     for (int m = 0; m < 3; ++m) {
-        material* M = &MAT[m];
-        double wsum = 0.0;
-        for (int i = 0; i < M->n; ++i) wsum += M->e[i].w;
-        M->n_e = M->photo = M->pairZ = M->S1 = M->S2 = 0.0;
-        for (int i = 0; i < M->n; ++i) {
-            double Z = M->e[i].Z, atoms = NAV * (M->e[i].w / wsum) / M->e[i].A; /* per g */
-            M->n_e   += atoms * Z;
-            M->photo += atoms * pow(Z, 5.0);
-            M->pairZ += atoms * Z * (Z + 1.0);
-            M->S1    += atoms * Z * (Z + 1.0) * log(183.0 * pow(Z, -1.0 / 3.0));
-            M->S2    += atoms * Z * (Z + 1.0) / 9.0;
-        }
-        /* Sternheimer & Peierls (1971) general density-effect parameters for
-           condensed media, evaluated at the material's nominal density. */
-        double hw = 28.816 * sqrt(M->rho0 * M->n_e / NAV);      /* eV */
-        double C = 2.0 * log(M->I_eV / hw) + 1.0, x0, x1;
-        if (M->I_eV < 100.0) { x1 = 2.0; x0 = (C < 3.681) ? 0.2 : 0.326 * C - 1.0; }
-        else                 { x1 = 3.0; x0 = (C < 5.215) ? 0.2 : 0.326 * C - 1.5; }
-        M->dC = C; M->dX0 = x0; M->dX1 = x1;
-        M->dA = (C - 2.0 * log(10.0) * x0) / pow(x1 - x0, 3.0);
+        derive_material(&MAT[m]);
+        DEFAULT_MAT[m] = MAT[m];
     }
+    N_MAT = 3;
 }
+
+int orc_set_materials(int n, const orc_material* defs)
+{
+    orc_init();
+    if (n < 1 || n > ORC_MAX_MAT || !defs) return -1;
+    for (int m = 0; m < n; ++m) {
+        const orc_material* d = defs + m;
+        double wsum = 0.0;
+        if (d->n_elements < 1 || d->n_elements > ORC_MAX_ELEM || !(d->I_eV > 0.0) || !(d->density > 0.0)) return -1;
+        for (int i = 0; i < d->n_elements; ++i) {
+            if (d->Z[i] < 1 || d->Z[i] > 100 || !(d->A[i] > 0.0) || !(d->mass_fraction[i] >= 0.0)) return -1;
+            wsum += d->mass_fraction[i];
+        }
+        if (!(wsum > 0.0)) return -1;
+    }
+    for (int m = 0; m < n; ++m) {
+        const orc_material* d = defs + m;
+        material* M = &MAT[m];
+        memset(M, 0, sizeof(*M));
+        M->name = "user";
+        M->I_eV = d->I_eV;
+        M->rho0 = d->density;
+        M->n = d->n_elements;
+        for (int i = 0; i < d->n_elements; ++i) {
+            M->e[i].Z = d->Z[i]; M->e[i].A = d->A[i]; M->e[i].w = d->mass_fraction[i];
+        }
+        derive_material(M);
+    }
+    N_MAT = n;
+    return 0;
+}
+
+void orc_reset_materials(void)
+{
+    orc_init();
+    for (int m = 0; m < 3; ++m) MAT[m] = DEFAULT_MAT[m];
+    N_MAT = 3;
+}
+
+int orc_n_materials(void) { return N_MAT; }
 
 double orc_material_const(int m, int which)
 {
@@ -428,7 +482,7 @@ typedef struct {
     const orc_phantom* ph; const orc_params* p;
     int64_t* tally; double* ledger; uint64_t* cnt;
     uint64_t hist; int64_t nvox; double L[3]; double dd[3]; int nn[3];
-    double rho_max[3]; int present[3];
+    double rho_max[ORC_MAX_MAT]; int present[ORC_MAX_MAT];
     particle stack[STACK_MAX]; int top;
 } run_ctx;
 
@@ -494,7 +548,7 @@ static void cross_face(const run_ctx* c, particle* q, int face)
 static double photon_majorant(const run_ctx* c, double E)
 {
     double mx = 0.0;
-    for (int m = 0; m < 3; ++m)
+    for (int m = 0; m < N_MAT; ++m)
         if (c->present[m]) mx = fmax(mx, c->rho_max[m] * orc_mu(m, E, 0));
     return mx;
 }
@@ -794,10 +848,10 @@ static int setup_ctx(run_ctx* c, const orc_phantom* ph, const orc_params* p)
     c->dd[0] = ph->dx; c->dd[1] = ph->dy; c->dd[2] = ph->dz;
     for (int a = 0; a < 3; ++a) c->L[a] = c->nn[a] * c->dd[a];
     c->nvox = (int64_t)ph->nx * ph->ny * ph->nz;
-    for (int m = 0; m < 3; ++m) { c->rho_max[m] = 0.0; c->present[m] = 0; }
+    for (int m = 0; m < ORC_MAX_MAT; ++m) { c->rho_max[m] = 0.0; c->present[m] = 0; }
     for (int64_t v = 0; v < c->nvox; ++v) {
         int m = ph->material[v];
-        if (m > 2) return -1;
+        if (m >= N_MAT) return -1;
         double r = ph->density[v];
         if (!(r >= 0.0)) return -1;
         c->present[m] = 1;

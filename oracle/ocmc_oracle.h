@@ -37,11 +37,31 @@ typedef struct {
     int32_t flags;    /* ORC_* test modes                                      */
 } orc_params;
 
+/* Materials (Sec. 2.1: the per-voxel material type selects the cross-section data; the
+ * paper's database has 16 materials). By default 0 water, 1 ICRP cortical bone, 2 ICRP lung;
+ * orc_set_materials replaces them with up to ORC_MAX_MAT compositions: elements (Z, atomic
+ * mass A in g/mol, mass fraction, normalised over the elements), mean excitation energy and the
+ * nominal density that fixes the density-effect parameters. Process-wide; set before runs. */
+#define ORC_MAX_MAT  16
+#define ORC_MAX_ELEM 16
+typedef struct {
+    int32_t n_elements;
+    int32_t Z[ORC_MAX_ELEM];
+    double A[ORC_MAX_ELEM];
+    double mass_fraction[ORC_MAX_ELEM];
+    double I_eV;
+    double density;
+} orc_material;
+
+int  orc_set_materials(int n, const orc_material* defs);   /* 0, or -1 on a bad definition */
+void orc_reset_materials(void);
+int  orc_n_materials(void);
+
 typedef struct {
     int32_t nx, ny, nz;      /* voxels, x fastest                       */
     double dx, dy, dz;       /* cm                                      */
     const float* density;    /* g/cm^3, nx*ny*nz                        */
-    const uint8_t* material; /* 0 water, 1 cortical bone, 2 lung        */
+    const uint8_t* material; /* index into the materials (default 0 water, 1 bone, 2 lung) */
 } orc_phantom;
 
 typedef struct {
