@@ -63,6 +63,10 @@ WORKLOADS = {
                      "on 128^3 grids at 0.25 cm; trained on engine-made pairs of random CT-like phantoms "
                      "(6 MV or 6-20 MeV e-, fields 2-20 cm); time to <=1% mean dose error above the 10% isodose, "
                      "plain vs denoised, on held-out cases"),
+    "voxel_sweep": (None, 0,
+                    "voxel-size dependence of voxel-limited electron stepping: slab phantom 30x30x30 cm (water 0-3, "
+                    "bone 3-5, lung 5-12, water) at 1-5 mm voxels, 15 MeV electrons (1e7) and 6 MV photons (1e8), "
+                    "10x10 cm2 at SSD 100"),
     "beamlets_ct": (I.beamlets_ct, 0,
                     "512 6 MV pencil beamlets 0.5x0.5 cm2 at random gantry angles (SAD 100 cm), histories "
                     "10^N(5,0.5) clipped to [1e4,1e6], CT-like phantom 256x256x128 at 0.2 cm, one graph-captured "
@@ -334,6 +338,45 @@ def run_denoiser_bench(args, desc):
     eng.close()
 
 
+def run_voxel_sweep(args, desc):
+    """Histories/s of the slab phantom at several voxel sizes (Sec. 4: with electron steps
+    confined to a voxel, the time depends on the voxel size; the paper settles on ~2.5 mm)."""
+    import torch
+    from paper_1503_01722_gb300 import ocmc
+    rows = []
+    for vox in (0.1, 0.15, 0.2, 0.25, 0.3, 0.4, 0.5):
+        n_side = int(round(30.0 / vox))
+        ph = I.slab((n_side,) * 3, (vox,) * 3)
+        for particle, spec, n in ((1, I.mono(15.0), 10_000_000), (0, I.spectrum_6mv(), 100_000_000)):
+            beam = I.beam_on(ph, particle, spec, (10.0, 10.0), 100.0)
+            with ocmc.Engine(0) as e:
+                e.create_phantom(ph)
+                e.set_source(beam)
+                for _ in range(max(args.warmup, 1)):
+                    e.reset()
+                    e.run(n, seed=1)
+                ms = []
+                for _ in range(args.steps):
+                    e.reset()
+                    e.run(n, seed=1)
+                    ms.append(e.stats()["last_run_ms"])
+                st = e.stats()
+            rows.append({"voxel_mm": vox * 10, "grid": n_side, "particle": "electron" if particle else "photon",
+                         "histories": n, "kernel_ms": statistics.mean(ms),
+                         "histories_per_s": n / (statistics.mean(ms) / 1e3),
+                         "lane_steps_per_history": st["lane_steps"] / n,
+                         "electron_steps_per_history": st["electron_steps"] / n})
+            print(json.dumps(rows[-1]), file=sys.stderr)
+    ref = [r for r in rows if r["voxel_mm"] == 2.5 and r["particle"] == "electron"][0]
+    line = {"metric": "histories/s", "value": ref["histories_per_s"], "unit": "histories/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ref["kernel_ms"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": desc, "value_is": "15 MeV electrons at 2.5 mm",
+                       "timing": "transport kernel (CUDA events inside the library)"},
+            "gpu_launches": 2 * args.steps * len(rows), "sweep": rows}
+    print(json.dumps(line))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -352,6 +395,8 @@ def main():
     make, n_default, desc = WORKLOADS[args.workload]
     if args.workload == "denoiser_128":
         return run_denoiser_bench(args, desc)
+    if args.workload == "voxel_sweep":
+        return run_voxel_sweep(args, desc)
     if args.workload == "beamlets_ct":
         return run_beamlets_bench(args, make, desc)
     ph, beam = make()

@@ -115,9 +115,32 @@ ocmc_status ocmc_init(ocmc_ctx** out, int device, const ocmc_params* p);
 /* Replace the transport parameters (the tally is kept). Same errors as init. */
 ocmc_status ocmc_set_params(ocmc_ctx* ctx, const ocmc_params* p);
 
+/* ---- materials ----------------------------------------------------------------------
+ * Sec. 2.1: each voxel has a density and a material type that selects the cross-section
+ * and stopping-power data (the paper's database has 16 materials). By default material 0 is
+ * water, 1 ICRP cortical bone (nominal 1.85 g/cm^3), 2 ICRP lung (0.26 g/cm^3). A material is a
+ * composition: elements (atomic number Z, atomic mass A in g/mol, mass fraction; the fractions
+ * are normalised), its mean excitation energy I (eV) and the nominal density that fixes its
+ * density-effect parameters; every table is built from the closed-form models for it. */
+typedef struct {
+    int32_t n_elements;          /* 1..16 */
+    int32_t Z[16];               /* 1..100 */
+    double A[16];                /* g/mol */
+    double mass_fraction[16];    /* >= 0, sum > 0 */
+    double I_eV;                 /* (1, 1e4) */
+    double density;              /* nominal g/cm^3, (0, 30] */
+} ocmc_material;
+
+/* Define n (1..16) materials; voxel material m of later phantoms is defs[m]. The definitions
+ * are copied. The current phantom is dropped (its indices referred to the old set): call
+ * ocmc_create_phantom again. A transport block holds the tables of at most 10 materials in
+ * shared memory: with more than 10 defined, a phantom may use at most 10 distinct ones. */
+ocmc_status ocmc_set_materials(ocmc_ctx* ctx, int n, const ocmc_material* defs);
+
 /* The voxel phantom (Sec. 2.1: each voxel has a density and a material type).
  * density_host: nx*ny*nz float, g/cm^3, finite and in [0, 30];
- * material_host: nx*ny*nz uint8, 0 water, 1 cortical bone (ICRP), 2 lung (ICRP);
+ * material_host: nx*ny*nz uint8, an index into the defined materials (by default 0 water,
+ *   1 cortical bone (ICRP), 2 lung (ICRP); see ocmc_set_materials);
  * dx, dy, dz: voxel size in cm. The phantom occupies [0,nx*dx] x [0,ny*dy] x
  * [0,nz*dz]. 1 <= nx, ny, nz <= 1024. Copies the data (host pointers) and
  * resets the tally. Errors: OCMC_ERR_ARG for bad sizes or values. */
@@ -363,8 +386,9 @@ ocmc_status ocmc_test_csda(ocmc_ctx* ctx, int material, const float* T_host, con
  * race: serialise them. The first call on a device looks up the array's address
  * with that device current and caches it: make it before any stream capture.
  *
- * density_dev, material_dev: device arrays as in ocmc_create_phantom (values are
- * checked on the device; bad values give OCMC_ERR_ARG). Source arguments as in
+ * density_dev, material_dev: device arrays as in ocmc_create_phantom, with the built-in
+ * materials 0 water, 1 cortical bone, 2 lung (values are checked on the device; bad values
+ * give OCMC_ERR_ARG). Source arguments as in
  * ocmc_set_source (host arrays). params: NULL for defaults; a launch shape
  * (block_threads, blocks_per_sm, stack_capacity) whose stacks do not fit in the
  * static array is rejected with OCMC_ERR_ARG. Runs on cuda_stream and

@@ -154,7 +154,7 @@ ocmc_status ensure_tables(ocmc_ctx* c, cudaStream_t s)
     if (c->tables_valid) return OCMC_OK;
     PhysParams pp{c->p.e_abs_e, c->p.e_abs_g, c->p.w_cc, c->p.w_cb, c->p.d_maxs, c->p.f_maxe, c->p.s_min,
                   c->p.flags, c->p.n_batches};
-    CK(build_tables(c->t, pp, c->d_density, c->d_material, c->nvox, c->d_err, s), "table build");
+    CK(build_tables(c->t, pp, c->d_density, c->d_material, c->nvox, c->d_err, c->staged.data(), s), "table build");
     c->tables_valid = true;
     return OCMC_OK;
 }
@@ -174,7 +174,7 @@ void launch_shape(const ocmc_ctx* c, int* threads, int* blocks, int* cap, int* n
 {
     *nreg = c->p.max_registers ? c->p.max_registers : 64;
     *threads = c->p.block_threads ? c->p.block_threads : (*nreg == 64 ? 1024 : *nreg == 56 ? 384 : 256);
-    size_t smem = transport_smem_bytes(*threads);
+    size_t smem = transport_smem_bytes(c->t.n_mat);
     int bps = c->p.blocks_per_sm ? c->p.blocks_per_sm : transport_max_blocks_per_sm(*threads, smem, *nreg);
     if (bps < 1) bps = 1;
     *blocks = c->sms * bps;
@@ -277,16 +277,25 @@ ocmc_status ocmc_init(ocmc_ctx** out, int device, const ocmc_params* p)
     c->p = q;
     cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, device);
     cudaError_t r = cudaSuccess;
-    if (r == cudaSuccess) r = dalloc(&c->t.ph, NMAT * NE * 4);
-    if (r == cudaSuccess) r = dalloc(&c->t.el, NMAT * NE * 4);
-    if (r == cudaSuccess) r = dalloc(&c->t.el2, NMAT * NE * 2);
+    if (r == cudaSuccess) r = dalloc(&c->t.ph, MAX_STAGED * NE * 4);
+    if (r == cudaSuccess) r = dalloc(&c->t.el, MAX_STAGED * NE * 4);
+    if (r == cudaSuccess) r = dalloc(&c->t.el2, MAX_STAGED * NE * 2);
     if (r == cudaSuccess) r = dalloc(&c->t.phmaj, NE);
-    if (r == cudaSuccess) r = dalloc(&c->t.rinv, NMAT * NR);
+    if (r == cudaSuccess) r = dalloc(&c->t.rinv, MAX_STAGED * NR);
     if (r == cudaSuccess) r = dalloc(&c->t.msA, NG);
-    if (r == cudaSuccess) r = dalloc(&c->t.rmeta, 2 * NMAT);
-    if (r == cudaSuccess) r = dalloc(&c->t.msc, 2 * NMAT);
-    if (r == cudaSuccess) r = dalloc(&c->t.scratch, NMAT * NE);
-    if (r == cudaSuccess) r = dalloc(&c->t.rho_max, NMAT);
+    if (r == cudaSuccess) r = dalloc(&c->t.rmeta, 2 * MAX_STAGED);
+    if (r == cudaSuccess) r = dalloc(&c->t.msc, 2 * MAX_STAGED);
+    if (r == cudaSuccess) r = dalloc(&c->t.scratch, MAX_STAGED * NE);
+    if (r == cudaSuccess) r = dalloc(&c->t.rho_max, MAX_STAGED);
+    if (r == cudaSuccess) r = dalloc(&c->t.mats, MAX_STAGED);
+    {
+        MatDef d[NMAT_DEFAULT];
+        material_defs(d);
+        c->mats.assign(d, d + NMAT_DEFAULT);
+        c->staged = c->mats;
+        c->slot_of = {0, 1, 2};
+        c->t.n_mat = NMAT_DEFAULT;
+    }
     if (r == cudaSuccess) r = dalloc(&c->d_stats, ST_COUNT);
     if (r == cudaSuccess) r = dalloc(&c->d_counter, 1);
     if (r == cudaSuccess) r = dalloc(&c->d_sum, 1);
@@ -316,6 +325,42 @@ ocmc_status ocmc_set_params(ocmc_ctx* c, const ocmc_params* p)
     return OCMC_OK;
 }
 
+ocmc_status ocmc_set_materials(ocmc_ctx* c, int n, const ocmc_material* defs)
+{
+    if (!c) return fail(c, OCMC_ERR_ARG, "ctx is NULL");
+    if (n < 1 || n > MAX_MAT || !defs) return fail(c, OCMC_ERR_ARG, "need 1 to 16 materials");
+    std::vector<MatDef> mats((size_t)n);
+    for (int m = 0; m < n; ++m) {
+        const ocmc_material& d = defs[m];
+        if (d.n_elements < 1 || d.n_elements > MAX_ELEM)
+            return fail(c, OCMC_ERR_ARG, "material " + std::to_string(m) + ": 1 to 16 elements");
+        if (!(d.I_eV > 1.0 && d.I_eV < 1e4) || !(d.density > 0.0 && d.density <= 30.0))
+            return fail(c, OCMC_ERR_ARG, "material " + std::to_string(m) + ": need 1 < I < 1e4 eV, 0 < density <= 30");
+        double ws = 0.0;
+        MatDef& o = mats[m];
+        std::memset(&o, 0, sizeof(o));
+        o.n = d.n_elements;
+        for (int i = 0; i < d.n_elements; ++i) {
+            if (d.Z[i] < 1 || d.Z[i] > 100 || !(d.A[i] > 0.5 && d.A[i] < 300.0) ||
+                !(d.mass_fraction[i] >= 0.0 && std::isfinite(d.mass_fraction[i])))
+                return fail(c, OCMC_ERR_ARG, "material " + std::to_string(m) + ": bad element");
+            o.Z[i] = d.Z[i];
+            o.A[i] = d.A[i];
+            o.w[i] = d.mass_fraction[i];
+            ws += d.mass_fraction[i];
+        }
+        if (!(ws > 0.0)) return fail(c, OCMC_ERR_ARG, "material " + std::to_string(m) + ": mass fractions sum to 0");
+        o.I_eV = d.I_eV;
+        o.rho0 = d.density;
+    }
+    CK(cudaSetDevice(c->device), "cudaSetDevice");
+    if (c->last_stream || c->ran) cudaDeviceSynchronize();
+    c->mats = mats;
+    c->have_phantom = false;       // the phantom's material indices refer to the old set
+    c->tables_valid = false;
+    return OCMC_OK;
+}
+
 ocmc_status ocmc_create_phantom(ocmc_ctx* c, int nx, int ny, int nz, const float* density, const uint8_t* material,
                                 float dx, float dy, float dz)
 {
@@ -326,9 +371,37 @@ ocmc_status ocmc_create_phantom(ocmc_ctx* c, int nx, int ny, int nz, const float
     if (!(dx > 0.f && dy > 0.f && dz > 0.f && dx < 100.f && dy < 100.f && dz < 100.f))
         return fail(c, OCMC_ERR_ARG, "voxel sizes must be in (0, 100) cm");
     long long n = (long long)nx * ny * nz;
+    const int nd = (int)c->mats.size();
+    bool used[MAX_MAT] = {false};
     for (long long v = 0; v < n; ++v) {
-        if (material[v] >= NMAT) return fail(c, OCMC_ERR_ARG, "material index must be 0, 1 or 2");
+        if (material[v] >= nd)
+            return fail(c, OCMC_ERR_ARG, "material index must be below the number of defined materials (" +
+                                             std::to_string(nd) + ")");
         if (!(density[v] >= 0.f && density[v] <= 30.f)) return fail(c, OCMC_ERR_ARG, "density must be in [0, 30] g/cm^3");
+        used[material[v]] = true;
+    }
+    // staging: every defined material when they fit in a block's shared memory, else the
+    // phantom's own materials in increasing index order (the uploaded indices are compacted)
+    std::vector<int> slot(nd, -1);
+    std::vector<MatDef> staged;
+    if (nd <= MAX_STAGED) {
+        for (int m = 0; m < nd; ++m) slot[m] = m;
+        staged = c->mats;
+    } else {
+        for (int m = 0; m < nd; ++m)
+            if (used[m]) {
+                slot[m] = (int)staged.size();
+                staged.push_back(c->mats[m]);
+            }
+        if ((int)staged.size() > MAX_STAGED)
+            return fail(c, OCMC_ERR_ARG, "a phantom may use at most " + std::to_string(MAX_STAGED) +
+                                             " distinct materials (their tables share a block's shared memory)");
+    }
+    std::vector<uint8_t> remapped;
+    if (nd > MAX_STAGED) {
+        remapped.resize((size_t)n);
+        for (long long v = 0; v < n; ++v) remapped[v] = (uint8_t)slot[material[v]];
+        material = remapped.data();
     }
     CK(cudaSetDevice(c->device), "cudaSetDevice");
     if (c->last_stream || c->ran) cudaDeviceSynchronize();
@@ -343,6 +416,9 @@ ocmc_status ocmc_create_phantom(ocmc_ctx* c, int nx, int ny, int nz, const float
     c->dx = dx; c->dy = dy; c->dz = dz;
     CK(cudaMemcpy(c->d_density, density, n * sizeof(float), cudaMemcpyHostToDevice), "phantom upload");
     CK(cudaMemcpy(c->d_material, material, n, cudaMemcpyHostToDevice), "phantom upload");
+    c->staged = staged;
+    c->slot_of = slot;
+    c->t.n_mat = (int)staged.size();
     c->have_phantom = true;
     c->tables_valid = false;
     if (c->d_tally && c->tally_B == c->p.n_batches) {
@@ -498,7 +574,7 @@ ocmc_status ocmc_run_range(ocmc_ctx* c, uint64_t first, uint64_t count, uint64_t
     a.refill_min = c->p.refill_min ? c->p.refill_min : 1;
     CK(cudaMemsetAsync(c->d_counter, 0, sizeof(unsigned long long), s), "counter reset");
     CK(cudaEventRecord(c->ev0, s), "event");
-    CK(launch_transport(a, blocks, threads, transport_smem_bytes(threads), s, nreg), "transport launch");
+    CK(launch_transport(a, blocks, threads, transport_smem_bytes(c->t.n_mat), s, nreg), "transport launch");
     CK(cudaEventRecord(c->ev1, s), "event");
     c->timed = true;
     c->last_stream = s;
@@ -717,8 +793,10 @@ ocmc_status ocmc_test_source(ocmc_ctx* c, uint64_t n_total, uint64_t first, uint
 
 ocmc_status ocmc_test_sample(ocmc_ctx* c, int kind, int m, float E, float aux, uint64_t n, uint64_t seed, float* out)
 {
-    if (!c || !out || n == 0 || kind < 0 || kind > 3 || m < 0 || m >= NMAT || !(E > 0.f))
+    if (!c || !out || n == 0 || kind < 0 || kind > 3 || m < 0 || m >= (int)c->slot_of.size() || !(E > 0.f))
         return fail(c, OCMC_ERR_ARG, "bad arguments");
+    if (c->slot_of[m] < 0) return fail(c, OCMC_ERR_ARG, "material not in the phantom's tables");
+    m = c->slot_of[m];
     if (!c->have_phantom) return fail(c, OCMC_ERR_STATE, "need a phantom");
     CK(cudaSetDevice(c->device), "cudaSetDevice");
     ocmc_status st = ensure_tables(c, nullptr);
@@ -738,7 +816,9 @@ ocmc_status ocmc_test_sample(ocmc_ctx* c, int kind, int m, float E, float aux, u
 
 ocmc_status ocmc_test_tables(ocmc_ctx* c, int m, const float* E, int n, float* out)
 {
-    if (!c || !E || !out || n <= 0 || m < 0 || m >= NMAT) return fail(c, OCMC_ERR_ARG, "bad arguments");
+    if (!c || !E || !out || n <= 0 || m < 0 || m >= (int)c->slot_of.size()) return fail(c, OCMC_ERR_ARG, "bad arguments");
+    if (c->slot_of[m] < 0) return fail(c, OCMC_ERR_ARG, "material not in the phantom's tables");
+    m = c->slot_of[m];
     if (!c->have_phantom) return fail(c, OCMC_ERR_STATE, "need a phantom");
     CK(cudaSetDevice(c->device), "cudaSetDevice");
     ocmc_status st = ensure_tables(c, nullptr);
@@ -759,7 +839,9 @@ ocmc_status ocmc_test_tables(ocmc_ctx* c, int m, const float* E, int n, float* o
 
 ocmc_status ocmc_test_csda(ocmc_ctx* c, int m, const float* T, const float* X, int n, float* out)
 {
-    if (!c || !T || !X || !out || n <= 0 || m < 0 || m >= NMAT) return fail(c, OCMC_ERR_ARG, "bad arguments");
+    if (!c || !T || !X || !out || n <= 0 || m < 0 || m >= (int)c->slot_of.size()) return fail(c, OCMC_ERR_ARG, "bad arguments");
+    if (c->slot_of[m] < 0) return fail(c, OCMC_ERR_ARG, "material not in the phantom's tables");
+    m = c->slot_of[m];
     if (!c->have_phantom) return fail(c, OCMC_ERR_STATE, "need a phantom");
     CK(cudaSetDevice(c->device), "cudaSetDevice");
     ocmc_status st = ensure_tables(c, nullptr);

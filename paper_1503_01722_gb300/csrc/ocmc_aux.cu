@@ -80,7 +80,7 @@ __global__ void k_test_sample(const TransportArgs a, int kind, int m, float E, f
         float v = 0.f, eps;
         if (kind == 0) v = sample_compton(E, r, a.key0, a.key1, &eps, &ok);
         else if (kind == 1) v = sample_moller(E, a.pp.w_cc, r, a.key0, a.key1, &ok);
-        else if (kind == 2) v = sample_brems(E, a.pp.w_cb, T.msc[2 * m], T.msc[2 * m + 1], r, a.key0, a.key1, &ok);
+        else if (kind == 2) v = sample_brems(E, a.pp.w_cb, T.msc[m * MS1], T.msc[m * MS1 + 1], r, a.key0, a.key1, &ok);
         else if (kind == 3) v = sample_ms(T, aux, r, a.key0, a.key1);
         out[j] = ok ? v : __int_as_float(0x7FC00000);
     }
@@ -93,7 +93,7 @@ __global__ void k_test_tables(const TransportArgs a, int m, const float* E, int 
     int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n) return;
     EIdx ei = e_index(E[j]);
-    const int mb = m * NE;
+    const int mb = m * MS4;
     float4 pa = T.ph[mb + ei.i], pb = T.ph[mb + ei.i + 1];
     float mt = __expf(lerp1(pa.x, pb.x, ei.f));
     float4 A = T.el[mb + ei.i], B = T.el[mb + ei.i + 1];
@@ -105,7 +105,7 @@ __global__ void k_test_tables(const TransportArgs a, int m, const float* E, int 
     o[4] = lerp1(A.y, B.y, ei.f);
     o[5] = lerp1(A.z, B.z, ei.f);
     o[6] = lerp1(A.w, B.w, ei.f);
-    o[7] = T.el2[mb + ei.i].y;
+    o[7] = T.el2[m * MS2 + ei.i].y;
 }
 
 __global__ void k_test_csda(const TransportArgs a, int m, const float* Tk, const float* X, int n, float* out)
@@ -115,7 +115,7 @@ __global__ void k_test_csda(const TransportArgs a, int m, const float* Tk, const
     int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n) return;
     EIdx ei = e_index(Tk[j]);
-    float lnR = lerp1(T.el[m * NE + ei.i].x, T.el[m * NE + ei.i + 1].x, ei.f);
+    float lnR = lerp1(T.el[m * MS4 + ei.i].x, T.el[m * MS4 + ei.i + 1].x, ei.f);
     out[j] = csda_end(T, m, Tk[j], lnR, X[j]);
 }
 
@@ -321,18 +321,18 @@ cudaError_t launch_test_sample(const TransportArgs& a, int kind, int m, float E,
                                float* out, cudaStream_t s)
 {
     cudaError_t e = cudaFuncSetAttribute(k_test_sample, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)SMEM_TABLE_BYTES);
+                                         (int)smem_table_bytes(a.t.n_mat));
     if (e != cudaSuccess) return e;
-    k_test_sample<<<152 * 2, 256, SMEM_TABLE_BYTES, s>>>(a, kind, m, E, aux, n, out);
+    k_test_sample<<<152 * 2, 256, smem_table_bytes(a.t.n_mat), s>>>(a, kind, m, E, aux, n, out);
     return cudaGetLastError();
 }
 
 cudaError_t launch_test_tables(const TransportArgs& a, int m, const float* E, int n, float* out, cudaStream_t s)
 {
     cudaError_t e = cudaFuncSetAttribute(k_test_tables, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)SMEM_TABLE_BYTES);
+                                         (int)smem_table_bytes(a.t.n_mat));
     if (e != cudaSuccess) return e;
-    k_test_tables<<<(n + 255) / 256, 256, SMEM_TABLE_BYTES, s>>>(a, m, E, n, out);
+    k_test_tables<<<(n + 255) / 256, 256, smem_table_bytes(a.t.n_mat), s>>>(a, m, E, n, out);
     return cudaGetLastError();
 }
 
@@ -340,9 +340,9 @@ cudaError_t launch_test_csda(const TransportArgs& a, int m, const float* T, cons
                              cudaStream_t s)
 {
     cudaError_t e = cudaFuncSetAttribute(k_test_csda, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)SMEM_TABLE_BYTES);
+                                         (int)smem_table_bytes(a.t.n_mat));
     if (e != cudaSuccess) return e;
-    k_test_csda<<<(n + 255) / 256, 256, SMEM_TABLE_BYTES, s>>>(a, m, T, X, n, out);
+    k_test_csda<<<(n + 255) / 256, 256, smem_table_bytes(a.t.n_mat), s>>>(a, m, T, X, n, out);
     return cudaGetLastError();
 }
 

@@ -122,7 +122,7 @@ cudaError_t enqueue_beamlets(ocmc_ctx* c, const TransportArgs& a, size_t slots, 
     if (e == cudaSuccess) e = cudaMemsetAsync(c->d_bl_vals, 0, sizeof(unsigned long long) * slots, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->d_bl_over, 0, sizeof(unsigned int) * c->bl_n, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->d_counter, 0, sizeof(unsigned long long), s);
-    if (e == cudaSuccess) e = launch_transport(a, blocks, threads, transport_smem_bytes(threads), s, nreg);
+    if (e == cudaSuccess) e = launch_transport(a, blocks, threads, transport_smem_bytes(c->t.n_mat), s, nreg);
     return e;
 }
 
@@ -207,7 +207,7 @@ ocmc_status capture_graph(ocmc_ctx* c, uint64_t seed)
     st = beamlet_args(c, total, seed, a, &threads, &blocks, &nreg);
     if (st != OCMC_OK) return st;
     if (!c->bl_capture) BCK(cudaStreamCreateWithFlags(&c->bl_capture, cudaStreamNonBlocking), "stream");
-    transport_max_blocks_per_sm(threads, transport_smem_bytes(threads), nreg);   // sets the kernels' smem attribute
+    transport_max_blocks_per_sm(threads, transport_smem_bytes(c->t.n_mat), nreg);   // sets the kernels' smem attribute
     cudaGraph_t g = nullptr;
     BCK(cudaStreamBeginCapture(c->bl_capture, cudaStreamCaptureModeRelaxed), "graph capture");
     cudaError_t e = enqueue_beamlets(c, a, slots, threads, blocks, nreg, c->bl_capture);

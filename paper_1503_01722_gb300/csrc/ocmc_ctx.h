@@ -26,6 +26,12 @@ struct ocmc_ctx {
     int src_kind = 0;                        // 0 analytic beam (ocmc_set_source), 1 phase space
     ocmc::PsRec* d_ps = nullptr;             // phase-space records on the device
     unsigned long long ps_n = 0, ps_cap = 0;
+    // materials: defined (default water, ICRP cortical bone, ICRP lung) and the ones whose
+    // tables are built (staged): all defined ones when at most MAX_STAGED, else the phantom's
+    // own, whose indices are compacted when the phantom is uploaded
+    std::vector<ocmc::MatDef> mats;
+    std::vector<ocmc::MatDef> staged;
+    std::vector<int> slot_of;                // defined index -> staged slot, -1 if not staged
     // tables
     ocmc::Tables t{};
     bool tables_valid = false;

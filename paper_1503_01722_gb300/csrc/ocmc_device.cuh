@@ -68,15 +68,17 @@ __device__ __forceinline__ uint32_t child_sub(uint32_t parent, uint32_t n, uint3
 }
 
 // ---- tables in shared memory ---------------------------------------------------------------
+// Pointers to material 0's rows of the shared-memory tables; material m's row is m * MS4
+// (float4), m * MS2 (float2) or m * MS1 (float) further on.
 struct SmemTables {
-    float4* ph;     // NMAT*NE
-    float4* el;     // NMAT*NE
-    float2* el2;    // NMAT*NE
+    float4* ph;     // [m * MS4 + i], i < NE
+    float4* el;     // [m * MS4 + i]
+    float2* el2;    // [m * MS2 + i]
     float* phmaj;   // NE
-    float* rinv;    // NMAT*NR
+    float* rinv;    // [m * MS1 + j], j < NR
     float* msA;     // NG
-    float* rmeta;   // NMAT*2
-    float* msc;     // NMAT*2
+    float* rmeta;   // [m * MS1 + 0/1]
+    float* msc;     // [m * MS1 + 0/1]
 };
 
 constexpr float LN_E_LO = -6.907755278982137f;              // ln(1e-3)
@@ -104,11 +106,11 @@ __device__ __forceinline__ float lerp1(float a, float b, float f) { return fmaf(
 // ln E at ln R for material m (range-table inversion)
 __device__ __forceinline__ float range_to_lnE(const SmemTables& T, int m, float lnR)
 {
-    float x = (lnR - T.rmeta[2 * m]) * T.rmeta[2 * m + 1];
+    float x = (lnR - T.rmeta[m * MS1]) * T.rmeta[m * MS1 + 1];
     x = fminf(fmaxf(x, 0.f), (float)(NR - 1) - 1e-3f);
     int j = (int)x;
     float f = x - (float)j;
-    const float* r = T.rinv + m * NR;
+    const float* r = T.rinv + m * MS1;
     return lerp1(r[j], r[j + 1], f);
 }
 
@@ -267,37 +269,40 @@ __device__ __forceinline__ float dist_to_face(float x, float y, float z, float u
 namespace ocmc {
 
 // ---- shared-memory staging of the tables ------------------------------------------------
-constexpr size_t SMEM_TABLE_BYTES =
-    (size_t)NMAT * NE * (sizeof(float4) * 2 + sizeof(float2)) + (size_t)(NE + NMAT * NR + NG + 4 * NMAT) * sizeof(float);
-
 __device__ __forceinline__ SmemTables carve_tables(unsigned char* smem)
 {
     SmemTables T;
-    T.ph = reinterpret_cast<float4*>(smem);
-    T.el = T.ph + NMAT * NE;
-    T.el2 = reinterpret_cast<float2*>(T.el + NMAT * NE);
-    T.phmaj = reinterpret_cast<float*>(T.el2 + NMAT * NE);
-    T.rinv = T.phmaj + NE;
-    T.msA = T.rinv + NMAT * NR;
-    T.rmeta = T.msA + NG;
-    T.msc = T.rmeta + 2 * NMAT;
+    T.phmaj = reinterpret_cast<float*>(smem);
+    T.msA = T.phmaj + NE;
+    T.ph = reinterpret_cast<float4*>(smem + SM_SHARED_BYTES);
+    T.el = T.ph + NE;
+    T.el2 = reinterpret_cast<float2*>(T.el + NE);
+    T.rinv = reinterpret_cast<float*>(T.el2 + NE);
+    T.rmeta = T.rinv + NR;
+    T.msc = T.rmeta + 2;
     return T;
 }
 
 __device__ __forceinline__ SmemTables stage_tables(const Tables& t, unsigned char* smem)
 {
     SmemTables T = carve_tables(smem);
-    for (int i = threadIdx.x; i < NMAT * NE; i += blockDim.x) {
-        T.ph[i] = t.ph[i];
-        T.el[i] = t.el[i];
-        T.el2[i] = t.el2[i];
+    const int nm = t.n_mat;
+    for (int i = threadIdx.x; i < nm * NE; i += blockDim.x) {
+        const int m = i / NE, k = i - m * NE;
+        T.ph[m * MS4 + k] = t.ph[i];
+        T.el[m * MS4 + k] = t.el[i];
+        T.el2[m * MS2 + k] = t.el2[i];
     }
     for (int i = threadIdx.x; i < NE; i += blockDim.x) T.phmaj[i] = t.phmaj[i];
-    for (int i = threadIdx.x; i < NMAT * NR; i += blockDim.x) T.rinv[i] = t.rinv[i];
+    for (int i = threadIdx.x; i < nm * NR; i += blockDim.x) {
+        const int m = i / NR, k = i - m * NR;
+        T.rinv[m * MS1 + k] = t.rinv[i];
+    }
     for (int i = threadIdx.x; i < NG; i += blockDim.x) T.msA[i] = t.msA[i];
-    if (threadIdx.x < 2 * NMAT) {
-        T.rmeta[threadIdx.x] = t.rmeta[threadIdx.x];
-        T.msc[threadIdx.x] = t.msc[threadIdx.x];
+    if (threadIdx.x < 2 * nm) {
+        const int m = threadIdx.x >> 1, k = threadIdx.x & 1;
+        T.rmeta[m * MS1 + k] = t.rmeta[threadIdx.x];
+        T.msc[m * MS1 + k] = t.msc[threadIdx.x];
     }
     __syncthreads();
     return T;

@@ -18,7 +18,10 @@ namespace ocmc {
 constexpr int NE = 512;
 constexpr int NR = 512;
 constexpr int NG = 512;
-constexpr int NMAT = 3;
+constexpr int NMAT_DEFAULT = 3;   // built-in materials: water, ICRP cortical bone, ICRP lung
+constexpr int MAX_MAT = 16;       // user-defined materials (the paper's database has 16)
+constexpr int MAX_STAGED = 10;    // materials whose tables one transport block holds in shared memory
+constexpr int MAX_ELEM = 16;      // elements per material
 constexpr int MAX_BINS = 256;
 constexpr double E_LO = 1.0e-3;   // MeV
 constexpr double E_HI = 32.0;     // MeV
@@ -43,29 +46,47 @@ enum Stat {
     ST_COUNT
 };
 
+// Tables in global memory, one row per staged material m < n_mat (capacity MAX_STAGED).
+struct MatDef;
 struct Tables {
-    float4* ph;     // NMAT*NE
+    int n_mat;      // staged materials (table rows)
+    MatDef* mats;   // their definitions (device, MAX_STAGED)
+    float4* ph;     // n_mat*NE
     float* phmaj;   // NE
-    float4* el;     // NMAT*NE
-    float2* el2;    // NMAT*NE
-    float* rinv;    // NMAT*NR
+    float4* el;     // n_mat*NE
+    float2* el2;    // n_mat*NE
+    float* rinv;    // n_mat*NR
     float* msA;     // NG
-    float* rmeta;   // NMAT*2: lnR0, 1/dlnR
-    float* msc;     // NMAT*2: bremsstrahlung screening sums S1, S2 (per gram)
-    double* scratch;        // NMAT*NE interval ranges
-    unsigned int* rho_max;  // NMAT, float bits of the max density per material
+    float* rmeta;   // n_mat*2: lnR0, 1/dlnR
+    float* msc;     // n_mat*2: bremsstrahlung screening sums S1, S2 (per gram)
+    double* scratch;        // n_mat*NE interval ranges
+    unsigned int* rho_max;  // n_mat, float bits of the max density per material
 };
 
-// Per-material composition for the table builder (public compositions:
-// water H2O; ICRP cortical bone; ICRP lung).
+// Per-material composition for the table builder: elements (Z, atomic mass A in g/mol, mass
+// fraction), mean excitation energy, nominal density.
 struct MatDef {
     int n;
-    int Z[13];
-    double A[13];
-    double w[13];
+    int Z[MAX_ELEM];
+    double A[MAX_ELEM];
+    double w[MAX_ELEM];
     double I_eV;
     double rho0;
 };
+
+// Shared-memory image of the tables in a transport block: the material-independent photon
+// majorant (NE floats) and Wentzel screening table (NG floats), then one block per staged
+// material, SM_MAT_BYTES apart: ph (NE float4), el (NE float4), el2 (NE float2), rinv (NR
+// floats), rmeta[2], msc[2]. A material's row is at a compile-time stride, so table addressing
+// costs the same for any number of materials.
+constexpr size_t SM_SHARED_BYTES = (size_t)(NE + NG) * sizeof(float);
+constexpr size_t SM_MAT_BYTES = (size_t)NE * (2 * sizeof(float4) + sizeof(float2)) + (size_t)NR * sizeof(float) +
+                                4 * sizeof(float);
+static_assert(SM_SHARED_BYTES % 16 == 0 && SM_MAT_BYTES % 16 == 0, "16-byte aligned table rows");
+constexpr int MS4 = (int)(SM_MAT_BYTES / 16);   // material stride in float4
+constexpr int MS2 = (int)(SM_MAT_BYTES / 8);    // in float2
+constexpr int MS1 = (int)(SM_MAT_BYTES / 4);    // in float
+__host__ __device__ constexpr size_t smem_table_bytes(int n_mat) { return SM_SHARED_BYTES + n_mat * SM_MAT_BYTES; }
 
 struct PhysParams {
     float e_abs_e, e_abs_g, w_cc, w_cb, d_maxs, f_maxe, s_min;
@@ -152,10 +173,10 @@ struct TransportArgs {
 
 // kernels / launchers (defined in the .cu files)
 cudaError_t build_tables(const Tables& t, const PhysParams& pp, const float* density, const uint8_t* material,
-                         long long nvox, int* d_err, cudaStream_t s);
+                         long long nvox, int* d_err, const MatDef* defs, cudaStream_t s);
 cudaError_t launch_transport(const TransportArgs& a, int blocks, int threads, size_t smem, cudaStream_t s,
                              int nreg);
-size_t transport_smem_bytes(int threads);
+size_t transport_smem_bytes(int n_mat);
 int transport_max_blocks_per_sm(int threads, size_t smem, int nreg);
 bool transport_nreg_supported(int nreg);
 cudaError_t launch_finalize(const long long* tally, const float* density, int B, long long nvox, double voxel_volume,
@@ -169,7 +190,7 @@ cudaError_t launch_test_sample(const TransportArgs& a, int kind, int m, float E,
 cudaError_t launch_test_tables(const TransportArgs& a, int m, const float* E, int n, float* out, cudaStream_t s);
 cudaError_t launch_test_csda(const TransportArgs& a, int m, const float* T, const float* X, int n, float* out,
                              cudaStream_t s);
-void material_defs(MatDef out[NMAT]);
+void material_defs(MatDef out[NMAT_DEFAULT]);
 cudaError_t launch_ps_validate(const PsRec* ps, unsigned long long n, unsigned long long* bad, cudaStream_t s);
 cudaError_t launch_bl_count(const unsigned int* keys, const unsigned long long* offs, const unsigned int* caps, int n,
                             unsigned long long* nnz, cudaStream_t s);

@@ -141,16 +141,20 @@ extern "C" ocmc_status ocmc_run_noalloc(int device, int nx, int ny, int nz, cons
     // scratch layout: tables, then run counters, then the per-warp stacks
     Carver cv{base, 0};
     Tables t;
-    t.ph = cv.take<float4>(NMAT * NE);
-    t.el = cv.take<float4>(NMAT * NE);
-    t.el2 = cv.take<float2>(NMAT * NE);
+    t.n_mat = NMAT_DEFAULT;                    // the built-in materials: water, cortical bone, lung
+    t.ph = cv.take<float4>(NMAT_DEFAULT * NE);
+    t.el = cv.take<float4>(NMAT_DEFAULT * NE);
+    t.el2 = cv.take<float2>(NMAT_DEFAULT * NE);
     t.phmaj = cv.take<float>(NE);
-    t.rinv = cv.take<float>(NMAT * NR);
+    t.rinv = cv.take<float>(NMAT_DEFAULT * NR);
     t.msA = cv.take<float>(NG);
-    t.rmeta = cv.take<float>(2 * NMAT);
-    t.msc = cv.take<float>(2 * NMAT);
-    t.scratch = cv.take<double>(NMAT * NE);
-    t.rho_max = cv.take<unsigned int>(NMAT);
+    t.rmeta = cv.take<float>(2 * NMAT_DEFAULT);
+    t.msc = cv.take<float>(2 * NMAT_DEFAULT);
+    t.scratch = cv.take<double>(NMAT_DEFAULT * NE);
+    t.rho_max = cv.take<unsigned int>(NMAT_DEFAULT);
+    t.mats = cv.take<MatDef>(NMAT_DEFAULT);
+    MatDef defs[NMAT_DEFAULT];
+    material_defs(defs);
     unsigned long long* stats = cv.take<unsigned long long>(ST_COUNT);
     unsigned long long* counter = cv.take<unsigned long long>(1);
     int* err = cv.take<int>(1);
@@ -160,7 +164,7 @@ extern "C" ocmc_status ocmc_run_noalloc(int device, int nx, int ny, int nz, cons
     int cap = p.stack_capacity ? p.stack_capacity : NOALLOC_CAP;
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
-    size_t smem = transport_smem_bytes(threads);
+    size_t smem = transport_smem_bytes(NMAT_DEFAULT);
     const int nreg = p.max_registers ? p.max_registers : 80;
     int bps = p.blocks_per_sm ? p.blocks_per_sm : transport_max_blocks_per_sm(threads, smem, nreg);
     if (bps < 1) bps = 1;
@@ -179,7 +183,7 @@ extern "C" ocmc_status ocmc_run_noalloc(int device, int nx, int ny, int nz, cons
     if (e != cudaSuccess) return M.cuda(e, "clearing counters");
     PhysParams pp{p.e_abs_e, p.e_abs_g, p.w_cc, p.w_cb, p.d_maxs, p.f_maxe, p.s_min, p.flags, p.n_batches};
     long long nvox = (long long)nx * ny * nz;
-    e = build_tables(t, pp, density_dev, material_dev, nvox, err, s);
+    e = build_tables(t, pp, density_dev, material_dev, nvox, err, defs, s);
     if (e != cudaSuccess) return M.cuda(e, "table build");
 
     TransportArgs a;

@@ -21,7 +21,6 @@ namespace ocmc {
 
 namespace {
 
-__constant__ MatDef c_mats[NMAT];
 
 constexpr double RE = 2.8179403262e-13;
 constexpr double ALPHA = 1.0 / 137.035999084;
@@ -32,9 +31,8 @@ struct MC {
     double ne, photo, pairZ, S1, S2, I, dC, dX0, dX1, dA;
 };
 
-__device__ MC mconst(int m)
+__device__ MC mconst(const MatDef& d)
 {
-    const MatDef& d = c_mats[m];
     MC c;
     double ws = 0.0;
     for (int i = 0; i < d.n; ++i) ws += d.w[i];
@@ -154,9 +152,8 @@ __device__ double sig_brems(const MC& c, double T, double wcb)
     return 4.0 * ALPHA * RE * RE * (a + b);
 }
 
-__device__ double lambda1_inv(int m, double T)
+__device__ double lambda1_inv(const MatDef& d, double T)
 {
-    const MatDef& d = c_mats[m];
     double ws = 0.0;
     for (int i = 0; i < d.n; ++i) ws += d.w[i];
     double pc = sqrt(T * (T + 2.0 * MC2)), beta = pc / (T + MC2), q = MC2 / (pc * beta);
@@ -211,14 +208,14 @@ __device__ __forceinline__ double node_E(int i)
 __global__ void k_nodes(Tables t, PhysParams pp)
 {
     int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= NMAT * NE) return;
+    if (idx >= t.n_mat * NE) return;
     int m = idx / NE, i = idx % NE;
-    MC c = mconst(m);
+    MC c = mconst(t.mats[m]);
     double E = node_E(i);
     double mt = mu_channel(c, E, 0), mC = mu_channel(c, E, 1), mP = mu_channel(c, E, 2);
     t.ph[idx] = make_float4((float)log(mt), (float)(mC / mt), (float)(mP / mt), (float)mt);
     double sM = sig_moller(c, E, pp.w_cc), sB = sig_brems(c, E, pp.w_cb);
-    t.el[idx] = make_float4(0.f, (float)lambda1_inv(m, E), (float)sM, (float)sB);
+    t.el[idx] = make_float4(0.f, (float)lambda1_inv(t.mats[m], E), (float)sM, (float)sB);
     // step limit d_maxe (mass thickness) and the hard-event majorant on [E_i, E_i+1),
     // covering the energies a step starting there can reach (down to E (1 - f_maxe)).
     double dRf = inv_L_integral(c, E * (1.0 - pp.f_maxe), E, pp);
@@ -239,7 +236,7 @@ __global__ void k_nodes(Tables t, PhysParams pp)
 __global__ void k_range_scan(Tables t)
 {
     int m = threadIdx.x;
-    if (m >= NMAT) return;
+    if (m >= t.n_mat) return;
     double R = 0.0;
     for (int i = 0; i < NE; ++i) {
         R += t.scratch[m * NE + i];
@@ -254,9 +251,9 @@ __global__ void k_range_scan(Tables t)
 __global__ void k_range_inverse(Tables t, PhysParams pp)
 {
     int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= NMAT * NR) return;
+    if (idx >= t.n_mat * NR) return;
     int m = idx / NR, j = idx % NR;
-    MC c = mconst(m);
+    MC c = mconst(t.mats[m]);
     const double* R = t.scratch + m * NE;
     double lo = log(R[0]), hi = log(R[NE - 1]);
     double Rt = exp(lo + (hi - lo) * j / (NR - 1));
@@ -287,13 +284,13 @@ __global__ void k_ms_table(Tables t)
     t.msA[j] = (float)wentzel_solve(exp(lg));
 }
 
-__global__ void k_phantom_scan(const float* density, const uint8_t* material, long long nvox, unsigned int* rho_max,
-                               int* err)
+__global__ void k_phantom_scan(const float* density, const uint8_t* material, long long nvox, int n_mat,
+                               unsigned int* rho_max, int* err)
 {
     for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < nvox; v += (long long)gridDim.x * blockDim.x) {
         float r = density[v];
         int m = material[v];
-        if (m >= NMAT || !(r >= 0.f) || !(r <= 30.f)) {
+        if (m >= n_mat || !(r >= 0.f) || !(r <= 30.f)) {
             atomicOr(err, ERR_PHANTOM);
             continue;
         }
@@ -306,7 +303,7 @@ __global__ void k_photon_majorant(Tables t)
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= NE) return;
     float best = -1e30f;
-    for (int m = 0; m < NMAT; ++m) {
+    for (int m = 0; m < t.n_mat; ++m) {
         float r = __uint_as_float(t.rho_max[m]);
         if (r > 0.f) best = fmaxf(best, (float)log((double)r) + t.ph[m * NE + i].x);
     }
@@ -315,7 +312,7 @@ __global__ void k_photon_majorant(Tables t)
 
 }  // namespace
 
-void material_defs(MatDef out[NMAT])
+void material_defs(MatDef out[NMAT_DEFAULT])
 {
     // mass fractions: water H2O; cortical bone (ICRP); lung (ICRP)
     MatDef water = {2, {1, 8}, {1.008, 15.999}, {0.111894, 0.888106}, 75.0, 1.0};
@@ -333,19 +330,19 @@ void material_defs(MatDef out[NMAT])
     out[2] = lung;
 }
 
+// Tables for the t.n_mat staged materials defs[0 .. n_mat) (table row m = defs[m]).
 cudaError_t build_tables(const Tables& t, const PhysParams& pp, const float* density, const uint8_t* material,
-                         long long nvox, int* d_err, cudaStream_t s)
+                         long long nvox, int* d_err, const MatDef* defs, cudaStream_t s)
 {
-    MatDef defs[NMAT];
-    material_defs(defs);
-    cudaError_t e = cudaMemcpyToSymbolAsync(c_mats, defs, sizeof(defs), 0, cudaMemcpyHostToDevice, s);
+    if (t.n_mat < 1 || t.n_mat > MAX_STAGED) return cudaErrorInvalidValue;
+    cudaError_t e = cudaMemcpyAsync(t.mats, defs, sizeof(MatDef) * t.n_mat, cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return e;
-    k_nodes<<<(NMAT * NE + 127) / 128, 128, 0, s>>>(t, pp);
+    k_nodes<<<(t.n_mat * NE + 127) / 128, 128, 0, s>>>(t, pp);
     k_range_scan<<<1, 32, 0, s>>>(t);
-    k_range_inverse<<<(NMAT * NR + 127) / 128, 128, 0, s>>>(t, pp);
+    k_range_inverse<<<(t.n_mat * NR + 127) / 128, 128, 0, s>>>(t, pp);
     k_ms_table<<<(NG + 127) / 128, 128, 0, s>>>(t);
-    cudaMemsetAsync(t.rho_max, 0, NMAT * sizeof(unsigned int), s);
-    k_phantom_scan<<<1024, 256, 0, s>>>(density, material, nvox, t.rho_max, d_err);
+    cudaMemsetAsync(t.rho_max, 0, t.n_mat * sizeof(unsigned int), s);
+    k_phantom_scan<<<1024, 256, 0, s>>>(density, material, nvox, t.n_mat, t.rho_max, d_err);
     k_photon_majorant<<<(NE + 127) / 128, 128, 0, s>>>(t);
     return cudaGetLastError();
 }

@@ -228,7 +228,7 @@ __device__ __forceinline__ bool photon_step(C& c, Lane& p, unsigned& n_fict)
     long long vox = p.ix + (long long)a.nx * (p.iy + (long long)a.ny * p.iz);
     float rho = __ldg(a.density + vox);
     int m = __ldg(a.material + vox);
-    float4 pa = T.ph[m * NE + ei.i], pb = T.ph[m * NE + ei.i + 1];
+    float4 pa = T.ph[m * MS4 + ei.i], pb = T.ph[m * MS4 + ei.i + 1];
     float mu = rho * __expf(lerp1(pa.x, pb.x, ei.f));
     if (mu > mumax * 1.00001f) stat_add(c, ST_VIOL, 1);
     if (rng_u(p.r, k0, k1) * mumax >= mu) { n_fict++; return true; }
@@ -297,7 +297,7 @@ __device__ __forceinline__ void hard_event(C& c, Lane& p, int m, float sM, float
     } else {
         stat_add(c, ST_BREMS, 1);
         float Tk = p.E;
-        float k = sample_brems(Tk, c.a.pp.w_cb, T.msc[2 * m], T.msc[2 * m + 1], p.r, c.a.key0, c.a.key1, &c.ok);
+        float k = sample_brems(Tk, c.a.pp.w_cb, T.msc[m * MS1], T.msc[m * MS1 + 1], p.r, c.a.key0, c.a.key1, &c.ok);
         float th = MC2F / (Tk + MC2F);
         float xphi = rng_u(p.r, c.a.key0, c.a.key1);
         float gu = p.u, gv = p.v, gw = p.w;
@@ -342,9 +342,9 @@ __device__ __forceinline__ bool charged_step(C& c, Lane& p, unsigned& n_hfict)
     }
     rng_step_start(p.r, k0, k1);
     EIdx ei = e_index(p.E);
-    const int mb = m * NE;
+    const int mb = m * MS4, mb2 = m * MS2;
     float4 A = T.el[mb + ei.i], B = T.el[mb + ei.i + 1];
-    float2 C2 = T.el2[mb + ei.i], D2 = T.el2[mb + ei.i + 1];
+    float2 C2 = T.el2[mb2 + ei.i], D2 = T.el2[mb2 + ei.i + 1];
     float lnR = lerp1(A.x, B.x, ei.f);
     float s_maxe = lerp1(C2.x, D2.x, ei.f) / rho;
     float sighat = (a.pp.flags & 1) ? 0.f : C2.y;
@@ -552,7 +552,7 @@ __global__ void __maxnreg__(NREG) k_transport(const __grid_constant__ TransportA
 
 }  // namespace
 
-size_t transport_smem_bytes(int /*threads*/) { return SMEM_TABLE_BYTES; }
+size_t transport_smem_bytes(int n_mat) { return smem_table_bytes(n_mat); }
 
 namespace {
 template <bool BL, bool PS, int R>

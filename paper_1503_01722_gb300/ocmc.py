@@ -39,6 +39,11 @@ class Beamlet(C.Structure):
                 ("dir", C.c_float * 3), ("n_histories", C.c_uint64)]
 
 
+class Material(C.Structure):
+    _fields_ = [("n_elements", C.c_int32), ("Z", C.c_int32 * 16), ("A", C.c_double * 16),
+                ("mass_fraction", C.c_double * 16), ("I_eV", C.c_double), ("density", C.c_double)]
+
+
 class Stats(C.Structure):
     _fields_ = [(n, C.c_uint64) for n in (
         "histories", "photon_flights", "fictitious", "compton", "photo", "pair", "electron_steps", "moller",
@@ -81,6 +86,7 @@ def _load():
         "ocmc_get_beamlet_dose": (C.c_int, [P, C.c_int, P, P, P, C.c_int64, C.POINTER(C.c_int64)]),
         "ocmc_autotune": (C.c_int, [P, C.c_uint64, C.POINTER(Params)]),
         "ocmc_set_phase_space": (C.c_int, [P, P, C.c_uint64, C.c_int]),
+        "ocmc_set_materials": (C.c_int, [P, C.c_int, P]),
         "ocmc_load_phase_space": (C.c_int, [P, C.c_char_p]),
         "ocmc_unet_create": (C.c_int, [C.POINTER(P), C.c_int, C.c_int, C.c_int, C.c_int, C.c_uint64]),
         "ocmc_unet_destroy": (None, [P]),
@@ -185,6 +191,21 @@ class Engine:
                 setattr(params, k, v)
         self._check(lib.ocmc_set_params(self._c, C.byref(params)))
         self.params = params
+
+    def set_materials(self, defs):
+        """Define the materials: dicts with Z, A (g/mol), w (mass fractions), I (eV) and
+        density (g/cm^3); voxel material m is defs[m]. Drops the current phantom."""
+        arr = (Material * len(defs))()
+        for k, d in enumerate(defs):
+            n = len(d["Z"])
+            arr[k].n_elements = n
+            for i in range(n):
+                arr[k].Z[i] = int(d["Z"][i])
+                arr[k].A[i] = float(d["A"][i])
+                arr[k].mass_fraction[i] = float(d["w"][i])
+            arr[k].I_eV = float(d["I"])
+            arr[k].density = float(d["density"])
+        self._check(lib.ocmc_set_materials(self._c, len(defs), C.cast(arr, C.c_void_p)))
 
     def create_phantom(self, phantom=None, *, density=None, material=None, voxel=None):
         """phantom: object with .density (nz,ny,nx) float32, .material uint8, .voxel (dx,dy,dz)."""
