@@ -31,9 +31,9 @@ import ocmc_inputs as I  # noqa: E402
 # smsp__thread_inst_executed.sum divided by the kernel's own lane-step counter)
 # and DRAM bytes per history, from the ncu capture summarised in
 # profiles/k_transport_photon_slab_120.md (re-measured whenever the kernel changes).
-INST_PER_LANE_STEP = 649.3
+INST_PER_LANE_STEP = 646.3
 # DRAM bytes of one transport launch measured by ncu on the full default workload
-DRAM_BYTES_PER_LAUNCH = {("photon_slab_120", 100_000_000): 21.547e9}
+DRAM_BYTES_PER_LAUNCH = {("photon_slab_120", 100_000_000): 21.687e9}
 
 WORKLOADS = {
     "photon_slab_120": (I.photon_slab_120, 100_000_000,

@@ -50,11 +50,15 @@ struct CtxT {
 template <class C>
 __device__ __forceinline__ void stat_add(C& c, int k, unsigned long long v) { atomicAdd(c.st + k, v); }
 
-// fixed-point energy (round to nearest even); the 32-bit conversion is exact below 16 MeV
+// fixed-point energy (round to nearest even) with 32-bit conversions only: below 2^32 units
+// (16 MeV) directly; above, q is a float >= 2^32 and therefore a multiple of 2^9, so q / 2^8 is
+// an integer below 2^32 for any energy under 4 GeV and the result is exact (no 64-bit
+// float-to-integer conversion, which would occupy the FP64 pipe)
 __device__ __forceinline__ unsigned long long fx(float e)
 {
     float q = e * TALLY_SCALE;
-    return q < 4294967040.f ? (unsigned long long)__float2uint_rn(q) : (unsigned long long)__float2ll_rn(q);
+    return q < 4294967040.f ? (unsigned long long)__float2uint_rn(q)
+                            : (unsigned long long)__float2uint_rn(q * 0.00390625f) << 8;
 }
 
 // Batched-beamlet tally: add q to voxel v of beamlet b's open-addressing table
