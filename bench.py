@@ -267,25 +267,26 @@ def run_denoiser_bench(args, desc):
     eng.set_source(beam)
     eng.run(1_000_000, seed=1)
     dose = torch.empty(shape, dtype=torch.float32, device="cuda")
-    eng.dose(out=(dose, None))
+    dsig = torch.empty_like(dose)
+    eng.dose(out=(dose, dsig))
     dens = torch.from_numpy(np.ascontiguousarray(ph.density)).cuda()
     net = ocmc.UNet(shape, seed=1)
     if weights is not None:
         net.set_params(weights)
     out = torch.empty_like(dose)
     for _ in range(args.warmup):
-        net.forward(dose, dens, out)
+        net.forward(dose, dens, out, sigma=dsig)
     torch.cuda.synchronize()
     ms = []
     with ClockSampler(0) as clk:
         for k in range(args.steps):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record()
-            net.forward(dose, dens, out)
+            net.forward(dose, dens, out, sigma=dsig)
             e1.record()
             e1.synchronize()
             ms.append(e0.elapsed_time(e1))
-        lt = net.layer_times(dose, dens, repeats=max(args.steps, 3))
+        lt = net.layer_times(dose, dens, repeats=max(args.steps, 3), sigma=dsig)
     clocks = clk.summary()
     # end to end through the C ABI: the dose of the engine's tally denoised into pinned host memory
     out_h = torch.empty(shape, dtype=torch.float32).pin_memory()
@@ -389,7 +390,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-study", action="store_true", help="denoiser_128: inference timing only")
     ap.add_argument("--study-train", type=int, default=200, help="denoiser_128: training cases")
-    ap.add_argument("--study-steps", type=int, default=4000, help="denoiser_128: training steps")
+    ap.add_argument("--study-steps", type=int, default=8000, help="denoiser_128: training steps")
     args = ap.parse_args()
 
     make, n_default, desc = WORKLOADS[args.workload]

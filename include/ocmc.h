@@ -301,19 +301,23 @@ const char* ocmc_unet_last_error(ocmc_unet* net);
 ocmc_status ocmc_unet_num_params(ocmc_unet* net, int64_t* n);
 ocmc_status ocmc_unet_get_params(ocmc_unet* net, float* host, int grads);
 ocmc_status ocmc_unet_set_params(ocmc_unet* net, const float* host);
-/* Denoised dose (same units as dose_dev) from (dose_dev, density_dev), device arrays. */
-ocmc_status ocmc_unet_forward(ocmc_unet* net, const float* dose_dev, const float* density_dev, float* out_dev,
-                              void* cuda_stream);
+/* Denoised dose (same units as dose_dev) from (dose_dev, sigma_dev, density_dev), device
+ * arrays of nx*ny*nz floats: the Monte Carlo dose, its statistical uncertainty (batch standard
+ * error, same units; may be NULL, read as zero) and the density in g/cm^3. The network sees
+ * dose / s, density and sigma / s, s the maximum of dose_dev. */
+ocmc_status ocmc_unet_forward(ocmc_unet* net, const float* dose_dev, const float* sigma_dev, const float* density_dev,
+                              float* out_dev, void* cuda_stream);
 /* One Adam step (learning rate lr; lr <= 0: gradients only) on the mean squared error
  * between output and target_dev / s over voxels with density >= 0.1 g/cm^3, s the
  * maximum of dose_dev. *loss_host (may be NULL) receives the loss (synchronises). */
-ocmc_status ocmc_unet_train_step(ocmc_unet* net, const float* dose_dev, const float* density_dev,
-                                 const float* target_dev, float lr, float* loss_host, void* cuda_stream);
+ocmc_status ocmc_unet_train_step(ocmc_unet* net, const float* dose_dev, const float* sigma_dev,
+                                 const float* density_dev, const float* target_dev, float lr, float* loss_host,
+                                 void* cuda_stream);
 /* Timing: forward passes with a CUDA event pair around every layer (20 layers, in the order
  * encoder level 0..3, then decoder level 2..0); ms_out[i] (may be NULL to query *n_layers) is
  * the mean duration of layer i over `repeats` passes. Synchronises. */
-ocmc_status ocmc_unet_layer_times(ocmc_unet* net, const float* dose_dev, const float* density_dev, int repeats,
-                                  float* ms_out, int* n_layers);
+ocmc_status ocmc_unet_layer_times(ocmc_unet* net, const float* dose_dev, const float* sigma_dev,
+                                  const float* density_dev, int repeats, float* ms_out, int* n_layers);
 /* One layer through the network's own kernels (for the gradient tests): mode 0 3x3x3
  * convolution, 1 2x2x2 stride-2 convolution, 2 its transposed form; (nx,ny,nz) is the
  * fine grid; x, dy, y, dx channels-last FP32 host arrays (inputs rounded to BF16);
@@ -321,7 +325,8 @@ ocmc_status ocmc_unet_layer_times(ocmc_unet* net, const float* dose_dev, const f
 ocmc_status ocmc_unet_test_layer(int device, int mode, int nx, int ny, int nz, int cin, int cout,
                                  const float* x_host, const float* w_host, const float* dy_host, float* y_host,
                                  float* dx_host, float* dw_host);
-/* Denoise the context's current dose with the network; where the denoised value
+/* Denoise the context's current dose (and its batch sigma, the network's third input) with the
+ * network; where the denoised value
  * differs from the plain Monte Carlo value by more than k_sigma times the plain dose's
  * batch standard error (pooled over the voxel's 3x3x3 neighbourhood: root of the mean
  * variance) the plain value is kept and flag_out (may be NULL) is 1. dose_out and

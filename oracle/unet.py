@@ -6,8 +6,10 @@ gradient can be compared with it. Arrays are channels-last, (z, y, x, c), float6
 Weights are (taps, cin, cout) with tap t = dx + 3 dy + 9 dz for 3x3x3 kernels
 (offsets -1..1) and t = dx + 2 dy + 4 dz for 2x2x2 kernels; the flat parameter
 vector lists, layer by layer, W then b, and finally the 1x1x1 head (16 weights,
-1 bias). With bf16=True, weights, inputs and every stored activation are rounded
-to bfloat16 (round to nearest even), as the model's arithmetic specifies.
+1 bias). Input channels: the dose over its maximum s, the density, and (optional) the dose's
+statistical uncertainty over s; the other 13 channels are zero. With bf16=True, weights,
+inputs and every stored activation are rounded to bfloat16 (round to nearest even), as the
+model's arithmetic specifies.
 """
 from __future__ import annotations
 
@@ -146,16 +148,18 @@ class UNet:
         W = self.p[off:off + np.prod(shape)].reshape(shape)
         return self.q(W), self.p[boff:boff + cout]
 
-    def _inputs(self, dose, dens):
+    def _inputs(self, dose, dens, sigma=None):
         s = dose.max()
         x0 = dose / s if s > 0 else np.zeros_like(dose)
         x = np.zeros(dose.shape + (16,))
         x[..., 0] = x0
         x[..., 1] = dens
+        if sigma is not None:
+            x[..., 2] = np.asarray(sigma, np.float64) / s if s > 0 else 0.0
         return self.q(x), x0, s
 
-    def forward(self, dose, dens, keep=False):
-        x, x0, s = self._inputs(np.asarray(dose, np.float64), np.asarray(dens, np.float64))
+    def forward(self, dose, dens, keep=False, sigma=None):
+        x, x0, s = self._inputs(np.asarray(dose, np.float64), np.asarray(dens, np.float64), sigma)
         A = {"x": x}
         for i, (mode, cin, cout, a_in, a_out) in enumerate(architecture()):
             if a_in.startswith("cat"):
@@ -169,10 +173,10 @@ class UNet:
             return out, s, A
         return out * s
 
-    def loss_and_grads(self, dose, dens, target):
+    def loss_and_grads(self, dose, dens, target, sigma=None):
         """Masked mean squared error of (out - target/s) and its gradient w.r.t. every parameter."""
         dose = np.asarray(dose, np.float64)
-        out, s, A = self.forward(dose, dens, keep=True)
+        out, s, A = self.forward(dose, dens, keep=True, sigma=sigma)
         mask = np.asarray(dens) >= 0.1
         e = np.where(mask, out - np.asarray(target, np.float64) / s, 0.0)
         cnt = mask.sum()

@@ -37,17 +37,23 @@ __global__ void k_max_reduce(const float* x, long long n, unsigned int* out)
     if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(m));   // non-negative floats
 }
 
-// x0 = dose / s, x1 = density. Channels 2-15 of the input activation are zeroed when the
-// network is created and never written, so each voxel needs one 4-byte store.
-__global__ void k_pack_input(const float* dose, const float* dens, long long n, const unsigned int* smax,
-                             __nv_bfloat16* x, float* x0f)
+// x0 = dose / s, x1 = density, x2 = sigma / s (0 without sigma). Channels 3-15 of the input
+// activation are zeroed when the network is created and never written, so each voxel needs one
+// 8-byte store (channels 0-3).
+__global__ void k_pack_input(const float* dose, const float* dens, const float* sigma, long long n,
+                             const unsigned int* smax, __nv_bfloat16* x, float* x0f)
 {
     float s = __uint_as_float(*smax);
     float inv = s > 0.f ? 1.f / s : 0.f;
     for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < n; v += (long long)gridDim.x * blockDim.x) {
         float d = dose[v] * inv;
         x0f[v] = d;
-        *reinterpret_cast<__nv_bfloat162*>(x + v * 16) = __floats2bfloat162_rn(d, dens[v]);
+        float sg = sigma ? sigma[v] * inv : 0.f;
+        __nv_bfloat162 lo = __floats2bfloat162_rn(d, dens[v]), hi = __floats2bfloat162_rn(sg, 0.f);
+        uint2 w;
+        w.x = *reinterpret_cast<uint32_t*>(&lo);
+        w.y = *reinterpret_cast<uint32_t*>(&hi);
+        *reinterpret_cast<uint2*>(x + v * 16) = w;
     }
 }
 
@@ -470,12 +476,12 @@ cudaError_t refresh_bf16(ocmc_unet* u, cudaStream_t s)
     return cudaGetLastError();
 }
 
-ocmc_status forward(ocmc_unet* u, const float* dose, const float* dens, cudaStream_t s)
+ocmc_status forward(ocmc_unet* u, const float* dose, const float* sigma, const float* dens, cudaStream_t s)
 {
     long long n = u->nvox;
     UCK(cudaMemsetAsync(u->smax, 0, sizeof(unsigned int), s), "memset");
     k_max_reduce<<<grid_for(n), 256, 0, s>>>(dose, n, u->smax);
-    k_pack_input<<<grid_for(n), 256, 0, s>>>(dose, dens, n, u->smax, u->acts[0].x, u->x0f);
+    k_pack_input<<<grid_for(n), 256, 0, s>>>(dose, dens, sigma, n, u->smax, u->acts[0].x, u->x0f);
     UCK(cudaGetLastError(), "input");
     for (const Layer& L : u->layers) UCK(layer_fwd(u, L, s), "layer forward");
     const Act& last = u->acts[u->layers.back().out_act];
@@ -688,12 +694,13 @@ ocmc_status ocmc_unet_set_params(ocmc_unet* u, const float* host)
     return OCMC_OK;
 }
 
-ocmc_status ocmc_unet_forward(ocmc_unet* u, const float* dose, const float* dens, float* out, void* stream)
+ocmc_status ocmc_unet_forward(ocmc_unet* u, const float* dose, const float* sigma, const float* dens, float* out,
+                              void* stream)
 {
     if (!u || !dose || !dens || !out) return ufail(u, OCMC_ERR_ARG, "NULL argument");
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     UCK(cudaSetDevice(u->device), "device");
-    ocmc_status st = forward(u, dose, dens, s);
+    ocmc_status st = forward(u, dose, sigma, dens, s);
     if (st != OCMC_OK) return st;
     k_denorm<<<grid_for(u->nvox), 256, 0, s>>>(u->outf, u->smax, u->nvox, out);
     UCK(cudaGetLastError(), "output");
@@ -702,13 +709,14 @@ ocmc_status ocmc_unet_forward(ocmc_unet* u, const float* dose, const float* dens
 
 // One training step: forward, masked MSE loss, backward, Adam (lr; betas 0.9/0.999).
 // lr <= 0 computes the gradients without updating the weights.
-ocmc_status ocmc_unet_train_step(ocmc_unet* u, const float* dose, const float* dens, const float* target, float lr,
+ocmc_status ocmc_unet_train_step(ocmc_unet* u, const float* dose, const float* sigma, const float* dens,
+                                 const float* target, float lr,
                                  float* loss_host, void* stream)
 {
     if (!u || !dose || !dens || !target) return ufail(u, OCMC_ERR_ARG, "NULL argument");
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     UCK(cudaSetDevice(u->device), "device");
-    ocmc_status st = forward(u, dose, dens, s);
+    ocmc_status st = forward(u, dose, sigma, dens, s);
     if (st != OCMC_OK) return st;
     long long n = u->nvox;
     UCK(cudaMemsetAsync(u->lacc, 0, 2 * sizeof(double), s), "memset");
@@ -747,7 +755,8 @@ ocmc_status ocmc_unet_train_step(ocmc_unet* u, const float* dose, const float* d
 
 // Forward pass with a CUDA event pair around every layer: ms_out[i] = mean time of layer i over
 // `repeats` passes (stream order, so each layer's time is its own launches only).
-ocmc_status ocmc_unet_layer_times(ocmc_unet* u, const float* dose, const float* dens, int repeats, float* ms_out,
+ocmc_status ocmc_unet_layer_times(ocmc_unet* u, const float* dose, const float* sigma, const float* dens, int repeats,
+                                  float* ms_out,
                                   int* n_layers)
 {
     if (!u || !dose || !dens || repeats < 1) return ufail(u, OCMC_ERR_ARG, "bad argument");
@@ -763,7 +772,7 @@ ocmc_status ocmc_unet_layer_times(ocmc_unet* u, const float* dose, const float* 
         long long n = u->nvox;
         cudaMemsetAsync(u->smax, 0, sizeof(unsigned int), nullptr);
         k_max_reduce<<<grid_for(n), 256>>>(dose, n, u->smax);
-        k_pack_input<<<grid_for(n), 256>>>(dose, dens, n, u->smax, u->acts[0].x, u->x0f);
+        k_pack_input<<<grid_for(n), 256>>>(dose, dens, sigma, n, u->smax, u->acts[0].x, u->x0f);
         cudaEventRecord(ev[0], nullptr);
         for (int i = 0; i < L; ++i) {
             if (layer_fwd(u, u->layers[i], nullptr) != cudaSuccess) { st = ufail(u, OCMC_ERR_CUDA, "layer"); break; }
@@ -890,7 +899,7 @@ ocmc_status ocmc_denoise(ocmc_ctx* c, ocmc_unet* u, float k_sigma, float* dose_o
     }
     ocmc_status st = ocmc_get_dose(c, dd, ds, 1);
     if (st == OCMC_OK || st == OCMC_ERR_OVERFLOW || st == OCMC_ERR_TIMEOUT) {
-        ocmc_status s2 = ocmc_unet_forward(u, dd, c->d_density, dout, nullptr);
+        ocmc_status s2 = ocmc_unet_forward(u, dd, ds, c->d_density, dout, nullptr);
         if (s2 == OCMC_OK) {
             k_fallback<<<grid_for(n), 256>>>(dd, ds, dout, dflag, k_sigma, u->g[0].nx, u->g[0].ny, u->g[0].nz);
             e = cudaGetLastError();

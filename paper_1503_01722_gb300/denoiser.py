@@ -2,8 +2,8 @@
 comparison of plain and denoised Monte Carlo by the time each needs to reach a target error.
 
 Training pairs. For every random case (phantom + beam) the engine runs n_low histories (the
-network's input) and, with an independent seed, n_high histories (the target). Both dose maps
-and the density stay on the device.
+network's input: the dose and its batch standard error) and, with an independent seed, n_high
+histories (the target). The maps and the density stay on the device.
 
 Error. The error of a dose D against a reference R is the mean of |D - R| / max(R) over the
 voxels with R >= 0.1 max(R) (the 10% isodose), the agreement statistic of the paper's Sec. 3.1.
@@ -37,8 +37,15 @@ def _dose(engine, shape, device):
     return d
 
 
+def _dose_sigma(engine, shape, device):
+    d = torch.empty(shape, dtype=torch.float32, device=device)
+    s = torch.empty_like(d)
+    engine.dose(out=(d, s))
+    return d, s
+
+
 def make_pairs(cases, n_low, n_high, seed=1, device=0, engine=None, log=None):
-    """Engine-generated (input, density, target) triples on the device, one per case.
+    """Engine-generated (input, input sigma, density, target) on the device, one per case.
     Seeds: input 2 k + seed, target 2 k + seed + 1 for case k (independent histories)."""
     own = engine is None
     eng = ocmc.Engine(device) if own else engine
@@ -50,12 +57,12 @@ def make_pairs(cases, n_low, n_high, seed=1, device=0, engine=None, log=None):
             eng.set_source(beam)
             eng.reset()
             eng.run(n_low, seed=2 * k + seed)
-            low = _dose(eng, ph.density.shape, dev)
+            low, low_sigma = _dose_sigma(eng, ph.density.shape, dev)
             eng.reset()
             eng.run(n_high, seed=2 * k + seed + 1)
             high = _dose(eng, ph.density.shape, dev)
             dens = torch.from_numpy(np.ascontiguousarray(ph.density)).to(dev)
-            out.append((low, dens, high))
+            out.append((low, low_sigma, dens, high))
             if log:
                 log(f"pair {k + 1}/{len(cases)}")
     finally:
@@ -64,18 +71,24 @@ def make_pairs(cases, n_low, n_high, seed=1, device=0, engine=None, log=None):
     return out
 
 
-def train(net: ocmc.UNet, pairs, steps: int, lr: float = 1e-3, lr_final: float = 1e-4, seed: int = 0,
-          log_every: int = 0, log=print):
-    """Adam on one pair per step, pairs drawn in shuffled epochs; cosine learning-rate decay
-    from lr to lr_final. Returns the per-step losses."""
+def train(net: ocmc.UNet, pairs, steps: int, lr: float = 5e-4, lr_final: float = 2e-5, warmup: int = 300,
+          seed: int = 0, log_every: int = 0, log=print):
+    """Adam on one pair per step, pairs drawn in shuffled epochs; the learning rate rises
+    linearly over `warmup` steps to lr, then decays to lr_final along a cosine (a high rate
+    from the start can silence every ReLU of a layer, after which the network only returns its
+    input). Returns the per-step losses."""
     rng = np.random.default_rng(seed)
     order, losses = [], []
     for t in range(steps):
         if not order:
             order = list(rng.permutation(len(pairs)))
-        low, dens, high = pairs[order.pop()]
-        a = lr_final + 0.5 * (lr - lr_final) * (1 + math.cos(math.pi * t / max(steps - 1, 1)))
-        losses.append(net.train_step(low, dens, high, a))
+        low, low_sigma, dens, high = pairs[order.pop()]
+        if t < warmup:
+            a = lr * (t + 1) / warmup
+        else:
+            x = (t - warmup) / max(steps - warmup - 1, 1)
+            a = lr_final + 0.5 * (lr - lr_final) * (1 + math.cos(math.pi * x))
+        losses.append(net.train_step(low, dens, high, a, sigma=low_sigma))
         if log_every and (t + 1) % log_every == 0:
             log(f"step {t + 1}/{steps} loss {np.mean(losses[-log_every:]):.4e} lr {a:.2e}")
     return losses
@@ -169,9 +182,9 @@ def _cases(seeds, shape, voxel, workers=8):
 
 
 def run_study(n_train=200, n_eval=8, lows=(10**5, 10**6, 10**7), n_high=10**8,
-              n_ref=(2 * 10**9, 3 * 10**8), steps=4000, lr=1e-3, shape=(128, 128, 128),
+              n_ref=(2 * 10**9, 3 * 10**8), steps=8000, lr=5e-4, shape=(128, 128, 128),
               voxel=(0.25, 0.25, 0.25), target=0.01, k_sigma=4.0, device=0, seed=1, log=print,
-              weights_out=None):
+              weights_out=None, warmup=300):
     """Generate training pairs on random cases, train the network, then on held-out cases
     compare plain and denoised Monte Carlo by the wall time each needs to reach `target`
     against a reference of n_ref histories (photon, electron beams). Returns a report dict."""
@@ -199,13 +212,14 @@ def run_study(n_train=200, n_eval=8, lows=(10**5, 10**6, 10**7), n_high=10**8,
             for j, n in enumerate(lows):
                 eng.reset()
                 eng.run(n, seed=7 * k + seed + 1 + j)
-                pairs.append((_dose(eng, shape, dev), dens, high))
+                low, low_sigma = _dose_sigma(eng, shape, dev)
+                pairs.append((low, low_sigma, dens, high))
             if (k + 1) % 25 == 0:
                 log(f"pairs: case {k + 1}/{n_train} ({time.perf_counter() - t0:.0f} s)")
         torch.cuda.synchronize()
         rep["t_pairs_s"] = time.perf_counter() - t0
         t0 = time.perf_counter()
-        losses = train(net, pairs, steps, lr=lr, seed=seed, log_every=max(steps // 10, 1), log=log)
+        losses = train(net, pairs, steps, lr=lr, warmup=warmup, seed=seed, log_every=max(steps // 10, 1), log=log)
         torch.cuda.synchronize()
         rep["t_train_s"] = time.perf_counter() - t0
         rep["loss_first_100"] = float(np.mean(losses[:100]))
@@ -260,11 +274,11 @@ def main(argv=None):
                                              "plain and denoised Monte Carlo by time to a target error")
     ap.add_argument("--train", type=int, default=200)
     ap.add_argument("--eval", type=int, default=8)
-    ap.add_argument("--steps", type=int, default=4000)
+    ap.add_argument("--steps", type=int, default=8000)
     ap.add_argument("--n-high", type=float, default=1e8)
     ap.add_argument("--grid", type=int, default=128)
     ap.add_argument("--voxel", type=float, default=0.25)
-    ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--lr", type=float, default=5e-4)
     ap.add_argument("--weights-out", default=None)
     ap.add_argument("--report", default=None)
     a = ap.parse_args(argv)

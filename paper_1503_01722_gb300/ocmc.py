@@ -94,9 +94,9 @@ def _load():
         "ocmc_unet_num_params": (C.c_int, [P, C.POINTER(C.c_int64)]),
         "ocmc_unet_get_params": (C.c_int, [P, P, C.c_int]),
         "ocmc_unet_set_params": (C.c_int, [P, P]),
-        "ocmc_unet_forward": (C.c_int, [P, P, P, P, P]),
-        "ocmc_unet_train_step": (C.c_int, [P, P, P, P, C.c_float, C.POINTER(C.c_float), P]),
-        "ocmc_unet_layer_times": (C.c_int, [P, P, P, C.c_int, P, C.POINTER(C.c_int)]),
+        "ocmc_unet_forward": (C.c_int, [P, P, P, P, P, P]),
+        "ocmc_unet_train_step": (C.c_int, [P, P, P, P, P, C.c_float, C.POINTER(C.c_float), P]),
+        "ocmc_unet_layer_times": (C.c_int, [P, P, P, P, C.c_int, P, C.POINTER(C.c_int)]),
         "ocmc_unet_test_layer": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
                                            P, P, P, P, P, P]),
         "ocmc_denoise": (C.c_int, [P, P, C.c_float, P, P, C.c_int]),
@@ -440,23 +440,26 @@ class UNet:
         p = np.ascontiguousarray(p, np.float32)
         self._check(lib.ocmc_unet_set_params(self._u, C.c_void_p(p.ctypes.data)))
 
-    def forward(self, dose, density, out, stream=None):
-        self._check(lib.ocmc_unet_forward(self._u, _ptr(dose)[0], _ptr(density)[0], _ptr(out)[0],
+    def forward(self, dose, density, out, stream=None, sigma=None):
+        sg = _ptr(sigma)[0] if sigma is not None else None
+        self._check(lib.ocmc_unet_forward(self._u, _ptr(dose)[0], sg, _ptr(density)[0], _ptr(out)[0],
                                           _stream_ptr(stream)))
         return out
 
-    def layer_times(self, dose, density, repeats=10):
+    def layer_times(self, dose, density, repeats=10, sigma=None):
         """Mean forward time of each layer in ms (CUDA events around every layer)."""
         n = C.c_int()
-        self._check(lib.ocmc_unet_layer_times(self._u, _ptr(dose)[0], _ptr(density)[0], 1, None, C.byref(n)))
+        sg = _ptr(sigma)[0] if sigma is not None else None
+        self._check(lib.ocmc_unet_layer_times(self._u, _ptr(dose)[0], sg, _ptr(density)[0], 1, None, C.byref(n)))
         out = np.empty(n.value, np.float32)
-        self._check(lib.ocmc_unet_layer_times(self._u, _ptr(dose)[0], _ptr(density)[0], int(repeats),
+        self._check(lib.ocmc_unet_layer_times(self._u, _ptr(dose)[0], sg, _ptr(density)[0], int(repeats),
                                               C.c_void_p(out.ctypes.data), C.byref(n)))
         return out
 
-    def train_step(self, dose, density, target, lr, stream=None):
+    def train_step(self, dose, density, target, lr, stream=None, sigma=None):
         loss = C.c_float()
-        self._check(lib.ocmc_unet_train_step(self._u, _ptr(dose)[0], _ptr(density)[0], _ptr(target)[0],
+        sg = _ptr(sigma)[0] if sigma is not None else None
+        self._check(lib.ocmc_unet_train_step(self._u, _ptr(dose)[0], sg, _ptr(density)[0], _ptr(target)[0],
                                              float(lr), C.byref(loss), _stream_ptr(stream)))
         return loss.value
 

@@ -15,7 +15,7 @@ def test_denoiser_beats_plain_mc_at_equal_histories(tmp_path):
     build.build()
     from paper_1503_01722_gb300 import denoiser
     rep = denoiser.run_study(n_train=24, n_eval=4, lows=(10**5, 10**6), n_high=10**7,
-                             n_ref=(4 * 10**8, 6 * 10**7), steps=600, shape=(64, 64, 64),
+                             n_ref=(4 * 10**8, 6 * 10**7), steps=600, lr=1e-3, warmup=30, shape=(64, 64, 64),
                              voxel=(0.5, 0.5, 0.5), log=lambda m: None)
     print(json.dumps({k: v for k, v in rep.items() if k != "cases"}))
     assert rep["loss_last_100"] < rep["loss_first_100"]

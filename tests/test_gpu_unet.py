@@ -109,14 +109,17 @@ def test_network_output_and_gradients_match_oracle(ocmc):
     p[-17:-1] = np.random.default_rng(5).standard_normal(16) * 0.2     # a head that passes signal
     net.set_params(p)
     dose, dens, target = random_case(shape, 7)
-    td, tr, tt = (torch.from_numpy(a).cuda() for a in (dose, dens, target))
+    sigma = (0.05 * dose + 0.01 * dose.max()).astype(np.float32)
+    td, tr, tt, ts = (torch.from_numpy(a).cuda() for a in (dose, dens, target, sigma))
     out = torch.empty_like(td)
-    net.forward(td, tr, out)
+    net.forward(td, tr, out, sigma=ts)
     ref = U.UNet(p.astype(np.float32).astype(np.float64), bf16_storage=True)
+    assert rel_l2(out.cpu().numpy(), ref.forward(dose, dens, sigma=sigma)) < 1e-2
+    net.forward(td, tr, out)                              # without sigma: channel 2 is zero
     assert rel_l2(out.cpu().numpy(), ref.forward(dose, dens)) < 1e-2
-    loss = net.train_step(td, tr, tt, lr=0.0)
+    loss = net.train_step(td, tr, tt, lr=0.0, sigma=ts)
     G = net.params(grads=True)
-    lr_, Gr = ref.loss_and_grads(dose, dens, target)
+    lr_, Gr = ref.loss_and_grads(dose, dens, target, sigma=sigma)
     assert abs(loss - lr_) < 1e-2 * lr_
     # Deep-layer gradients are sums with heavy cancellation at random initialisation, so the
     # BF16 rounding of stored activations and gradients moves them by up to ~25% (fp64 oracle
@@ -126,7 +129,8 @@ def test_network_output_and_gradients_match_oracle(ocmc):
     # least 3%); measured, mma.sync kernels sit at 0.5-0.7 and tcgen05 kernels at 0.7-1.1 of
     # it. A wiring mistake (wrong skip, missing ReLU mask, swapped operand) gives errors of
     # order 1, and every kernel is checked on its own to BF16 rounding by the layer tests.
-    _, G64 = U.UNet(p.astype(np.float32).astype(np.float64), bf16_storage=False).loss_and_grads(dose, dens, target)
+    _, G64 = U.UNet(p.astype(np.float32).astype(np.float64), bf16_storage=False).loss_and_grads(
+        dose, dens, target, sigma=sigma)
     lay, hw, hb = U.param_layout()
     rows, bad = [], []
     for i, (off, shp, boff, cout) in enumerate(lay):
@@ -193,7 +197,8 @@ def test_denoise_fallback(ocmc):
         # huge k: the network output
         ocmc.denoise(e, net, 1e30, out, flag)
         ref = torch.empty_like(out)
-        net.forward(torch.from_numpy(D).cuda(), torch.from_numpy(ph.density).cuda(), ref)
+        net.forward(torch.from_numpy(D).cuda(), torch.from_numpy(ph.density).cuda(), ref,
+                    sigma=torch.from_numpy(S).cuda())
         assert flag.sum().item() == 0 and torch.equal(out, ref)
         # moderate k: the rule itself, |denoised - plain| > k * pooled sigma, with sigma pooled
         # as the root of the mean variance over the 3x3x3 neighbourhood (float32, same order)
