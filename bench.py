@@ -34,6 +34,9 @@ import ocmc_inputs as I  # noqa: E402
 INST_PER_LANE_STEP = 646.3
 # DRAM bytes of one transport launch measured by ncu on the full default workload
 DRAM_BYTES_PER_LAUNCH = {("photon_slab_120", 100_000_000): 21.687e9}
+# the same for the beamlet-mode kernel (hash tallies) on the 512-beamlet CT workload, measured by
+# ncu on the same workload with every beamlet's histories scaled by 0.02
+INST_PER_LANE_STEP_BEAMLETS = 693.9
 
 WORKLOADS = {
     "photon_slab_120": (I.photon_slab_120, 100_000_000,
@@ -186,11 +189,32 @@ def run_reference(args, ph, beam, desc):
     print(json.dumps(line))
 
 
+def cpu_baseline_beamlets(ph, spec, bl, target_s=12.0):
+    """The oracle on the host cores for a bounded sample of the beamlet workload: the first
+    histories of successive beamlets (each beamlet is its own beam), until ~target_s of work."""
+    import oracle as O
+    threads = os.cpu_count() or 1
+    done, t_total, k = 0, 0.0, 0
+    while t_total < target_s and k < len(bl):
+        b = bl[k]
+        beam = I.Beam(0, spec[0], spec[1], b["field"], b["ssd"], b["iso"], b["direction"])
+        n = min(b["n_histories"], 4000)
+        t = time.perf_counter()
+        O.run(ph, beam, n, seed=1, threads=threads)
+        t_total += time.perf_counter() - t
+        done += n
+        k += 1
+    return {"value": done / t_total, "unit": "histories/s", "cores": threads, "kind": "oracle",
+            "sample": f"the first min(n, 4000) histories of beamlets 0..{k - 1}: {done} histories, {t_total:.1f} s"}
+
+
 def run_beamlets_bench(args, make, desc):
     """Batched beamlets: one step = one replay of the captured launch over all beamlets."""
     import torch
     from paper_1503_01722_gb300 import ocmc
     ph, spec, bl = make()
+    if args.beamlet_scale != 1.0:
+        bl = [dict(b, n_histories=max(1, int(b["n_histories"] * args.beamlet_scale))) for b in bl]
     n_total = sum(b["n_histories"] for b in bl)
     eng = ocmc.Engine(0)
     eng.create_phantom(ph)
@@ -240,6 +264,18 @@ def run_beamlets_bench(args, make, desc):
         "clocks": clocks,
         "kernel_stats_last_step": {k: v for k, v in st.items() if isinstance(v, (int, float))},
     }
+    peaks = measured_peaks()
+    sm_mhz = clocks["sm_mhz"] or peaks.get("sm_max_mhz", 2070.0)
+    peak = sm_peak_thread_inst(sm_mhz) / 1e12
+    kern_ms = st["last_run_ms"]
+    achieved = (None if INST_PER_LANE_STEP_BEAMLETS is None else
+                st["lane_steps"] * INST_PER_LANE_STEP_BEAMLETS / (kern_ms / 1e3) / 1e12)
+    line["roofline"] = {"bound": "alu", "kernel": "k_transport (beamlet mode)", "achieved": achieved, "peak": peak,
+                        "unit": "Tinst/s", "frac": None if achieved is None else achieved / peak,
+                        "peak_basis": f"152 SMs x 128 lanes x median SM clock under load ({sm_mhz:.0f} MHz)",
+                        "traffic": None, "kernel_ms": kern_ms, "lane_steps_per_launch": st["lane_steps"]}
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline_beamlets(ph, spec, bl)
     print(json.dumps(line))
     eng.close()
 
@@ -389,6 +425,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-study", action="store_true", help="denoiser_128: inference timing only")
+    ap.add_argument("--beamlet-scale", type=float, default=1.0, help="beamlets_ct: scale every beamlet's histories")
     ap.add_argument("--study-train", type=int, default=200, help="denoiser_128: training cases")
     ap.add_argument("--study-steps", type=int, default=8000, help="denoiser_128: training steps")
     args = ap.parse_args()

@@ -226,7 +226,8 @@ ocmc_status ocmc_add_raw_tally(ocmc_ctx* ctx, const int64_t* in, int on_device,
 /* Zero the tally, the history count and the statistics. */
 ocmc_status ocmc_reset_tally(ocmc_ctx* ctx);
 
-/* Statistics of the runs since the last reset (synchronises). */
+/* Statistics of the runs since the last reset (synchronises); after ocmc_run_beamlets, of that
+ * beamlet run alone (a beamlet run replaces its tallies). */
 ocmc_status ocmc_get_stats(ocmc_ctx* ctx, ocmc_stats* out);
 
 /* Number of voxels and batches of the current phantom/parameters. */

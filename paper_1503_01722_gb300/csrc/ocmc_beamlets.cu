@@ -122,6 +122,8 @@ cudaError_t enqueue_beamlets(ocmc_ctx* c, const TransportArgs& a, size_t slots, 
     if (e == cudaSuccess) e = cudaMemsetAsync(c->d_bl_vals, 0, sizeof(unsigned long long) * slots, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->d_bl_over, 0, sizeof(unsigned int) * c->bl_n, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->d_counter, 0, sizeof(unsigned long long), s);
+    // a beamlet run replaces its tallies, so its statistics describe that run alone
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->d_stats, 0, sizeof(unsigned long long) * ST_COUNT, s);
     if (e == cudaSuccess) e = launch_transport(a, blocks, threads, transport_smem_bytes(c->t.n_mat), s, nreg);
     return e;
 }
