@@ -178,7 +178,7 @@ void launch_shape(const ocmc_ctx* c, int* threads, int* blocks, int* cap, int* n
     int bps = c->p.blocks_per_sm ? c->p.blocks_per_sm : transport_max_blocks_per_sm(*threads, smem, *nreg);
     if (bps < 1) bps = 1;
     *blocks = c->sms * bps;
-    *cap = c->p.stack_capacity ? c->p.stack_capacity : 1024;
+    *cap = c->p.stack_capacity ? c->p.stack_capacity : 8192;
 }
 
 }  // namespace
@@ -569,7 +569,7 @@ ocmc_status ocmc_run_range(ocmc_ctx* c, uint64_t first, uint64_t count, uint64_t
     a.key1 = (uint32_t)(seed >> 32);
     a.stacks = c->d_stacks;
     a.cap = cap;
-    a.switch_high = c->p.switch_high ? c->p.switch_high : 256;
+    a.switch_high = c->p.switch_high ? c->p.switch_high : cap - cap / 16;
     a.switch_low = c->p.switch_low ? c->p.switch_low : 8;
     a.refill_min = c->p.refill_min ? c->p.refill_min : 1;
     CK(cudaMemsetAsync(c->d_counter, 0, sizeof(unsigned long long), s), "counter reset");

@@ -108,7 +108,7 @@ ocmc_status beamlet_args(ocmc_ctx* c, unsigned long long total, uint64_t seed, T
     if (st != OCMC_OK) return st;
     a.stacks = c->d_stacks;
     a.cap = cap;
-    a.switch_high = c->p.switch_high ? c->p.switch_high : 256;
+    a.switch_high = c->p.switch_high ? c->p.switch_high : cap - cap / 16;
     a.switch_low = c->p.switch_low ? c->p.switch_low : 8;
     a.refill_min = c->p.refill_min ? c->p.refill_min : 1;
     return OCMC_OK;
@@ -369,7 +369,7 @@ ocmc_status ocmc_autotune(ocmc_ctx* c, uint64_t pilot, ocmc_params* chosen)
     if (pilot < 1) return ctx_fail(c, OCMC_ERR_ARG, "pilot_histories must be > 0");
     // (register cap, threads per block) pairs that fill an SM, x type-switch thresholds
     const int shape_c[][2] = {{64, 1024}, {64, 512}, {80, 256}, {56, 384}};
-    const int high_c[] = {128, 256, 512};
+    const int high_c[] = {2048, 4096, 7680};   // of the default 8192-record stacks
     const int low_c[] = {8, 16};
     ocmc_params base = c->p, best = c->p;
     float best_ms = 3.0e38f;

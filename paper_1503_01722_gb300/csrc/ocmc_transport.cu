@@ -434,6 +434,9 @@ __global__ void __maxnreg__(NREG) k_transport(const __grid_constant__ TransportA
     constexpr bool ps_src = PS && !BL;
     int mode = src_mode;
     bool src_done = a.count == 0;
+    // with switch_high >= cap, switching on stack size is off (stacks may then overflow, which
+    // is reported); otherwise a warp also switches when the other stack nears its capacity
+    const int emergency = a.switch_high < a.cap ? a.cap - 128 : 0x7FFFFFFF;
     bool active = false, just_switched = false;
     Lane p;
     unsigned n_fict = 0, n_hfict = 0;
@@ -511,6 +514,9 @@ __global__ void __maxnreg__(NREG) k_transport(const __grid_constant__ TransportA
             if (!m_avail && nact <= a.switch_low && (topo > nact || (!ps_src && other == src_mode && !src_done)))
                 sw = true;
             else if (topo >= a.switch_high && topo >= 2 * (nact + topm)) sw = true;
+            // the other stack is within one iteration's pushes (32 lanes x 3 secondaries, plus
+            // 32 refilled primaries) of its capacity: switch before it can overflow
+            else if (topo >= emergency && topo > topm) sw = true;
         }
         if (sw) {
             if (active) { push_lane(c, mode, p); active = false; }
