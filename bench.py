@@ -36,7 +36,7 @@ INST_PER_LANE_STEP = 660.9
 DRAM_BYTES_PER_LAUNCH = {("photon_slab_120", 100_000_000): 20.850e9}
 # the same for the beamlet-mode kernel (hash tallies) on the 512-beamlet CT workload, measured by
 # ncu on the same workload with every beamlet's histories scaled by 0.02
-INST_PER_LANE_STEP_BEAMLETS = 693.9
+INST_PER_LANE_STEP_BEAMLETS = 699.9
 
 WORKLOADS = {
     "photon_slab_120": (I.photon_slab_120, 100_000_000,
