@@ -209,6 +209,24 @@ def test_error_statuses(ocmc):
             e.dose()
 
 
+def test_emergency_switch_prevents_overflow(ocmc):
+    """Small stacks with a switch threshold just below their capacity: a warp switches type
+    when the other stack nears its capacity, so nothing overflows and the tally equals the
+    default launch's bit for bit."""
+    ph = I.homogeneous((20, 20, 20), (1.0, 1.0, 1.0))
+    beam = I.beam_on(ph, 0, I.mono(6.0), (10, 10), 100.0)
+    tallies = []
+    for kw in ({}, {"stack_capacity": 256, "switch_high": 250, "block_threads": 32, "blocks_per_sm": 1}):
+        with ocmc.Engine(0, **kw) as e:
+            e.create_phantom(ph)
+            e.set_source(beam)
+            e.run(200_000, seed=1)
+            e.dose()                                   # raises on an overflow
+            assert e.stats()["dropped"] == 0
+            tallies.append(e.raw_tally())
+    assert np.array_equal(tallies[0], tallies[1])
+
+
 def test_stack_overflow_is_reported_not_faulted(ocmc):
     """A tiny stack with type switching disabled overflows under a photon beam: the
     kernel drops the excess, flags OCMC_ERR_OVERFLOW and the context stays usable."""
