@@ -323,6 +323,16 @@ def run_denoiser_bench(args, desc):
             e1.synchronize()
             ms.append(e0.elapsed_time(e1))
         lt = net.layer_times(dose, dens, repeats=max(args.steps, 3), sigma=dsig)
+        # one training step (forward, loss, backward, Adam; learning rate 0 keeps the weights)
+        train_ms = []
+        for k in range(args.warmup + args.steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            net.train_step(dose, dens, dose, 0.0, sigma=dsig)
+            e1.record()
+            e1.synchronize()
+            if k >= args.warmup:
+                train_ms.append(e0.elapsed_time(e1))
     clocks = clk.summary()
     # end to end through the C ABI: the dose of the engine's tally denoised into pinned host memory
     out_h = torch.empty(shape, dtype=torch.float32).pin_memory()
@@ -345,7 +355,7 @@ def run_denoiser_bench(args, desc):
     peak = peaks.get("bf16_tflops")
     fwd_ms = statistics.mean(ms)
     flops = D.forward_flops(shape)
-    launches = 3 + sum(8 if k == "up" else 1 for k, _, _, _ in layers)
+    launches = 3 + len(layers)            # input packing, one launch per layer, head
     line = {
         "metric": "time to <=1% mean dose error (>10% isodose), denoised", "unit": "s",
         "value": study["median_time_denoised_s"] if study else None, "higher_is_better": False,
@@ -356,6 +366,7 @@ def run_denoiser_bench(args, desc):
         "config": {"workload": desc, "step": "one U-Net forward pass over 128^3 (inference)",
                    "l2": "activations 0.5 GB per pass, larger than L2", "forward_gflop": flops / 1e9},
         "forward_tflops": flops / (fwd_ms / 1e3) / 1e12,
+        "train_step_ms": statistics.mean(train_ms),
         "e2e": {"value": statistics.mean(e2e_ms) / 1e3, "unit": "s per denoised dose (ocmc_denoise to host)",
                 "h2d_bytes_per_step": 0, "d2h_bytes_per_step": int(np.prod(shape) * 4)},
         "gpu_launches": launches * args.steps,

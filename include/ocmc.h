@@ -323,8 +323,9 @@ ocmc_status ocmc_unet_layer_times(ocmc_unet* net, const float* dose_dev, const f
                                   const float* density_dev, int repeats, float* ms_out, int* n_layers);
 /* One layer through the network's own kernels (for the gradient tests): mode 0 3x3x3
  * convolution, 1 2x2x2 stride-2 convolution, 2 its transposed form; (nx,ny,nz) is the
- * fine grid; x, dy, y, dx channels-last FP32 host arrays (inputs rounded to BF16);
- * w [taps][cin][cout]; y = layer(x) without bias or ReLU; dx, dw the gradients for dy. */
+ * fine grid (even sides of 2 to 512); cin, cout multiples of 16 up to 256; x, dy, y, dx
+ * channels-last FP32 host arrays (inputs rounded to BF16); w [taps][cin][cout];
+ * y = layer(x) without bias or ReLU; dx, dw the gradients for dy. OCMC_ERR_ARG otherwise. */
 ocmc_status ocmc_unet_test_layer(int device, int mode, int nx, int ny, int nz, int cin, int cout,
                                  const float* x_host, const float* w_host, const float* dy_host, float* y_host,
                                  float* dx_host, float* dw_host);

@@ -15,6 +15,7 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -295,19 +296,46 @@ ocmc_status take_kernel_flag(ocmc_unet* u, cudaStream_t s)
     return ufail(u, OCMC_ERR_TIMEOUT, "a tensor-memory convolution timed out waiting for its data");
 }
 
+template <int BK, int BN>
+cudaError_t launch_conv_tile(const ConvArgs& a, dim3 grid, cudaStream_t s)
+{
+    constexpr int smem = conv_smem_bytes(BK, BN);
+    static std::once_flag once;
+    static cudaError_t attr = cudaSuccess;
+    std::call_once(once, [] {
+        attr = cudaFuncSetAttribute(k_conv<BK, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    });
+    if (attr != cudaSuccess) return attr;
+    k_conv<BK, BN><<<grid, THREADS, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+int sm_count()
+{
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms > 0 ? sms : 1;
+}
+
+// Column tile: the widest of 128 / 64 / 32 / 16 that still gives about two blocks per SM (small
+// grids at the coarse levels would otherwise leave most SMs idle).
 template <int BK>
 cudaError_t launch_conv_bk(const ConvArgs& a, cudaStream_t s)
 {
-    long long rows = a.mode == UP ? a.gin.n() : a.gout.n();
-    int bn = std::min(a.cout, 128);
-    dim3 grid((unsigned)((rows + BM - 1) / BM), (unsigned)(a.cout / bn));
+    const long long rows = a.mode == UP ? a.gin.n() : a.gout.n();
+    const int cols = a.mode == UP ? 8 * a.cout : a.cout;
+    const long long rb = (rows + BM - 1) / BM;
+    int bn = std::min(cols, 128);
+    const long long want = 2LL * sm_count();
+    while (bn > 16 && rb * (cols / bn) < want) bn /= 2;
+    dim3 grid((unsigned)rb, (unsigned)(cols / bn));
     switch (bn) {
-    case 16: k_conv<BK, 16><<<grid, THREADS, 0, s>>>(a); break;
-    case 32: k_conv<BK, 32><<<grid, THREADS, 0, s>>>(a); break;
-    case 64: k_conv<BK, 64><<<grid, THREADS, 0, s>>>(a); break;
-    default: k_conv<BK, 128><<<grid, THREADS, 0, s>>>(a); break;
+    case 16: return launch_conv_tile<BK, 16>(a, grid, s);
+    case 32: return launch_conv_tile<BK, 32>(a, grid, s);
+    case 64: return launch_conv_tile<BK, 64>(a, grid, s);
+    default: return launch_conv_tile<BK, 128>(a, grid, s);
     }
-    return cudaGetLastError();
 }
 
 cudaError_t launch_conv(const ConvArgs& a, cudaStream_t s)
@@ -385,18 +413,9 @@ cudaError_t layer_fwd(ocmc_unet* u, const Layer& L, cudaStream_t s)
     a.bias = u->params + L.boff;
     a.relu = 1;
     a.err = u->kerr;
-    if (L.mode != UP) {
-        a.w = L.wf;
-        a.wtc = u->tc ? L.wtc_f : nullptr;
-        return launch_conv(a, s);
-    }
-    for (int p = 0; p < 8; ++p) {
-        a.parity = p;
-        a.w = L.wf + (size_t)p * L.cin * L.cout;
-        cudaError_t e = launch_conv(a, s);
-        if (e != cudaSuccess) return e;
-    }
-    return cudaSuccess;
+    a.w = L.wf;
+    a.wtc = (u->tc && L.mode == CONV3) ? L.wtc_f : nullptr;
+    return launch_conv(a, s);
 }
 
 // backward of layer L: weight and bias gradients, then the data gradient into the
@@ -443,17 +462,12 @@ cudaError_t layer_bwd(ocmc_unet* u, const Layer& L, bool need_dx, cudaStream_t s
         a.err = u->kerr;
         return launch_conv(a, s);
     }
-    if (L.mode == DOWN) {           // fine <- coarse: UP over parities with W'[p][n][c]
+    if (L.mode == DOWN) {           // fine <- coarse: UP (all parities) with W'[p][n][c]
         a.mode = UP;
         a.gin = u->g[L.lout];
         a.gout = u->g[L.lin];
-        for (int p = 0; p < 8; ++p) {
-            a.parity = p;
-            a.w = L.wt + (size_t)p * L.cin * L.cout;
-            e = launch_conv(a, s);
-            if (e != cudaSuccess) return e;
-        }
-        return cudaSuccess;
+        a.w = L.wt;
+        return launch_conv(a, s);
     }
     a.mode = DOWN;                  // UP layer: coarse <- fine, DOWN gather with W'[p][n][c]
     a.gin = u->g[L.lout];
@@ -799,7 +813,8 @@ ocmc_status ocmc_unet_layer_times(ocmc_unet* u, const float* dose, const float* 
 ocmc_status ocmc_unet_test_layer(int device, int mode, int nx, int ny, int nz, int cin, int cout, const float* x,
                                  const float* w, const float* dy, float* y, float* dx, float* dw)
 {
-    if (mode < 0 || mode > 2 || cin % 16 || cout % 16 || cin > 256 || cout > 256 || nx % 2 || ny % 2 || nz % 2)
+    if (mode < 0 || mode > 2 || cin % 16 || cout % 16 || cin > 256 || cout > 256 || nx % 2 || ny % 2 || nz % 2 ||
+        nx < 2 || ny < 2 || nz < 2 || nx > 512 || ny > 512 || nz > 512)
         return OCMC_ERR_ARG;
     if (cudaSetDevice(device) != cudaSuccess) return OCMC_ERR_CUDA;
     Grid3 fine{nx, ny, nz}, coarse{nx / 2, ny / 2, nz / 2};
@@ -837,8 +852,8 @@ ocmc_status ocmc_unet_test_layer(int device, int mode, int nx, int ny, int nz, i
         a.mode = m; a.gin = gi; a.gout = go; a.in = Slice{dX, cin, 0}; a.out = Slice{dY, cout, 0};
         a.cin = cin; a.cout = cout;
         a.wtc = pf; a.err = kerr;
-        if (m != UP && e == cudaSuccess) { a.w = wf; e = launch_conv(a, nullptr); }
-        else for (int p = 0; p < 8 && e == cudaSuccess; ++p) { a.parity = p; a.w = wf + (size_t)p * cin * cout; e = launch_conv(a, nullptr); }
+        a.w = wf;
+        if (e == cudaSuccess) e = launch_conv(a, nullptr);
     }
     if (e == cudaSuccess) {
         ConvArgs a;
@@ -847,10 +862,8 @@ ocmc_status ocmc_unet_test_layer(int device, int mode, int nx, int ny, int nz, i
         a.gin = go; a.gout = gi;
         a.wtc = pt; a.err = kerr;
         if (m == CONV3) { a.mode = CONV3; a.w = wt; e = launch_conv(a, nullptr); }
-        else if (m == DOWN) {
-            a.mode = UP;
-            for (int p = 0; p < 8 && e == cudaSuccess; ++p) { a.parity = p; a.w = wt + (size_t)p * cin * cout; e = launch_conv(a, nullptr); }
-        } else { a.mode = DOWN; a.w = wt; e = launch_conv(a, nullptr); }
+        else if (m == DOWN) { a.mode = UP; a.w = wt; e = launch_conv(a, nullptr); }
+        else { a.mode = DOWN; a.w = wt; e = launch_conv(a, nullptr); }
     }
     if (e == cudaSuccess) {
         if (m == UP) {

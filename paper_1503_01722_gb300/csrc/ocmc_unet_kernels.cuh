@@ -10,8 +10,9 @@
 // layer kinds: each output row (voxel) gathers its input voxels per tap:
 //   CONV3 : 3x3x3, stride 1, zero padding 1      (27 taps, src = v + d - 1)
 //   DOWN  : 2x2x2, stride 2 (fine -> coarse)      (8 taps,  src = 2v + d)
-//   UP    : 2x2x2 transposed, stride 2 (coarse -> fine), one launch per output parity:
-//           row = coarse voxel u, out voxel = 2u + p, single tap p.
+//   UP    : 2x2x2 transposed, stride 2 (coarse -> fine), all eight output parities in one
+//           launch: row = coarse voxel u, column j = p * cout + n (N = 8 cout, K = cin),
+//           out voxel 2u + p, channel n.
 // Data gradients use the same kernel with transposed (and, for CONV3, flipped)
 // weights: dgrad(CONV3) = CONV3, dgrad(DOWN) = UP, dgrad(UP) = DOWN.
 // The weight gradient is a second kernel: dW[tap][c][n] = sum over rows of
@@ -49,7 +50,6 @@ struct ConvArgs {
     int accumulate;              // out = out + result
     const __nv_bfloat16* mask;   // multiply by (mask(v, c) > 0), mask is a Slice-like buffer
     int mask_stride, mask_c0;
-    int parity;                  // UP mode: output parity 0..7
     const __nv_bfloat16* wtc;    // CONV3: weights packed for the tensor-memory kernel, or null
     int* err;                    // device error flag for the tensor-memory kernel (may be null)
 };
@@ -68,6 +68,8 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem, bool va
 
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
 
 __device__ __forceinline__ void ldsm_x4(uint32_t& r0, uint32_t& r1, uint32_t& r2, uint32_t& r3, const void* p)
 {
@@ -103,59 +105,50 @@ __device__ __forceinline__ void mma_bf16(float* d, uint32_t a0, uint32_t a1, uin
 
 __device__ __forceinline__ int num_taps(Mode m) { return m == CONV3 ? 27 : (m == DOWN ? 8 : 1); }
 
-// Input voxel of output row r for tap t (-1: zero padding). For UP the row is the
-// coarse voxel itself.
-__device__ __forceinline__ long long src_voxel(const ConvArgs& a, long long r, int t)
+// Input voxel for tap t of the output row at (x, y, z) (-1: zero padding). For UP the row is
+// the coarse voxel (x, y, z) itself and there is one tap.
+__device__ __forceinline__ long long src_of(const ConvArgs& a, int x, int y, int z, int t)
 {
-    if (a.mode == UP) return r;
-    const Grid3& go = a.gout;
-    int x = (int)(r % go.nx);
-    long long q = r / go.nx;
-    int y = (int)(q % go.ny);
-    int z = (int)(q / go.ny);
     int sx, sy, sz;
     if (a.mode == CONV3) {
         sx = x + (t % 3) - 1;
         sy = y + (t / 3) % 3 - 1;
         sz = z + t / 9 - 1;
-    } else {
+    } else if (a.mode == DOWN) {
         sx = 2 * x + (t & 1);
         sy = 2 * y + ((t >> 1) & 1);
         sz = 2 * z + (t >> 2);
+    } else {
+        sx = x;
+        sy = y;
+        sz = z;
     }
     const Grid3& gi = a.gin;
     if (sx < 0 || sy < 0 || sz < 0 || sx >= gi.nx || sy >= gi.ny || sz >= gi.nz) return -1;
     return sx + (long long)gi.nx * (sy + (long long)gi.ny * sz);
 }
 
-// Output voxel of row r.
-__device__ __forceinline__ long long dst_voxel(const ConvArgs& a, long long r)
-{
-    if (a.mode != UP) return r;
-    const Grid3& gi = a.gin;   // coarse
-    int x = (int)(r % gi.nx);
-    long long q = r / gi.nx;
-    int y = (int)(q % gi.ny);
-    int z = (int)(q / gi.ny);
-    int p = a.parity;
-    int ox = 2 * x + (p & 1), oy = 2 * y + ((p >> 1) & 1), oz = 2 * z + (p >> 2);
-    const Grid3& go = a.gout;
-    if (ox >= go.nx || oy >= go.ny || oz >= go.nz) return -1;
-    return ox + (long long)go.nx * (oy + (long long)go.ny * oz);
-}
-
 constexpr int BM = 128;        // rows per block
 constexpr int THREADS = 256;   // 8 warps, 16 rows each
+constexpr int NSTAGE = 4;      // cp.async pipeline depth (K chunks in flight)
 
-// Implicit-GEMM convolution. BK: input channels per K chunk (16 or 32); BN: output
-// channels per block (16, 32, 64 or 128; gridDim.y covers cout / BN).
+// Shared memory of k_conv<BK, BN>: NSTAGE stages of an A tile (BM x BK) and a B tile (BK x BN),
+// rows padded by 16 bytes against bank conflicts.
+__host__ __device__ constexpr int conv_smem_bytes(int bk, int bn)
+{
+    return NSTAGE * (BM * (bk + 8) + bk * (bn + 8)) * 2;
+}
+
+// Implicit-GEMM convolution. BK: input channels per K chunk (16 or 32); BN: output columns per
+// block (16, 32, 64 or 128; gridDim.y covers the columns: cout, or 8 cout for UP).
 template <int BK, int BN>
 __global__ void __launch_bounds__(THREADS) k_conv(const ConvArgs a)
 {
-    constexpr int AST = BK + 8;        // smem row strides (bf16), +16 B against bank conflicts
+    constexpr int AST = BK + 8;        // smem row strides (bf16)
     constexpr int BST = BN + 8;
-    __shared__ __align__(16) __nv_bfloat16 sA[2][BM * AST];
-    __shared__ __align__(16) __nv_bfloat16 sB[2][BK * BST];
+    extern __shared__ __align__(16) unsigned char conv_smem[];
+    __nv_bfloat16* sA = reinterpret_cast<__nv_bfloat16*>(conv_smem);                  // [NSTAGE][BM * AST]
+    __nv_bfloat16* sB = sA + NSTAGE * BM * AST;                                        // [NSTAGE][BK * BST]
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const long long rows = a.mode == UP ? a.gin.n() : a.gout.n();
     const long long r0 = (long long)blockIdx.x * BM;
@@ -164,44 +157,78 @@ __global__ void __launch_bounds__(THREADS) k_conv(const ConvArgs a)
     const int KC = a.cin / BK;                    // chunks per tap
     const int steps = T * KC;
 
+    // A rows this thread copies (the same rows for every K chunk): their grid coordinates are
+    // worked out once, so the per-chunk gathers need no divisions
+    constexpr int CH_A = BK / 8;                 // 16-byte chunks per A row
+    constexpr int RPT = BM * CH_A / THREADS;     // rows per thread
+    const int ach = tid % CH_A;
+    int rx[RPT], ry[RPT], rz[RPT];
+#pragma unroll
+    for (int k = 0; k < RPT; ++k) {
+        const long long row = r0 + tid / CH_A + k * (THREADS / CH_A);
+        const Grid3& gr = a.mode == UP ? a.gin : a.gout;
+        if (row < rows) {
+            rx[k] = (int)(row % gr.nx);
+            const long long q = row / gr.nx;
+            ry[k] = (int)(q % gr.ny);
+            rz[k] = (int)(q / gr.ny);
+        } else {
+            rx[k] = -1 << 20;                    // far outside: every tap reads zeros
+            ry[k] = rz[k] = 0;
+        }
+    }
+
     auto load = [&](int step, int buf) {
-        const int t = a.mode == UP ? a.parity : step / KC;
-        const int wt = a.mode == UP ? 0 : t;     // UP passes the parity's weights as a 1-tap tensor
+        const int t = step / KC;
         const int c0 = (step % KC) * BK;
-        constexpr int CH_A = BK / 8;             // 16-byte chunks per A row
-        for (int i = tid; i < BM * CH_A; i += THREADS) {
-            int r = i / CH_A, ch = i % CH_A;
-            long long row = r0 + r;
-            long long s = row < rows ? src_voxel(a, row, t) : -1;
-            const __nv_bfloat16* g = a.in.ptr + (s >= 0 ? s : 0) * a.in.stride + a.in.c0 + c0 + ch * 8;
-            cp_async16(&sA[buf][r * AST + ch * 8], g, s >= 0);
+        __nv_bfloat16* dA = sA + buf * BM * AST;
+        __nv_bfloat16* dB = sB + buf * BK * BST;
+#pragma unroll
+        for (int k = 0; k < RPT; ++k) {
+            const int r = tid / CH_A + k * (THREADS / CH_A);
+            const long long s = src_of(a, rx[k], ry[k], rz[k], t);
+            const __nv_bfloat16* g = a.in.ptr + (s >= 0 ? s : 0) * a.in.stride + a.in.c0 + c0 + ach * 8;
+            cp_async16(&dA[r * AST + ach * 8], g, s >= 0);
         }
         constexpr int CH_B = BN / 8;
         for (int i = tid; i < BK * CH_B; i += THREADS) {
             int k = i / CH_B, ch = i % CH_B;
-            const __nv_bfloat16* g = a.w + ((long long)wt * a.cin + c0 + k) * a.cout + n0 + ch * 8;
-            cp_async16(&sB[buf][k * BST + ch * 8], g, true);
+            const int col = n0 + ch * 8;
+            // UP: column p * cout + n reads parity p's weights [p][cin][cout] (cout is a multiple
+            // of 8, so a 16-byte chunk never straddles two parities)
+            const int wt = a.mode == UP ? col / a.cout : t;
+            const int n = a.mode == UP ? col % a.cout : col;
+            const __nv_bfloat16* g = a.w + ((long long)wt * a.cin + c0 + k) * a.cout + n;
+            cp_async16(&dB[k * BST + ch * 8], g, true);
         }
-        cp_async_commit();
     };
 
     float acc[BN / 8][4];
 #pragma unroll
     for (int j = 0; j < BN / 8; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
 
-    load(0, 0);
+    // NSTAGE - 1 chunks in flight ahead of the one being multiplied; one commit group per
+    // chunk (empty past the end), so wait_group<NSTAGE - 2> means "chunk s has landed"
+#pragma unroll
+    for (int st = 0; st < NSTAGE - 1; ++st) {
+        if (st < steps) load(st, st);
+        cp_async_commit();
+    }
     for (int s = 0; s < steps; ++s) {
-        const int buf = s & 1;
-        cp_async_wait_all();
-        __syncthreads();
-        if (s + 1 < steps) load(s + 1, buf ^ 1);
+        const int buf = s % NSTAGE;
+        cp_async_wait<NSTAGE - 2>();
+        __syncthreads();   // chunk s visible to all; buffer (s - 1) % NSTAGE free again
+        if (s + NSTAGE - 1 < steps) load(s + NSTAGE - 1, (s + NSTAGE - 1) % NSTAGE);
+        cp_async_commit();
+        const __nv_bfloat16* cA = sA + buf * BM * AST;
+        const __nv_bfloat16* cB = sB + buf * BK * BST;
 #pragma unroll
         for (int kk = 0; kk < BK; kk += 16) {
             uint32_t a0, a1, a2, a3;
             {
                 int row = warp * 16 + (lane & 7) + 8 * ((lane >> 3) & 1);
                 int col = kk + 8 * (lane >> 4);
-                ldsm_x4(a0, a1, a2, a3, &sA[buf][row * AST + col]);
+                ldsm_x4(a0, a1, a2, a3, &cA[row * AST + col]);
             }
 #pragma unroll
             for (int j = 0; j < BN / 8; j += 2) {
@@ -209,29 +236,43 @@ __global__ void __launch_bounds__(THREADS) k_conv(const ConvArgs a)
                     uint32_t b0, b1, b2, b3;
                     int k = kk + (lane & 7) + 8 * ((lane >> 3) & 1);
                     int n = j * 8 + 8 * (lane >> 4);
-                    ldsm_x4_t(b0, b1, b2, b3, &sB[buf][k * BST + n]);
+                    ldsm_x4_t(b0, b1, b2, b3, &cB[k * BST + n]);
                     mma_bf16(acc[j], a0, a1, a2, a3, b0, b1);
                     mma_bf16(acc[j + 1], a0, a1, a2, a3, b2, b3);
                 } else {
                     uint32_t b0, b1;
                     int k = kk + (lane & 7) + 8 * ((lane >> 3) & 1);
-                    ldsm_x2_t(b0, b1, &sB[buf][k * BST + j * 8]);
+                    ldsm_x2_t(b0, b1, &cB[k * BST + j * 8]);
                     mma_bf16(acc[j], a0, a1, a2, a3, b0, b1);
                 }
             }
         }
     }
+    cp_async_wait<0>();
     // epilogue: rows g and g+8 of the warp's 16, columns 2t, 2t+1 of each n-tile
     const int g = lane >> 2, t4 = lane & 3;
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
         long long row = r0 + warp * 16 + g + 8 * h;
         if (row >= rows) continue;
-        long long v = dst_voxel(a, row);
-        if (v < 0) continue;
+        int ux = 0, uy = 0, uz = 0;              // UP: the row's coarse voxel
+        if (a.mode == UP) {
+            ux = (int)(row % a.gin.nx);
+            const long long q = row / a.gin.nx;
+            uy = (int)(q % a.gin.ny);
+            uz = (int)(q / a.gin.ny);
+        }
 #pragma unroll
         for (int j = 0; j < BN / 8; ++j) {
-            int n = n0 + j * 8 + 2 * t4;
+            const int col = n0 + j * 8 + 2 * t4;
+            const int p = a.mode == UP ? col / a.cout : 0;
+            const int n = a.mode == UP ? col % a.cout : col;
+            long long v = row;
+            if (a.mode == UP) {
+                const int ox = 2 * ux + (p & 1), oy = 2 * uy + ((p >> 1) & 1), oz = 2 * uz + (p >> 2);
+                if (ox >= a.gout.nx || oy >= a.gout.ny || oz >= a.gout.nz) continue;
+                v = ox + (long long)a.gout.nx * (oy + (long long)a.gout.ny * oz);
+            }
             float x0 = acc[j][2 * h], x1 = acc[j][2 * h + 1];
             if (a.bias) { x0 += a.bias[n]; x1 += a.bias[n + 1]; }
             __nv_bfloat162* o = reinterpret_cast<__nv_bfloat162*>(a.out.ptr + v * a.out.stride + a.out.c0 + n);
@@ -264,13 +305,14 @@ struct WgradArgs {
 
 // Row r's input voxel for the weight gradient: for UP the rows are output (fine)
 // voxels whose single source is their coarse parent, and the tap is their parity.
+// Grids hold fewer than 2^31 voxels (at most 512^3), so 32-bit division suffices.
 __device__ __forceinline__ long long wsrc(const WgradArgs& a, long long r, int t)
 {
     const Grid3& go = a.gout;
-    int x = (int)(r % go.nx);
-    long long q = r / go.nx;
-    int y = (int)(q % go.ny);
-    int z = (int)(q / go.ny);
+    const unsigned ur = (unsigned)r, unx = (unsigned)go.nx, q = ur / unx;
+    int x = (int)(ur - q * unx);
+    int y = (int)(q % (unsigned)go.ny);
+    int z = (int)(q / (unsigned)go.ny);
     int sx, sy, sz;
     if (a.mode == CONV3) {
         sx = x + (t % 3) - 1; sy = y + (t / 3) % 3 - 1; sz = z + t / 9 - 1;

@@ -10,10 +10,14 @@
 // tap (dx, dy, dz) for slice s is a no-swizzle K-major matrix starting at halo voxel
 // (dx, dy, s + dz): 8 rows 16 bytes apart (x), next 8-row group 160 bytes on (y), second
 // 8 channels one plane on (K). No data is copied per tap.
-// The layer's weights stay in shared memory for the whole kernel, packed [tap][channel group]
-// [out channel][8 channels] so that B (N = out channels, K = 16 input channels) is K-major too.
-// Each (tap, slice) is one MMA of M = 128, N = cout, K = 16, accumulating in FP32 in tensor
-// memory; two accumulator sets let the epilogue of one tile overlap the MMAs of the next.
+// Output channels are split into slices of NSL (NSL = cout for up to 32 input channels; 32 or
+// 16 for the 64- and 128-channel layers, whose whole weights would not fit): blockIdx.y is the
+// slice, and the slice's weights stay in shared memory for the whole kernel, packed [tap]
+// [channel group][out channel][8 channels] so that B (N = NSL out channels, K = 16 input
+// channels) is K-major too. Each (tap, z-slice) is one MMA of M = 128, N = NSL, K = 16,
+// accumulating in FP32 in tensor memory; two accumulator sets let the epilogue of one tile
+// overlap the MMAs of the next. Blocks of different channel slices read the same halo tiles,
+// which L2 serves.
 //
 // Warp roles (192 threads): warp 0 issues the TMA copies, warp 1 owns tensor memory and one of
 // its lanes issues the MMAs, warps 2-5 read the accumulators (each warp its 32-lane quarter of
@@ -52,21 +56,21 @@ struct TcArgs {
     int* err;
 };
 
-template <int CIN, int COUT, int TZ, int NS_>
+template <int CIN, int NSL, int TZ, int NS_>
 struct Cfg {
     static constexpr int NS = NS_;                                       // halo stages
     static constexpr int G = CIN / 8;
     static constexpr int CHUNKS = CIN / 16;
-    static constexpr uint32_t W_BYTES = 27u * CIN * COUT * 2;
+    static constexpr uint32_t W_BYTES = 27u * CIN * NSL * 2;             // one channel slice
     static constexpr uint32_t PLANE = (uint32_t)(TZ + 2) * HY * HX * 16;
     static constexpr uint32_t STAGE = 2 * PLANE;
     static constexpr uint32_t BAR_OFF = W_BYTES + NS * STAGE;
     static constexpr uint32_t BIAS_OFF = BAR_OFF + 256;
-    static constexpr uint32_t SMEM = BIAS_OFF + COUT * 4;
-    static constexpr uint32_t COLS = 2 * TZ * COUT;
+    static constexpr uint32_t SMEM = BIAS_OFF + NSL * 4;
+    static constexpr uint32_t COLS = 2 * TZ * NSL;
     static constexpr uint32_t NCOLS = COLS <= 32 ? 32 : COLS <= 64 ? 64 : COLS <= 128 ? 128 : COLS <= 256 ? 256 : 512;
     static_assert(COLS <= 512, "tensor memory holds 512 columns");
-    static_assert(CIN % 16 == 0 && COUT % 16 == 0 && COUT <= 256, "MMA shape");
+    static_assert(CIN % 16 == 0 && NSL % 16 == 0 && NSL <= 256, "MMA shape");
     static_assert(W_BYTES % 128 == 0 && PLANE % 128 == 0, "TMA destinations 128-byte aligned");
     static_assert(SMEM <= 232448, "shared memory per block");
 };
@@ -77,10 +81,10 @@ __device__ __forceinline__ bool wait_bounded(uint64_t* bar, uint32_t parity)
     return mbar_wait(bar, parity, &dummy, WAIT_NS);
 }
 
-template <int CIN, int COUT, int TZ, int NS_>
+template <int CIN, int NSL, int TZ, int NS_>
 __global__ void __launch_bounds__(TC_THREADS, 1) k_conv3_tc(const __grid_constant__ CUtensorMap tmap, const TcArgs a)
 {
-    using C = Cfg<CIN, COUT, TZ, NS_>;
+    using C = Cfg<CIN, NSL, TZ, NS_>;
     constexpr int NS = C::NS;
     extern __shared__ __align__(1024) uint8_t smem[];
     uint8_t* sw = smem;
@@ -96,7 +100,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv3_tc(const __grid_constan
     volatile int* abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
     float* sbias = reinterpret_cast<float*>(smem + C::BIAS_OFF);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int i = threadIdx.x; i < COUT; i += TC_THREADS) sbias[i] = a.bias ? a.bias[i] : 0.f;
+    const int n0 = blockIdx.y * NSL;                  // this block's output channels n0 .. n0 + NSL - 1
+    for (int i = threadIdx.x; i < NSL; i += TC_THREADS) sbias[i] = a.bias ? a.bias[n0 + i] : 0.f;
 
     if (threadIdx.x == 0) {
         mbar_init(w_full, 1);
@@ -122,9 +127,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv3_tc(const __grid_constan
         // ---- producer: weights once, then one halo chunk per (tile, chunk) ----
         if (lane == 0) {
             mbar_expect_tx(w_full, C::W_BYTES);
+            const uint8_t* wsrc = reinterpret_cast<const uint8_t*>(a.wpack) + (size_t)blockIdx.y * C::W_BYTES;
             for (uint32_t off = 0; off < C::W_BYTES; off += 32768u)
-                bulk_load(sw + off, reinterpret_cast<const uint8_t*>(a.wpack) + off, min(32768u, C::W_BYTES - off),
-                          w_full);
+                bulk_load(sw + off, wsrc + off, min(32768u, C::W_BYTES - off), w_full);
             int it = 0;
             int last[NS];
 #pragma unroll
@@ -154,14 +159,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv3_tc(const __grid_constan
             bool issued = false;
             if (mbar_wait(w_full, 0, abort, WAIT_NS)) {
                 fence_after_sync();
-                constexpr uint32_t idesc = idesc_bf16_f32(128, COUT);
+                constexpr uint32_t idesc = idesc_bf16_f32(128, NSL);
                 const uint32_t sw_addr = saddr(sw), sh_addr = saddr(sh);
                 int it = 0, lt = 0;
                 for (int tile = blockIdx.x; tile < a.ntiles && !*abort; tile += gridDim.x, ++lt) {
                     const int acc = lt & 1, ua = lt >> 1;
                     if (!mbar_wait(&t_empty[acc], (ua & 1) ^ 1, abort, WAIT_NS)) break;
                     fence_after_sync();
-                    const uint32_t d0 = tmem + (uint32_t)(acc * TZ * COUT);
+                    const uint32_t d0 = tmem + (uint32_t)(acc * TZ * NSL);
                     for (int c = 0; c < C::CHUNKS; ++c, ++it) {
                         const int st = it % NS, u = it / NS;
                         if (!mbar_wait(&h_full[st], u & 1, abort, WAIT_NS)) break;
@@ -169,14 +174,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv3_tc(const __grid_constan
                         // descriptors are built once per chunk; a tap or slice only moves the start
                         // address, which is the descriptor's low field in 16-byte units
                         const uint64_t a0 = sdesc(sh_addr + (uint32_t)st * C::STAGE, C::PLANE, HX * 16);
-                        const uint64_t b0 = sdesc(sw_addr + (uint32_t)(2 * c) * COUT * 16, COUT * 16, 128);
+                        const uint64_t b0 = sdesc(sw_addr + (uint32_t)(2 * c) * NSL * 16, NSL * 16, 128);
 #pragma unroll
                         for (int t = 0; t < 27; ++t) {
                             const int dx = t % 3, dy = (t / 3) % 3, dz = t / 9;
-                            const uint64_t bd = b0 + (uint64_t)(t * C::G * COUT);
+                            const uint64_t bd = b0 + (uint64_t)(t * C::G * NSL);
 #pragma unroll
                             for (int s = 0; s < TZ; ++s)
-                                mma_f16(d0 + (uint32_t)(s * COUT), a0 + (uint64_t)(((s + dz) * HY + dy) * HX + dx), bd,
+                                mma_f16(d0 + (uint32_t)(s * NSL), a0 + (uint64_t)(((s + dz) * HY + dy) * HX + dx), bd,
                                         idesc, (t != 0 || c != 0) ? 1u : 0u);
                         }
                         mma_commit(&h_empty[st]);
@@ -203,19 +208,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv3_tc(const __grid_constan
             fence_after_sync();
             const int tx = tile % a.tiles_x, r = tile / a.tiles_x;
             const int x = tx * TX + (row & 7), y = (r % a.tiles_y) * TY + (row >> 3), z0 = (r / a.tiles_y) * TZ;
-            const uint32_t tbase = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(acc * TZ * COUT);
+            const uint32_t tbase = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(acc * TZ * NSL);
 #pragma unroll 1
             for (int s = 0; s < TZ; ++s) {
-                float v[COUT];
+                float v[NSL];
 #pragma unroll
-                for (int j = 0; j < COUT / 16; ++j) tmem_ld16(tbase + (uint32_t)(s * COUT + 16 * j), v + 16 * j);
+                for (int j = 0; j < NSL / 16; ++j) tmem_ld16(tbase + (uint32_t)(s * NSL + 16 * j), v + 16 * j);
                 const int z = z0 + s;
                 if (x < a.g.nx && y < a.g.ny && z < a.g.nz) {
                     const long long vox = x + (long long)a.g.nx * (y + (long long)a.g.ny * z);
-                    __nv_bfloat16* o = a.out.ptr + vox * a.out.stride + a.out.c0;
-                    const __nv_bfloat16* mk = a.mask ? a.mask + vox * a.mask_stride + a.mask_c0 : nullptr;
+                    __nv_bfloat16* o = a.out.ptr + vox * a.out.stride + a.out.c0 + n0;
+                    const __nv_bfloat16* mk = a.mask ? a.mask + vox * a.mask_stride + a.mask_c0 + n0 : nullptr;
 #pragma unroll
-                    for (int j = 0; j < COUT / 8; ++j) {
+                    for (int j = 0; j < NSL / 8; ++j) {
                         float f[8];
 #pragma unroll
                         for (int e = 0; e < 8; ++e) f[e] = v[8 * j + e] + sbias[8 * j + e];
@@ -265,18 +270,20 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv3_tc(const __grid_constan
     if (threadIdx.x == 0 && *abort && a.err) atomicExch(a.err, 1);
 }
 
-// [taps][K][N] -> [taps][K/8][N][8]
-__global__ void k_pack_tc(const __nv_bfloat16* src, int taps, int K, int N, __nv_bfloat16* dst)
+// [taps][K][N] -> [N / NSL][taps][K/8][NSL][8]: one contiguous block per output-channel slice
+__global__ void k_pack_tc(const __nv_bfloat16* src, int taps, int K, int N, int nsl, __nv_bfloat16* dst)
 {
     long long total = (long long)taps * K * N;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
         int kk = (int)(i & 7);
         long long q = i >> 3;
-        int n = (int)(q % N);
-        q /= N;
+        int nn = (int)(q % nsl);
+        q /= nsl;
         int g = (int)(q % (K / 8));
-        int t = (int)(q / (K / 8));
-        dst[i] = src[((long long)t * K + 8 * g + kk) * N + n];
+        q /= K / 8;
+        int t = (int)(q % taps);
+        int sl = (int)(q / taps);
+        dst[i] = src[((long long)t * K + 8 * g + kk) * N + sl * nsl + nn];
     }
 }
 
@@ -294,14 +301,14 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
     return fn;
 }
 
-template <int CIN, int COUT, int TZ, int NS>
+template <int CIN, int NSL, int TZ, int NS>
 cudaError_t launch_cfg(const ConvArgs& a, const __nv_bfloat16* wpack, int* err, cudaStream_t s)
 {
-    using C = Cfg<CIN, COUT, TZ, NS>;
+    using C = Cfg<CIN, NSL, TZ, NS>;
     static std::once_flag once;
     static cudaError_t attr = cudaSuccess;
     std::call_once(once, [] {
-        attr = cudaFuncSetAttribute(k_conv3_tc<CIN, COUT, TZ, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+        attr = cudaFuncSetAttribute(k_conv3_tc<CIN, NSL, TZ, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
     });
     if (attr != cudaSuccess) return attr;
     auto enc = encode_fn();
@@ -335,9 +342,25 @@ cudaError_t launch_cfg(const ConvArgs& a, const __nv_bfloat16* wpack, int* err, 
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int blocks = std::max(1, std::min(t.ntiles, sms));
-    k_conv3_tc<CIN, COUT, TZ, NS><<<blocks, TC_THREADS, C::SMEM, s>>>(m, t);
+    const int slices = a.cout / NSL;
+    const dim3 blocks((unsigned)std::max(1, std::min(t.ntiles, sms / slices)), (unsigned)slices);
+    k_conv3_tc<CIN, NSL, TZ, NS><<<blocks, TC_THREADS, C::SMEM, s>>>(m, t);
     return cudaGetLastError();
+}
+
+// Output channels per block: the whole layer where its weights fit next to the halo stages,
+// else slices of 32 (64 input channels) or 16 (128 input channels).
+int slice_width(int cin, int cout)
+{
+    if (cin <= 32) return cout;
+    if (cin == 64) return cout <= 32 ? cout : 32;
+    return 16;
+}
+
+// Tiles of 8 x 16 x tz voxels over the grid, times the channel slices.
+long long tc_blocks(Grid3 g, int tz, int slices)
+{
+    return (long long)((g.nx + TX - 1) / TX) * ((g.ny + TY - 1) / TY) * ((g.nz + tz - 1) / tz) * slices;
 }
 
 }  // namespace
@@ -345,28 +368,37 @@ cudaError_t launch_cfg(const ConvArgs& a, const __nv_bfloat16* wpack, int* err, 
 bool conv3_tc_supported(int cin, int cout)
 {
     return (cin == 16 && (cout == 16 || cout == 32)) || (cin == 32 && (cout == 16 || cout == 32 || cout == 64)) ||
-           (cin == 64 && cout == 32);
+           (cin == 64 && (cout == 32 || cout == 64 || cout == 128)) || (cin == 128 && (cout == 64 || cout == 128));
 }
 
 cudaError_t pack_conv3_tc(const __nv_bfloat16* w, int cin, int cout, __nv_bfloat16* wpack, cudaStream_t s)
 {
     long long n = 27LL * cin * cout;
-    k_pack_tc<<<(unsigned)std::min<long long>((n + 255) / 256, 4096), 256, 0, s>>>(w, 27, cin, cout, wpack);
+    k_pack_tc<<<(unsigned)std::min<long long>((n + 255) / 256, 4096), 256, 0, s>>>(w, 27, cin, cout,
+                                                                                  slice_width(cin, cout), wpack);
     return cudaGetLastError();
 }
 
 cudaError_t launch_conv3_tc(const ConvArgs& a, const __nv_bfloat16* wpack, int* err, cudaStream_t s)
 {
     if (a.mode != CONV3 || a.in.c0 % 8 || a.in.stride % 8 || a.out.c0 % 8 || a.out.stride % 8 ||
-        (a.mask && (a.mask_c0 % 8 || a.mask_stride % 8)))
+        (a.mask && (a.mask_c0 % 8 || a.mask_stride % 8)) || !conv3_tc_supported(a.cin, a.cout))
         return cudaErrorInvalidValue;
     if (a.cin == 16 && a.cout == 16) return launch_cfg<16, 16, 8, 3>(a, wpack, err, s);
     if (a.cin == 16 && a.cout == 32) return launch_cfg<16, 32, 8, 3>(a, wpack, err, s);
     if (a.cin == 32 && a.cout == 16) return launch_cfg<32, 16, 8, 3>(a, wpack, err, s);
     if (a.cin == 32 && a.cout == 32) return launch_cfg<32, 32, 8, 3>(a, wpack, err, s);
-    if (a.cin == 64 && a.cout == 32) return launch_cfg<64, 32, 8, 2>(a, wpack, err, s);
     if (a.cin == 32 && a.cout == 64) return launch_cfg<32, 64, 4, 3>(a, wpack, err, s);
-    return cudaErrorInvalidValue;
+    if (a.cin == 64 && a.cout == 32) return launch_cfg<64, 32, 8, 2>(a, wpack, err, s);
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int slices = a.cout / slice_width(a.cin, a.cout);
+    // thin z-tiles where 4-deep ones would leave half the SMs idle (the 16^3 level); otherwise
+    // 4-deep tiles, which re-read less halo for the same number of rounds
+    const bool thin = 2 * tc_blocks(a.gin, 4, slices) < sms;
+    if (a.cin == 64) return thin ? launch_cfg<64, 32, 2, 4>(a, wpack, err, s) : launch_cfg<64, 32, 4, 3>(a, wpack, err, s);
+    return thin ? launch_cfg<128, 16, 2, 4>(a, wpack, err, s) : launch_cfg<128, 16, 4, 3>(a, wpack, err, s);
 }
 
 }  // namespace unet

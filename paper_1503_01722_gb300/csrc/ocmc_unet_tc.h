@@ -8,10 +8,12 @@
 namespace ocmc {
 namespace unet {
 
-// Channel counts the tensor-memory kernel covers (its layer weights fit in shared memory).
+// Channel counts the tensor-memory kernel covers (16 to 128; each block holds the weights of a
+// slice of the output channels in shared memory).
 bool conv3_tc_supported(int cin, int cout);
 
-// Repack BF16 weights [27][cin][cout] into the kernel's layout [27][cin/8][cout][8].
+// Repack BF16 weights [27][cin][cout] into the kernel's layout [cout/nsl][27][cin/8][nsl][8],
+// nsl the kernel's output-channel slice for (cin, cout).
 cudaError_t pack_conv3_tc(const __nv_bfloat16* w, int cin, int cout, __nv_bfloat16* wpack, cudaStream_t s);
 
 // CONV3 convolution (forward, or data gradient with flipped transposed weights) with the same

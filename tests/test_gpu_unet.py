@@ -21,7 +21,8 @@ def rel_l2(a, b):
     return float(np.linalg.norm(np.ravel(a) - np.ravel(b)) / max(np.linalg.norm(np.ravel(b)), 1e-30))
 
 
-CASES = [(0, 16, 16), (0, 32, 16), (0, 16, 32), (0, 32, 32), (0, 64, 32), (0, 32, 64), (0, 64, 128), (0, 128, 64),
+CASES = [(0, 16, 16), (0, 32, 16), (0, 16, 32), (0, 32, 32), (0, 64, 32), (0, 32, 64), (0, 64, 64), (0, 64, 128),
+         (0, 128, 64), (0, 128, 128),
          (1, 16, 32), (1, 32, 64), (1, 64, 128), (2, 128, 64), (2, 64, 32), (2, 32, 16)]
 
 
@@ -50,12 +51,13 @@ def test_layer_matches_oracle(ocmc, mode, cin, cout):
     assert np.allclose(dw, dwr, rtol=1e-4, atol=1e-4 * np.abs(dwr).max())
 
 
-@pytest.mark.parametrize("cin,cout", [(16, 16), (32, 64), (64, 32)])
+@pytest.mark.parametrize("cin,cout", [(16, 16), (32, 64), (64, 32), (64, 64), (128, 64), (128, 128)])
 def test_conv3_large_grid(ocmc, cin, cout):
-    """A grid of 480+ output tiles, so every block of the persistent tensor-memory kernel runs
-    several tiles (both accumulator sets, every halo stage reused)."""
+    """A grid of 190+ output tiles per channel slice, so every block of the persistent
+    tensor-memory kernel runs several tiles (both accumulator sets, every halo stage reused);
+    for 64 and 128 input channels the blocks also split the output channels into slices."""
     rng = np.random.default_rng(cin * 7 + cout)
-    fine = (48, 80, 128)
+    fine = (48, 80, 128) if cin < 64 else (32, 48, 64)
     x = U.bf16(rng.standard_normal(fine + (cin,)))
     W = U.bf16(rng.standard_normal((27, cin, cout)) / np.sqrt(27 * cin))
     dy = U.bf16(rng.standard_normal(fine + (cout,)))
