@@ -136,14 +136,32 @@ __global__ void k_head_bwd(const __nv_bfloat16* h, const float* w, const float* 
     }
 }
 
-// sum of `parts` rows of length m, fixed order
-__global__ void k_sum_rows(const float* part, int parts, int m, float* out)
+// Sum of `parts` rows of length m in a fixed order: thread (x, y) of a 32 x 32 block adds rows
+// [y L, (y + 1) L) of column j in order (loads unrolled, so many are in flight), then the 32
+// partial sums of the column are added in order of y.
+__global__ void __launch_bounds__(1024) k_sum_rows(const float* part, int parts, int m, float* out)
 {
-    int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= m) return;
+    __shared__ float sh[32][33];
+    const int j = blockIdx.x * 32 + threadIdx.x;
+    const int L = (parts + 31) / 32;
+    const int i0 = threadIdx.y * L, i1 = min(parts, i0 + L);
     float s = 0.f;
-    for (int i = 0; i < parts; ++i) s += part[(long long)i * m + j];
-    out[j] = s;
+    if (j < m) {
+#pragma unroll 8
+        for (int i = i0; i < i1; ++i) s += part[(long long)i * m + j];
+    }
+    sh[threadIdx.y][threadIdx.x] = s;
+    __syncthreads();
+    if (threadIdx.y == 0 && j < m) {
+        float t = 0.f;
+        for (int y = 0; y < 32; ++y) t += sh[y][threadIdx.x];
+        out[j] = t;
+    }
+}
+
+void sum_rows(const float* part, int parts, long long m, float* out, cudaStream_t s)
+{
+    k_sum_rows<<<(unsigned)((m + 31) / 32), dim3(32, 32), 0, s>>>(part, parts, (int)m, out);
 }
 
 // bias gradient partials: per block sums of dy[v][n] over its voxels, in a fixed order (thread
@@ -356,6 +374,40 @@ __global__ void k_transpose_pnc(const float* src, int taps, int n, int c, float*
     }
 }
 
+// Weight gradient of a 3x3x3 convolution over grid g (input and output) into dW [27][cin][cout].
+cudaError_t launch_wgrad3(Grid3 g, Slice x, Slice dy, int cin, int cout, float* part, size_t part_cap, float* dW,
+                          cudaStream_t s)
+{
+    Wgrad3Args a;
+    a.g = g;
+    a.in = x;
+    a.dy = dy;
+    a.cin = cin;
+    a.cout = cout;
+    a.seg_x = (g.nx + WSEG - 1) / WSEG;
+    a.nseg = (long long)a.seg_x * g.ny * g.nz;
+    const int bc = std::min(cin, 32), bn = std::min(cout, 32);
+    const int tiles = (cin / bc) * (cout / bn);
+    const long long m = 27LL * cin * cout;
+    // one wave of four blocks per SM (the kernel's registers allow four) over (chunks, 3
+    // z-offsets, channel tiles)
+    long long chunks = std::max<long long>(1, std::min<long long>(a.nseg, (4LL * sm_count() + 3 * tiles - 1) / (3 * tiles)));
+    while (chunks > 1 && (size_t)(chunks * m) > part_cap) chunks /= 2;
+    if ((size_t)(chunks * m) > part_cap) return cudaErrorMemoryAllocation;
+    a.seg_per_chunk = (a.nseg + chunks - 1) / chunks;
+    chunks = (a.nseg + a.seg_per_chunk - 1) / a.seg_per_chunk;
+    a.partial = part;
+    dim3 grid((unsigned)chunks, 3, (unsigned)tiles);
+    if (bc == 16 && bn == 16) k_wgrad3<16, 16><<<grid, THREADS, 0, s>>>(a);
+    else if (bc == 16) k_wgrad3<16, 32><<<grid, THREADS, 0, s>>>(a);
+    else if (bn == 16) k_wgrad3<32, 16><<<grid, THREADS, 0, s>>>(a);
+    else k_wgrad3<32, 32><<<grid, THREADS, 0, s>>>(a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    sum_rows(part, (int)chunks, m, dW, s);
+    return cudaGetLastError();
+}
+
 // Weight gradient of one layer into dW (FP32, [taps][cin][cout]).
 cudaError_t launch_wgrad(Mode mode, Grid3 gin, Grid3 gout, Slice x, Slice dy, int cin, int cout, float* part,
                          size_t part_cap, float* dW, cudaStream_t s)
@@ -370,7 +422,8 @@ cudaError_t launch_wgrad(Mode mode, Grid3 gin, Grid3 gout, Slice x, Slice dy, in
     a.dy = dy;
     a.cin = cin;
     a.cout = cout;
-    const int taps = mode == CONV3 ? 27 : 8;
+    if (mode == CONV3) return launch_wgrad3(gout, x, dy, cin, cout, part, part_cap, dW, s);
+    const int taps = 8;
     long long rows = gout.n();
     int bc = std::min(cin, 64), bn = std::min(cout, 64);
     int tiles = (cin / bc) * (cout / bn);
@@ -388,7 +441,7 @@ cudaError_t launch_wgrad(Mode mode, Grid3 gin, Grid3 gout, Slice x, Slice dy, in
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     long long m = (long long)taps * cin * cout;
-    k_sum_rows<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(part, (int)chunks, (int)m, dW);
+    sum_rows(part, (int)chunks, m, dW, s);
     return cudaGetLastError();
 }
 
@@ -440,7 +493,7 @@ cudaError_t layer_bwd(ocmc_unet* u, const Layer& L, bool need_dx, cudaStream_t s
     long long nout = u->g[L.lout].n();
     int blocks = grid_for(nout * L.cout);
     k_bias_part<<<blocks, 256, 0, s>>>(dy.ptr, dy.stride, dy.c0, L.cout, nout, u->bpart);
-    k_sum_rows<<<1, 128, 0, s>>>(u->bpart, blocks, L.cout, u->grads + L.boff);
+    sum_rows(u->bpart, blocks, L.cout, u->grads + L.boff, s);
     e = cudaGetLastError();
     if (e != cudaSuccess || !need_dx) return e;
     ConvArgs a;
@@ -741,7 +794,7 @@ ocmc_status ocmc_unet_train_step(ocmc_unet* u, const float* dose, const float* s
     const Act& last = u->acts[lastL.out_act];
     int hb = grid_for(n);
     k_head_bwd<<<hb, 256, 0, s>>>(last.x, u->params + u->head_w, u->gout, n, last.g, u->bpart);
-    k_sum_rows<<<1, 32, 0, s>>>(u->bpart, hb, 17, u->grads + u->head_w);
+    sum_rows(u->bpart, hb, 17, u->grads + u->head_w, s);
     UCK(cudaGetLastError(), "head backward");
     // layers in reverse; UP weight gradients come out as [p][n][c] and are transposed
     for (int i = (int)u->layers.size() - 1; i >= 0; --i) {

@@ -417,5 +417,140 @@ __global__ void __launch_bounds__(THREADS) k_wgrad(const WgradArgs a)
     }
 }
 
+// Weight gradient of a 3x3x3 convolution, all nine taps of one z-offset per block:
+// dW[t][c][n] = sum over output voxels v of x[v + d_t][c] dy[v][n] (zero outside the grid).
+// The K dimension runs over segments of WSEG = 32 voxels along x. For a segment at (x0, y, z)
+// the block stages dy[x0 .. x0+31, y, z] and, for dy' = -1, 0, 1, the input run
+// x[x0-1 .. x0+32, y+dy', z+dz] (zero-filled where it leaves the grid); tap (dx, dy') then
+// reads its A operand from that run shifted by dx rows, so one staged segment feeds nine taps
+// (the per-tap kernel above re-reads both operands for every tap). blockIdx = (segment chunk,
+// z-offset, channel tile); a block walks its contiguous segments with running coordinates.
+// Partials [chunk][27][cin][cout] are summed in a fixed order.
+constexpr int WSEG = 32;
+
+struct Wgrad3Args {
+    Grid3 g;
+    Slice in, dy;
+    int cin, cout;
+    int seg_x;                   // segments per x line
+    long long nseg, seg_per_chunk;
+    float* partial;
+};
+
+template <int BC, int BN>
+__global__ void __launch_bounds__(THREADS, 4) k_wgrad3(const Wgrad3Args a)
+{
+    constexpr int RUN = WSEG + 2, NST = 4;
+    constexpr int XST = BC + 8, YST = BN + 8;
+    constexpr int XS = 3 * RUN * XST, YS = WSEG * YST;
+    constexpr int CX = BC / 8, CY = BN / 8;
+    __shared__ __align__(16) __nv_bfloat16 sX[NST][XS];
+    __shared__ __align__(16) __nv_bfloat16 sY[NST][YS];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int dz = blockIdx.y;
+    const int tiles_n = a.cout / BN;
+    const int c0 = (blockIdx.z / tiles_n) * BC, n0 = (blockIdx.z % tiles_n) * BN;
+    const long long sb = (long long)blockIdx.x * a.seg_per_chunk;
+    const long long se = sb + a.seg_per_chunk < a.nseg ? sb + a.seg_per_chunk : a.nseg;
+    const int steps = se > sb ? (int)(se - sb) : 0;
+    constexpr int MT = BC / 16, NT = BN / 8, TILES = 9 * MT * NT;
+    constexpr int PER_WARP = (TILES + 7) / 8;
+    const Grid3 g = a.g;
+    float acc[PER_WARP][4];
+#pragma unroll
+    for (int i = 0; i < PER_WARP; ++i) acc[i][0] = acc[i][1] = acc[i][2] = acc[i][3] = 0.f;
+
+    // coordinates of the next segment to stage (segments are loaded strictly in order)
+    int lx0, ly, lz;
+    {
+        const unsigned sg = (unsigned)sb;                 // grids hold fewer than 2^31 voxels
+        const unsigned q = sg / (unsigned)a.seg_x;
+        lx0 = (int)(sg - q * (unsigned)a.seg_x) * WSEG;
+        ly = (int)(q % (unsigned)g.ny);
+        lz = (int)(q / (unsigned)g.ny);
+    }
+    auto load = [&](int buf) {
+        const int zz = lz + dz - 1;
+        const bool zok = zz >= 0 && zz < g.nz;
+        for (int i = tid; i < 3 * RUN * CX; i += THREADS) {
+            const int ch = i % CX, pos = (i / CX) % RUN, r = i / (CX * RUN);
+            const int xx = lx0 - 1 + pos, yy = ly + r - 1;
+            const bool ok = zok && xx >= 0 && xx < g.nx && yy >= 0 && yy < g.ny;
+            const int v = ok ? xx + g.nx * (yy + g.ny * zz) : 0;
+            cp_async16(&sX[buf][(r * RUN + pos) * XST + ch * 8], a.in.ptr + (long long)v * a.in.stride + a.in.c0 + c0 + ch * 8,
+                       ok);
+        }
+        for (int i = tid; i < WSEG * CY; i += THREADS) {
+            const int ch = i % CY, k = i / CY;
+            const int xx = lx0 + k;
+            const bool ok = xx < g.nx;
+            const int v = ok ? xx + g.nx * (ly + g.ny * lz) : 0;
+            cp_async16(&sY[buf][k * YST + ch * 8], a.dy.ptr + (long long)v * a.dy.stride + a.dy.c0 + n0 + ch * 8, ok);
+        }
+        lx0 += WSEG;
+        if (lx0 >= a.seg_x * WSEG) {
+            lx0 = 0;
+            if (++ly == g.ny) { ly = 0; ++lz; }
+        }
+    };
+
+#pragma unroll
+    for (int st = 0; st < NST - 1; ++st) {
+        if (st < steps) load(st);
+        cp_async_commit();
+    }
+    for (int s = 0; s < steps; ++s) {
+        const int buf = s % NST;
+        cp_async_wait<NST - 2>();
+        __syncthreads();
+        if (s + NST - 1 < steps) load((s + NST - 1) % NST);
+        cp_async_commit();
+#pragma unroll
+        for (int kk = 0; kk < WSEG; kk += 16) {
+            uint32_t bfr[NT][2];                          // dy fragments, shared by the nine taps
+#pragma unroll
+            for (int nt = 0; nt < NT; ++nt) {
+                const int row = kk + (lane & 7) + 8 * ((lane >> 3) & 1);
+                ldsm_x2_t(bfr[nt][0], bfr[nt][1], &sY[buf][row * YST + nt * 8]);
+            }
+#pragma unroll
+            for (int i = 0; i < PER_WARP; ++i) {
+                const int tile = warp + 8 * i;
+                if (tile >= TILES) break;
+                const int t9 = tile / (MT * NT), rem = tile % (MT * NT);
+                const int mt = rem / NT, nt = rem % NT;
+                const int ddx = t9 % 3, ddy = t9 / 3;
+                uint32_t a0, a1, a2, a3;
+                // A (M = channel, K = position) from the run of row offset ddy, shifted by ddx
+                const int j = lane >> 3;
+                const int row = ddy * RUN + ddx + kk + (lane & 7) + 8 * (j >> 1);
+                const int col = mt * 16 + 8 * (j & 1);
+                ldsm_x4_t(a0, a1, a2, a3, &sX[buf][row * XST + col]);
+                uint32_t b0 = bfr[0][0], b1 = bfr[0][1];
+#pragma unroll
+                for (int q = 1; q < NT; ++q)              // select, not an indexed (local-memory) read
+                    if (q == nt) { b0 = bfr[q][0]; b1 = bfr[q][1]; }
+                mma_bf16(acc[i], a0, a1, a2, a3, b0, b1);
+            }
+        }
+    }
+    cp_async_wait<0>();
+    const int gq = lane >> 2, t4 = lane & 3;
+#pragma unroll
+    for (int i = 0; i < PER_WARP; ++i) {
+        const int tile = warp + 8 * i;
+        if (tile >= TILES) break;
+        const int t9 = tile / (MT * NT), rem = tile % (MT * NT);
+        const int mt = rem / NT, nt = rem % NT;
+        const int t = 9 * dz + t9;                       // tap index dx + 3 dy + 9 dz
+        float* P = a.partial + ((long long)blockIdx.x * 27 + t) * a.cin * a.cout;
+        const int c = c0 + mt * 16 + gq, n = n0 + nt * 8 + 2 * t4;
+        P[(long long)c * a.cout + n] = acc[i][0];
+        P[(long long)c * a.cout + n + 1] = acc[i][1];
+        P[(long long)(c + 8) * a.cout + n] = acc[i][2];
+        P[(long long)(c + 8) * a.cout + n + 1] = acc[i][3];
+    }
+}
+
 }  // namespace unet
 }  // namespace ocmc

@@ -267,6 +267,29 @@ def run_study(n_train=200, n_eval=8, lows=(10**5, 10**6, 10**7), n_high=10**8,
     return rep
 
 
+def time_training(shape=(128, 128, 128), steps=5, warmup=2, seed=1):
+    """Mean CUDA-event time (ms) of one training step (forward, loss, backward, Adam) on seeded
+    synthetic inputs of the given grid; the study's pairs are not needed for timing."""
+    import torch
+    from . import ocmc
+    rng = np.random.default_rng(seed)
+    dose = torch.from_numpy(rng.random(shape, dtype=np.float32)).cuda()
+    sig = torch.from_numpy((0.1 * rng.random(shape)).astype(np.float32)).cuda()
+    dens = torch.from_numpy(rng.uniform(0.3, 1.8, shape).astype(np.float32)).cuda()
+    net = ocmc.UNet(shape, seed=seed)
+    ms = []
+    for k in range(warmup + steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        net.train_step(dose, dens, dose, 1e-4, sigma=sig)
+        e1.record()
+        e1.synchronize()
+        if k >= warmup:
+            ms.append(e0.elapsed_time(e1))
+    net.close()
+    return float(np.mean(ms)) if ms else 0.0
+
+
 def main(argv=None):
     import argparse
     import json
@@ -281,8 +304,13 @@ def main(argv=None):
     ap.add_argument("--lr", type=float, default=5e-4)
     ap.add_argument("--weights-out", default=None)
     ap.add_argument("--report", default=None)
+    ap.add_argument("--time-steps", type=int, default=0,
+                    help="only time this many training steps on synthetic input (after two warm-up steps)")
     a = ap.parse_args(argv)
     g = a.grid
+    if a.time_steps:
+        print(json.dumps({"grid": g, "train_step_ms": time_training((g, g, g), steps=a.time_steps)}))
+        return
     rep = run_study(n_train=a.train, n_eval=a.eval, n_high=int(a.n_high), steps=a.steps, lr=a.lr,
                     shape=(g, g, g), voxel=(a.voxel,) * 3, weights_out=a.weights_out,
                     log=lambda m: print(m, flush=True))
