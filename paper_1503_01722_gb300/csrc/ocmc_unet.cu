@@ -491,7 +491,8 @@ cudaError_t layer_bwd(ocmc_unet* u, const Layer& L, bool need_dx, cudaStream_t s
         if (e != cudaSuccess) return e;
     }
     long long nout = u->g[L.lout].n();
-    int blocks = grid_for(nout * L.cout);
+    // four blocks per SM stream dy once; few partials keep their fixed-order sum short
+    int blocks = (int)std::min<long long>(grid_for(nout * L.cout), 4LL * sm_count());
     k_bias_part<<<blocks, 256, 0, s>>>(dy.ptr, dy.stride, dy.c0, L.cout, nout, u->bpart);
     sum_rows(u->bpart, blocks, L.cout, u->grads + L.boff, s);
     e = cudaGetLastError();

@@ -249,8 +249,11 @@ __global__ void __launch_bounds__(THREADS) k_conv(const ConvArgs a)
         }
     }
     cp_async_wait<0>();
-    // epilogue: rows g and g+8 of the warp's 16, columns 2t, 2t+1 of each n-tile
+    // epilogue: rows g and g+8 of the warp's 16, columns 2t, 2t+1 of each n-tile. UP column
+    // p * cout + n: cout is a power of two in the network, so p and n come from a shift and a mask
     const int g = lane >> 2, t4 = lane & 3;
+    const bool pow2 = (a.cout & (a.cout - 1)) == 0;
+    const int csh = 31 - __clz(a.cout);
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
         long long row = r0 + warp * 16 + g + 8 * h;
@@ -265,8 +268,11 @@ __global__ void __launch_bounds__(THREADS) k_conv(const ConvArgs a)
 #pragma unroll
         for (int j = 0; j < BN / 8; ++j) {
             const int col = n0 + j * 8 + 2 * t4;
-            const int p = a.mode == UP ? col / a.cout : 0;
-            const int n = a.mode == UP ? col % a.cout : col;
+            int p = 0, n = col;
+            if (a.mode == UP) {
+                p = pow2 ? col >> csh : col / a.cout;
+                n = col - p * a.cout;
+            }
             long long v = row;
             if (a.mode == UP) {
                 const int ox = 2 * ux + (p & 1), oy = 2 * uy + ((p >> 1) & 1), oz = 2 * uz + (p >> 2);
