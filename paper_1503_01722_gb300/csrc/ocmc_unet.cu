@@ -358,6 +358,10 @@ cudaError_t launch_conv_bk(const ConvArgs& a, cudaStream_t s)
 
 cudaError_t launch_conv(const ConvArgs& a, cudaStream_t s)
 {
+    // 16-byte copies and stores: channel offsets and strides in multiples of 8 (BF16)
+    if (a.in.c0 % 8 || a.in.stride % 8 || a.out.c0 % 8 || a.out.stride % 8 || a.cin % 16 || a.cout % 16 ||
+        (a.mask && (a.mask_c0 % 8 || a.mask_stride % 8)))
+        return cudaErrorInvalidValue;
     if (a.mode == CONV3 && a.wtc && conv3_tc_supported(a.cin, a.cout)) return launch_conv3_tc(a, a.wtc, a.err, s);
     return a.cin % 32 == 0 ? launch_conv_bk<32>(a, s) : launch_conv_bk<16>(a, s);
 }

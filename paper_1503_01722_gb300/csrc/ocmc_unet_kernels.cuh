@@ -133,10 +133,12 @@ constexpr int THREADS = 256;   // 8 warps, 16 rows each
 constexpr int NSTAGE = 4;      // cp.async pipeline depth (K chunks in flight)
 
 // Shared memory of k_conv<BK, BN>: NSTAGE stages of an A tile (BM x BK) and a B tile (BK x BN),
-// rows padded by 16 bytes against bank conflicts.
+// rows padded by 16 bytes against bank conflicts; reused for the epilogue's FP32 output tile.
 __host__ __device__ constexpr int conv_smem_bytes(int bk, int bn)
 {
-    return NSTAGE * (BM * (bk + 8) + bk * (bn + 8)) * 2;
+    // the pipeline stages, or the FP32 output tile staged by the epilogue, whichever is larger
+    return NSTAGE * (BM * (bk + 8) + bk * (bn + 8)) * 2 > BM * (bn + 5) * 4 ? NSTAGE * (BM * (bk + 8) + bk * (bn + 8)) * 2
+                                                                             : BM * (bn + 5) * 4;
 }
 
 // Implicit-GEMM convolution. BK: input channels per K chunk (16 or 32); BN: output columns per
@@ -249,53 +251,87 @@ __global__ void __launch_bounds__(THREADS) k_conv(const ConvArgs a)
         }
     }
     cp_async_wait<0>();
-    // epilogue: rows g and g+8 of the warp's 16, columns 2t, 2t+1 of each n-tile. UP column
-    // p * cout + n: cout is a power of two in the network, so p and n come from a shift and a mask
-    const int g = lane >> 2, t4 = lane & 3;
+    __syncthreads();                             // the pipeline buffers are free: stage the tile
+    // epilogue, in two passes through shared memory so that every store is 16 bytes: the FP32
+    // fragments (rows g and g+8 of the warp's 16, columns 2t, 2t+1 of each n-tile) go to a
+    // [BM][BN] staging tile; then each thread finishes 8 consecutive columns of one row (bias,
+    // accumulate, ReLU, mask, BF16) and stores them at once. UP column p * cout + n: cout is a
+    // power of two in the network, so p and n come from a shift and a mask.
+    constexpr int CST = BN + 4;
+    float* sC = reinterpret_cast<float*>(conv_smem);
+    unsigned* sRow = reinterpret_cast<unsigned*>(sC + BM * CST);   // UP: coarse (x, y, z) of each row, 10 bits each
+    if (a.mode == UP && tid < BM) {
+        const unsigned row = (unsigned)(r0 + tid), nx = (unsigned)a.gin.nx, ny = (unsigned)a.gin.ny;
+        const unsigned q = row / nx;                                 // grids hold fewer than 2^31 voxels, sides <= 512
+        sRow[tid] = (row - q * nx) | ((q % ny) << 10) | ((q / ny) << 20);
+    }
+    {
+        const int g = lane >> 2, t4 = lane & 3;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            float* rowp = sC + (warp * 16 + g + 8 * h) * CST + 2 * t4;
+#pragma unroll
+            for (int j = 0; j < BN / 8; ++j) *reinterpret_cast<float2*>(rowp + j * 8) = make_float2(acc[j][2 * h], acc[j][2 * h + 1]);
+        }
+    }
+    __syncthreads();
     const bool pow2 = (a.cout & (a.cout - 1)) == 0;
     const int csh = 31 - __clz(a.cout);
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        long long row = r0 + warp * 16 + g + 8 * h;
+    constexpr int NCH = BN / 8;
+    for (int q = tid; q < BM * NCH; q += THREADS) {
+        const int r = q / NCH, cc = q % NCH;
+        const long long row = r0 + r;
         if (row >= rows) continue;
-        int ux = 0, uy = 0, uz = 0;              // UP: the row's coarse voxel
+        const int col = n0 + cc * 8;
+        int n = col;
+        long long v = row;
         if (a.mode == UP) {
-            ux = (int)(row % a.gin.nx);
-            const long long q = row / a.gin.nx;
-            uy = (int)(q % a.gin.ny);
-            uz = (int)(q / a.gin.ny);
+            const int p = pow2 ? col >> csh : col / a.cout;
+            n = col - p * a.cout;
+            const unsigned c3 = sRow[r];
+            const int ux = (int)(c3 & 1023u), uy = (int)((c3 >> 10) & 1023u), uz = (int)(c3 >> 20);
+            const int ox = 2 * ux + (p & 1), oy = 2 * uy + ((p >> 1) & 1), oz = 2 * uz + (p >> 2);
+            if (ox >= a.gout.nx || oy >= a.gout.ny || oz >= a.gout.nz) continue;
+            v = ox + (long long)a.gout.nx * (oy + (long long)a.gout.ny * oz);
         }
+        float f[8];
+        const float4 lo = *reinterpret_cast<const float4*>(sC + r * CST + cc * 8);
+        const float4 hi = *reinterpret_cast<const float4*>(sC + r * CST + cc * 8 + 4);
+        f[0] = lo.x; f[1] = lo.y; f[2] = lo.z; f[3] = lo.w; f[4] = hi.x; f[5] = hi.y; f[6] = hi.z; f[7] = hi.w;
+        if (a.bias) {
 #pragma unroll
-        for (int j = 0; j < BN / 8; ++j) {
-            const int col = n0 + j * 8 + 2 * t4;
-            int p = 0, n = col;
-            if (a.mode == UP) {
-                p = pow2 ? col >> csh : col / a.cout;
-                n = col - p * a.cout;
-            }
-            long long v = row;
-            if (a.mode == UP) {
-                const int ox = 2 * ux + (p & 1), oy = 2 * uy + ((p >> 1) & 1), oz = 2 * uz + (p >> 2);
-                if (ox >= a.gout.nx || oy >= a.gout.ny || oz >= a.gout.nz) continue;
-                v = ox + (long long)a.gout.nx * (oy + (long long)a.gout.ny * oz);
-            }
-            float x0 = acc[j][2 * h], x1 = acc[j][2 * h + 1];
-            if (a.bias) { x0 += a.bias[n]; x1 += a.bias[n + 1]; }
-            __nv_bfloat162* o = reinterpret_cast<__nv_bfloat162*>(a.out.ptr + v * a.out.stride + a.out.c0 + n);
-            if (a.accumulate) {
-                float2 old = __bfloat1622float2(*o);
-                x0 += old.x;
-                x1 += old.y;
-            }
-            if (a.relu) { x0 = fmaxf(x0, 0.f); x1 = fmaxf(x1, 0.f); }
-            if (a.mask) {
-                __nv_bfloat162 mk = *reinterpret_cast<const __nv_bfloat162*>(a.mask + v * a.mask_stride + a.mask_c0 + n);
-                float2 m = __bfloat1622float2(mk);
-                if (!(m.x > 0.f)) x0 = 0.f;
-                if (!(m.y > 0.f)) x1 = 0.f;
-            }
-            *o = __floats2bfloat162_rn(x0, x1);
+            for (int e = 0; e < 8; ++e) f[e] += a.bias[n + e];
         }
+        uint4* o = reinterpret_cast<uint4*>(a.out.ptr + v * a.out.stride + a.out.c0 + n);
+        if (a.accumulate) {
+            const uint4 old = *o;
+            const __nv_bfloat162* ob = reinterpret_cast<const __nv_bfloat162*>(&old);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const float2 t = __bfloat1622float2(ob[e]);
+                f[2 * e] += t.x;
+                f[2 * e + 1] += t.y;
+            }
+        }
+        if (a.relu) {
+#pragma unroll
+            for (int e = 0; e < 8; ++e) f[e] = fmaxf(f[e], 0.f);
+        }
+        if (a.mask) {
+            const uint4 mv = *reinterpret_cast<const uint4*>(a.mask + v * a.mask_stride + a.mask_c0 + n);
+            const __nv_bfloat162* mb = reinterpret_cast<const __nv_bfloat162*>(&mv);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const float2 t = __bfloat1622float2(mb[e]);
+                if (!(t.x > 0.f)) f[2 * e] = 0.f;
+                if (!(t.y > 0.f)) f[2 * e + 1] = 0.f;
+            }
+        }
+        uint4 w;
+        __nv_bfloat162* wb = reinterpret_cast<__nv_bfloat162*>(&w);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) wb[e] = __floats2bfloat162_rn(f[2 * e], f[2 * e + 1]);
+        *o = w;
     }
 }
 
