@@ -209,6 +209,43 @@ def test_error_statuses(ocmc):
             e.dose()
 
 
+def test_full_size_workload(ocmc):
+    """The timed workload at its full size in the timed launch configuration (6 MV on the
+    slab phantom 120^3, 10^8 histories per launch): what holds at any size -- the energy
+    balance, nothing dropped, every history run once, the same tally bit for bit from two
+    halves of the history range and from another launch shape -- and the deposited energy per
+    history against the oracle's (2*10^5 histories) within its statistical error. The dose
+    itself is compared voxel by voxel at this size by tests/parity_full_size.py (the oracle
+    needs hours of CPU time for 10^8 histories)."""
+    ph, beam = I.photon_slab_120()
+    n = 100_000_000
+    with ocmc.Engine(0) as e:
+        e.create_phantom(ph)
+        e.set_source(beam)
+        e.run(n, seed=1)
+        st = e.stats()
+        full = e.raw_tally()
+        e.reset()
+        e.run_range(0, n // 2, n, seed=1)
+        e.run_range(n // 2, n - n // 2, n, seed=1)
+        halves = e.raw_tally()
+    check_conservation(st)
+    assert st["histories"] == n and st["missed"] == 0
+    assert np.array_equal(full, halves)
+    with ocmc.Engine(0, block_threads=256, blocks_per_sm=3, max_registers=80) as e:
+        e.create_phantom(ph)
+        e.set_source(beam)
+        e.run(n, seed=1)
+        assert np.array_equal(e.raw_tally(), full)
+    B = full.shape[0]
+    m = 200_000
+    r = O.run(ph, beam, m, seed=1, p=O.params(n_batches=B))
+    e_gpu, e_orc = st["e_dep"] / n, r.ledger["e_dep"] / m
+    per_batch = r.tally.sum(axis=(1, 2, 3)) / 2 ** 28 / (m / B)
+    sd = per_batch.std(ddof=1) / math.sqrt(B)
+    assert abs(e_gpu - e_orc) < 4 * sd + 1e-3 * e_orc, (e_gpu, e_orc, sd)
+
+
 def test_emergency_switch_prevents_overflow(ocmc):
     """Small stacks with a switch threshold just below their capacity: a warp switches type
     when the other stack nears its capacity, so nothing overflows and the tally equals the
