@@ -438,7 +438,7 @@ def main():
     ap.add_argument("--no-study", action="store_true", help="denoiser_128: inference timing only")
     ap.add_argument("--beamlet-scale", type=float, default=1.0, help="beamlets_ct: scale every beamlet's histories")
     ap.add_argument("--study-train", type=int, default=200, help="denoiser_128: training cases")
-    ap.add_argument("--study-steps", type=int, default=8000, help="denoiser_128: training steps")
+    ap.add_argument("--study-steps", type=int, default=12000, help="denoiser_128: training steps")
     args = ap.parse_args()
 
     make, n_default, desc = WORKLOADS[args.workload]

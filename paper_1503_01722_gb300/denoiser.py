@@ -72,17 +72,24 @@ def make_pairs(cases, n_low, n_high, seed=1, device=0, engine=None, log=None):
 
 
 def train(net: ocmc.UNet, pairs, steps: int, lr: float = 5e-4, lr_final: float = 2e-5, warmup: int = 300,
-          seed: int = 0, log_every: int = 0, log=print):
+          seed: int = 0, log_every: int = 0, log=print, flips: bool = False):
     """Adam on one pair per step, pairs drawn in shuffled epochs; the learning rate rises
     linearly over `warmup` steps to lr, then decays to lr_final along a cosine (a high rate
     from the start can silence every ReLU of a layer, after which the network only returns its
-    input). Returns the per-step losses."""
+    input). With flips, each step mirrors its pair (all four grids alike) along a random
+    subset of the three axes: a mirrored case is another valid geometry, so the network sees
+    eight times as many distinct cases. Returns the per-step losses."""
     rng = np.random.default_rng(seed)
     order, losses = [], []
     for t in range(steps):
         if not order:
             order = list(rng.permutation(len(pairs)))
         low, low_sigma, dens, high = pairs[order.pop()]
+        if flips:
+            bits = int(rng.integers(0, 8))
+            dims = [d for d in range(3) if bits >> d & 1]
+            if dims:
+                low, low_sigma, dens, high = (torch.flip(x, dims).contiguous() for x in (low, low_sigma, dens, high))
         if t < warmup:
             a = lr * (t + 1) / warmup
         else:
@@ -182,9 +189,9 @@ def _cases(seeds, shape, voxel, workers=8):
 
 
 def run_study(n_train=200, n_eval=8, lows=(10**5, 10**6, 10**7), n_high=10**8,
-              n_ref=(2 * 10**9, 3 * 10**8), steps=8000, lr=5e-4, shape=(128, 128, 128),
+              n_ref=(2 * 10**9, 3 * 10**8), steps=12000, lr=5e-4, shape=(128, 128, 128),
               voxel=(0.25, 0.25, 0.25), target=0.01, k_sigma=4.0, device=0, seed=1, log=print,
-              weights_out=None, warmup=300):
+              weights_out=None, warmup=300, flips=True):
     """Generate training pairs on random cases, train the network, then on held-out cases
     compare plain and denoised Monte Carlo by the wall time each needs to reach `target`
     against a reference of n_ref histories (photon, electron beams). Returns a report dict."""
@@ -196,7 +203,7 @@ def run_study(n_train=200, n_eval=8, lows=(10**5, 10**6, 10**7), n_high=10**8,
     eng = ocmc.Engine(device)
     net = ocmc.UNet(shape, device=device, seed=seed)
     rep = {"shape": list(shape), "voxel_cm": list(voxel), "n_train": n_train, "n_eval": n_eval,
-           "lows": list(lows), "n_high": n_high, "n_ref": list(n_ref), "steps": steps, "target": target,
+           "lows": list(lows), "n_high": n_high, "n_ref": list(n_ref), "steps": steps, "flips": flips, "target": target,
            "k_sigma": k_sigma, "t_case_generation_s": t_cases}
     try:
         # training data: several input noise levels per case, one target
@@ -219,7 +226,8 @@ def run_study(n_train=200, n_eval=8, lows=(10**5, 10**6, 10**7), n_high=10**8,
         torch.cuda.synchronize()
         rep["t_pairs_s"] = time.perf_counter() - t0
         t0 = time.perf_counter()
-        losses = train(net, pairs, steps, lr=lr, warmup=warmup, seed=seed, log_every=max(steps // 10, 1), log=log)
+        losses = train(net, pairs, steps, lr=lr, warmup=warmup, seed=seed, log_every=max(steps // 10, 1), log=log,
+                       flips=flips)
         torch.cuda.synchronize()
         rep["t_train_s"] = time.perf_counter() - t0
         rep["loss_first_100"] = float(np.mean(losses[:100]))
@@ -297,7 +305,8 @@ def main(argv=None):
                                              "plain and denoised Monte Carlo by time to a target error")
     ap.add_argument("--train", type=int, default=200)
     ap.add_argument("--eval", type=int, default=8)
-    ap.add_argument("--steps", type=int, default=8000)
+    ap.add_argument("--steps", type=int, default=12000)
+    ap.add_argument("--no-flips", action="store_true", help="train without mirrored copies of the pairs")
     ap.add_argument("--n-high", type=float, default=1e8)
     ap.add_argument("--grid", type=int, default=128)
     ap.add_argument("--voxel", type=float, default=0.25)
@@ -311,7 +320,7 @@ def main(argv=None):
     if a.time_steps:
         print(json.dumps({"grid": g, "train_step_ms": time_training((g, g, g), steps=a.time_steps)}))
         return
-    rep = run_study(n_train=a.train, n_eval=a.eval, n_high=int(a.n_high), steps=a.steps, lr=a.lr,
+    rep = run_study(n_train=a.train, n_eval=a.eval, n_high=int(a.n_high), steps=a.steps, lr=a.lr, flips=not a.no_flips,
                     shape=(g, g, g), voxel=(a.voxel,) * 3, weights_out=a.weights_out,
                     log=lambda m: print(m, flush=True))
     s = json.dumps(rep)
