@@ -31,12 +31,12 @@ import ocmc_inputs as I  # noqa: E402
 # smsp__thread_inst_executed.sum divided by the kernel's own lane-step counter)
 # and DRAM bytes per history, from the ncu capture summarised in
 # profiles/k_transport_photon_slab_120.md (re-measured whenever the kernel changes).
-INST_PER_LANE_STEP = 660.9
+INST_PER_LANE_STEP = 732.2
 # DRAM bytes of one transport launch measured by ncu on the full default workload
-DRAM_BYTES_PER_LAUNCH = {("photon_slab_120", 100_000_000): 20.850e9}
+DRAM_BYTES_PER_LAUNCH = {("photon_slab_120", 100_000_000): 21.222e9}
 # the same for the beamlet-mode kernel (hash tallies) on the 512-beamlet CT workload, measured by
 # ncu on the same workload with every beamlet's histories scaled by 0.02
-INST_PER_LANE_STEP_BEAMLETS = 699.9
+INST_PER_LANE_STEP_BEAMLETS = 772.6
 
 WORKLOADS = {
     "photon_slab_120": (I.photon_slab_120, 100_000_000,
@@ -439,6 +439,8 @@ def main():
     ap.add_argument("--beamlet-scale", type=float, default=1.0, help="beamlets_ct: scale every beamlet's histories")
     ap.add_argument("--study-train", type=int, default=200, help="denoiser_128: training cases")
     ap.add_argument("--study-steps", type=int, default=12000, help="denoiser_128: training steps")
+    ap.add_argument("--e-class-split", type=float, default=None,
+                    help="energy-class boundary (MeV) of the charged stacks; default: the engine's")
     args = ap.parse_args()
 
     make, n_default, desc = WORKLOADS[args.workload]
@@ -466,6 +468,8 @@ def main():
     params = {}
     if args.workload.startswith("paper_"):
         params = dict(e_abs_e=0.2, e_abs_g=0.05, w_cc=0.2, w_cb=0.05)
+    if args.e_class_split is not None:
+        params["e_class_split"] = args.e_class_split
     dist = None
     if world > 1:
         import torch.distributed as dist

@@ -81,6 +81,10 @@ typedef struct {
     int32_t refill_min;     /* free lanes a warp waits for before refilling (0=1)  */
     int32_t max_registers;  /* register cap of the transport kernel: 56, 64 or 80; */
                             /* 0 = 64 (with 1024-thread blocks)                    */
+    float e_class_split;    /* MeV; > 0: charged particles waiting below this      */
+                            /* energy go to a third per-warp stack, so that a warp */
+                            /* steps electrons of one energy class at a time       */
+                            /* (2.0; 0 = one charged stack)                        */
 } ocmc_params;
 
 /* Run statistics accumulated since the last ocmc_reset_tally(). */

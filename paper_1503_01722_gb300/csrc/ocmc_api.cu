@@ -73,6 +73,7 @@ const char* check_params(const ocmc_params* p)
         return "max_registers must be 0, 56, 64 or 80";
     if (!(p->beamlet_capacity_scale >= 0.f && p->beamlet_capacity_scale <= 1e6f))
         return "beamlet_capacity_scale must be in [0, 1e6]";
+    if (!(p->e_class_split >= 0.f && p->e_class_split <= 30.f)) return "e_class_split must be in [0, 30] MeV";
     return nullptr;
 }
 
@@ -256,6 +257,7 @@ void ocmc_default_params(ocmc_params* p)
     p->f_maxe = 0.05f;
     p->s_min = 1e-4f;
     p->n_batches = 10;
+    p->e_class_split = 2.0f;
 }
 
 ocmc_status ocmc_init(ocmc_ctx** out, int device, const ocmc_params* p)
@@ -553,7 +555,8 @@ ocmc_status ocmc_run_range(ocmc_ctx* c, uint64_t first, uint64_t count, uint64_t
     if (st != OCMC_OK) return st;
     int threads, blocks, cap, nreg;
     launch_shape(c, &threads, &blocks, &cap, &nreg);
-    size_t need = (size_t)blocks * (threads / 32) * 2 * cap;
+    const int nstk = c->p.e_class_split > 0.f ? 3 : 2;
+    size_t need = (size_t)blocks * (threads / 32) * nstk * cap;
     if (need > c->stack_records) {
         if (c->ran || c->last_stream) cudaDeviceSynchronize();
         CK(dalloc(&c->d_stacks, need), "stack allocation");
@@ -569,6 +572,8 @@ ocmc_status ocmc_run_range(ocmc_ctx* c, uint64_t first, uint64_t count, uint64_t
     a.key1 = (uint32_t)(seed >> 32);
     a.stacks = c->d_stacks;
     a.cap = cap;
+    a.nstk = nstk;
+    a.e_split = c->p.e_class_split;
     a.switch_high = c->p.switch_high ? c->p.switch_high : cap - cap / 16;
     a.switch_low = c->p.switch_low ? c->p.switch_low : 8;
     a.refill_min = c->p.refill_min ? c->p.refill_min : 1;

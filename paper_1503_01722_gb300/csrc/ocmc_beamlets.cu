@@ -104,10 +104,13 @@ ocmc_status beamlet_args(ocmc_ctx* c, unsigned long long total, uint64_t seed, T
     a.bl_overflow = c->d_bl_over;
     int cap;
     ctx_launch_shape(c, threads, blocks, &cap, nreg);
-    ocmc_status st = ctx_ensure_stacks(c, (size_t)*blocks * (*threads / 32) * 2 * cap);
+    const int nstk = c->p.e_class_split > 0.f ? 3 : 2;
+    ocmc_status st = ctx_ensure_stacks(c, (size_t)*blocks * (*threads / 32) * nstk * cap);
     if (st != OCMC_OK) return st;
     a.stacks = c->d_stacks;
     a.cap = cap;
+    a.nstk = nstk;
+    a.e_split = c->p.e_class_split;
     a.switch_high = c->p.switch_high ? c->p.switch_high : cap - cap / 16;
     a.switch_low = c->p.switch_low ? c->p.switch_low : 8;
     a.refill_min = c->p.refill_min ? c->p.refill_min : 1;
@@ -367,38 +370,42 @@ ocmc_status ocmc_autotune(ocmc_ctx* c, uint64_t pilot, ocmc_params* chosen)
     if (!c) return ctx_fail(c, OCMC_ERR_ARG, "ctx is NULL");
     if (!c->have_phantom || !c->have_source) return ctx_fail(c, OCMC_ERR_STATE, "need a phantom and a source");
     if (pilot < 1) return ctx_fail(c, OCMC_ERR_ARG, "pilot_histories must be > 0");
-    // (register cap, threads per block) pairs that fill an SM, x type-switch thresholds
+    // (register cap, threads per block) pairs that fill an SM, x type-switch thresholds, x
+    // energy classes of the charged stacks (one stack, or a second below 2 MeV)
     const int shape_c[][2] = {{64, 1024}, {64, 512}, {80, 256}, {56, 384}};
     const int high_c[] = {2048, 4096, 7680};   // of the default 8192-record stacks
     const int low_c[] = {8, 16};
+    const float split_c[] = {0.f, 2.f};
     ocmc_params base = c->p, best = c->p;
     float best_ms = 3.0e38f;
     for (const auto& sh : shape_c)
         for (int hi : high_c)
-            for (int lo : low_c) {
-                ocmc_params q = base;
-                q.max_registers = sh[0];
-                q.block_threads = sh[1];
-                q.blocks_per_sm = 0;
-                q.switch_high = hi;
-                q.switch_low = lo;
-                ocmc_status st = ocmc_set_params(c, &q);
-                if (st != OCMC_OK) return st;
-                float ms_min = 3.0e38f;
-                for (int rep = 0; rep < 3; ++rep) {
-                    st = ocmc_reset_tally(c);
-                    if (st == OCMC_OK) st = ocmc_run_range(c, 0, pilot, pilot, 1, nullptr);
+            for (int lo : low_c)
+                for (float sp : split_c) {
+                    ocmc_params q = base;
+                    q.max_registers = sh[0];
+                    q.block_threads = sh[1];
+                    q.blocks_per_sm = 0;
+                    q.switch_high = hi;
+                    q.switch_low = lo;
+                    q.e_class_split = sp;
+                    ocmc_status st = ocmc_set_params(c, &q);
                     if (st != OCMC_OK) return st;
-                    BCK(cudaEventSynchronize(c->ev1), "synchronize");
-                    float ms = 0.f;
-                    BCK(cudaEventElapsedTime(&ms, c->ev0, c->ev1), "timing");
-                    if (rep > 0) ms_min = std::min(ms_min, ms);
+                    float ms_min = 3.0e38f;
+                    for (int rep = 0; rep < 3; ++rep) {
+                        st = ocmc_reset_tally(c);
+                        if (st == OCMC_OK) st = ocmc_run_range(c, 0, pilot, pilot, 1, nullptr);
+                        if (st != OCMC_OK) return st;
+                        BCK(cudaEventSynchronize(c->ev1), "synchronize");
+                        float ms = 0.f;
+                        BCK(cudaEventElapsedTime(&ms, c->ev0, c->ev1), "timing");
+                        if (rep > 0) ms_min = std::min(ms_min, ms);
+                    }
+                    if (ms_min < best_ms) {
+                        best_ms = ms_min;
+                        best = q;
+                    }
                 }
-                if (ms_min < best_ms) {
-                    best_ms = ms_min;
-                    best = q;
-                }
-            }
     ocmc_status st = ocmc_set_params(c, &best);
     if (st == OCMC_OK) st = ocmc_reset_tally(c);
     if (st == OCMC_OK && chosen) *chosen = best;

@@ -151,8 +151,10 @@ struct TransportArgs {
     uint32_t key0, key1;
     unsigned long long* tally;
     // scratch
-    PRec* stacks;               // per warp: 2 stacks of `cap` records
+    PRec* stacks;               // per warp: nstk stacks of `cap` records
     int cap;
+    int nstk;                   // 2 (photons, charged) or 3 (photons, charged >= e_split, charged < e_split)
+    float e_split;              // MeV; energy-class boundary of the charged stacks when nstk == 3
     int switch_high, switch_low;
     int refill_min;                      // free lanes needed before a warp refills (>= 1)
     unsigned long long* hist_counter;

@@ -31,7 +31,7 @@ namespace {
 
 constexpr size_t NOALLOC_BYTES = OCMC_NOALLOC_SCRATCH_BYTES;
 constexpr int NOALLOC_THREADS = 256;
-constexpr int NOALLOC_CAP = 256;        // records per stack (two stacks per warp)
+constexpr int NOALLOC_CAP = 256;        // records per stack (two or three stacks per warp)
 constexpr int MAX_DEVICES = 64;
 
 static __device__ __align__(256) unsigned char g_scratch[NOALLOC_BYTES];
@@ -118,7 +118,8 @@ extern "C" ocmc_status ocmc_run_noalloc(int device, int nx, int ny, int nz, cons
         p.blocks_per_sm < 0 || p.blocks_per_sm > 32 ||
         (p.stack_capacity != 0 && (p.stack_capacity < 64 || p.stack_capacity > (1 << 20))) || p.switch_high < 0 ||
         p.switch_low < 0 || p.switch_low > 32 || p.refill_min < 0 || p.refill_min > 32 ||
-        (p.max_registers != 0 && !transport_nreg_supported(p.max_registers)))
+        (p.max_registers != 0 && !transport_nreg_supported(p.max_registers)) ||
+        !(p.e_class_split >= 0.f && p.e_class_split <= 30.f))
         return M.fail(OCMC_ERR_ARG, "invalid execution parameters");
     double W = 0.0;
     for (int i = 0; i < n_bins; ++i) {
@@ -168,14 +169,15 @@ extern "C" ocmc_status ocmc_run_noalloc(int device, int nx, int ny, int nz, cons
     const int nreg = p.max_registers ? p.max_registers : 80;
     int bps = p.blocks_per_sm ? p.blocks_per_sm : transport_max_blocks_per_sm(threads, smem, nreg);
     if (bps < 1) bps = 1;
-    size_t per_block = (size_t)(threads / 32) * 2 * cap * sizeof(PRec);
+    const int nstk = p.e_class_split > 0.f ? 3 : 2;
+    size_t per_block = (size_t)(threads / 32) * nstk * cap * sizeof(PRec);
     size_t room = NOALLOC_BYTES - cv.used;
     long long blocks = (long long)sms * bps;
     if (!p.blocks_per_sm && (size_t)blocks * per_block > room) blocks = (long long)(room / per_block);
     if (blocks < 1 || (size_t)blocks * per_block > room)
         return M.fail(OCMC_ERR_ARG, "launch shape needs more secondary-stack scratch than the 64 MiB static array "
                                    "(lower stack_capacity, block_threads or blocks_per_sm)");
-    PRec* stacks = cv.take<PRec>((size_t)blocks * (threads / 32) * 2 * cap);
+    PRec* stacks = cv.take<PRec>((size_t)blocks * (threads / 32) * nstk * cap);
 
     cudaStream_t s = reinterpret_cast<cudaStream_t>(cuda_stream);
     size_t stats_off = (size_t)(reinterpret_cast<unsigned char*>(stats) - base);
@@ -203,6 +205,8 @@ extern "C" ocmc_status ocmc_run_noalloc(int device, int nx, int ny, int nz, cons
     a.tally = reinterpret_cast<unsigned long long*>(tally_dev);
     a.stacks = stacks;
     a.cap = cap;
+    a.nstk = nstk;
+    a.e_split = p.e_class_split;
     a.switch_high = p.switch_high ? p.switch_high : 256;
     a.switch_low = p.switch_low ? p.switch_low : 8;
     a.refill_min = p.refill_min ? p.refill_min : 1;

@@ -40,8 +40,8 @@ struct CtxT {
     static constexpr bool beamlets = BL;
     const TransportArgs& a;
     const SmemTables& T;
-    PRec* stk;                   // warp's stacks: [0, cap) photons, [cap, 2cap) charged
-    int* top;                    // shared: top[0] photons, top[1] charged
+    PRec* stk;                   // warp's stacks: [0, cap) photons, [cap, 2cap) charged, [2cap, 3cap) slow charged
+    int* top;                    // shared: top[0] photons, top[1] charged, top[2] charged below e_split
     unsigned long long* st;      // shared block statistics
     float inv_dx, inv_dy, inv_dz, Lx, Ly, Lz;
     bool ok;
@@ -49,6 +49,10 @@ struct CtxT {
 
 template <class C>
 __device__ __forceinline__ void stat_add(C& c, int k, unsigned long long v) { atomicAdd(c.st + k, v); }
+
+// Stack of a waiting charged particle: 1, or 2 below the energy-class boundary (e_split is 0
+// when the warps keep a single charged stack, so that everything then goes to stack 1).
+__device__ __forceinline__ int charged_stack(const TransportArgs& a, float E) { return E < a.e_split ? 2 : 1; }
 
 // fixed-point energy (round to nearest even) with 32-bit conversions only: below 2^32 units
 // (16 MeV) directly; above, q is a float >= 2^32 and therefore a multiple of 2^9, so q / 2^8 is
@@ -180,7 +184,7 @@ __device__ void emit_charged(C& c, const Lane& p, int type, float E, float du, f
 {
     uint32_t sub = child_sub(p.r.sub, p.r.n, slot);
     if (E >= c.a.pp.e_abs_e && !(c.a.pp.flags & 8)) {
-        push(c, 1, p.x, p.y, p.z, E, du, dv, dw, p.ix, p.iy, p.iz, type, p.r.h0, p.r.h1, sub);
+        push(c, charged_stack(c.a, E), p.x, p.y, p.z, E, du, dv, dw, p.ix, p.iy, p.iz, type, p.r.h0, p.r.h1, sub);
         return;
     }
     deposit(c, p, p.ix, p.iy, p.iz, E);
@@ -417,15 +421,15 @@ template <bool BL, bool PS, int NREG>
 __global__ void __maxnreg__(NREG) k_transport(const __grid_constant__ TransportArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ int s_top[MAX_WARPS][2];
+    __shared__ int s_top[MAX_WARPS][3];
     __shared__ unsigned long long s_st[ST_COUNT];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     for (int i = threadIdx.x; i < ST_COUNT; i += blockDim.x) s_st[i] = 0ull;
-    if (lane == 0) { s_top[wib][0] = 0; s_top[wib][1] = 0; }
+    if (lane == 0) { s_top[wib][0] = 0; s_top[wib][1] = 0; s_top[wib][2] = 0; }
     SmemTables T = stage_tables(a.t, smem);   // ends with __syncthreads()
 
     const long long gw = (long long)blockIdx.x * (blockDim.x >> 5) + wib;
-    CtxT<BL> c{a, T, a.stacks + (size_t)gw * 2 * a.cap, s_top[wib], s_st,
+    CtxT<BL> c{a, T, a.stacks + (size_t)gw * a.nstk * a.cap, s_top[wib], s_st,
           1.f / a.dx, 1.f / a.dy, 1.f / a.dz, a.nx * a.dx, a.ny * a.dy, a.nz * a.dz, true};
     const unsigned lt = (1u << lane) - 1u;
     const int src_mode = a.src.particle == 0 ? 0 : 1;
@@ -442,15 +446,17 @@ __global__ void __maxnreg__(NREG) k_transport(const __grid_constant__ TransportA
     unsigned n_fict = 0, n_hfict = 0;
     unsigned long long iters = 0, lanes_ph = 0, lanes_ch = 0, hist = 0, e_in = 0, e_miss = 0, missed = 0;
 
+    // modes (= stacks): 0 photons, 1 charged particles (at or above e_split when there are
+    // three stacks), 2 charged particles below e_split
     for (;;) {
         __syncwarp();
-        int top0 = min(c.top[0], a.cap), top1 = min(c.top[1], a.cap);
+        int top0 = min(c.top[0], a.cap), top1 = min(c.top[1], a.cap), top2 = a.nstk == 3 ? min(c.top[2], a.cap) : 0;
         unsigned act = __ballot_sync(FULL, active);
         int nfree = 32 - __popc(act);
         // refill when enough lanes are free: the refill code runs on the free lanes only,
         // so waiting for several of them spreads its cost
         if (nfree >= a.refill_min || nfree == 32) {
-            int topm = mode ? top1 : top0;
+            int topm = mode == 0 ? top0 : (mode == 1 ? top1 : top2);
             int rank = __popc(~act & lt);
             int take = min(nfree, topm);
             if (!active && rank < take) {
@@ -478,8 +484,9 @@ __global__ void __maxnreg__(NREG) k_transport(const __grid_constant__ TransportA
                         e_in += fx(p.E);
                         const bool charged = p.type != PHOTON;
                         if (p.E >= ecut && !(charged && (a.pp.flags & 8))) {
-                            if ((charged ? 1 : 0) == mode) active = true;
-                            else push_lane(c, charged ? 1 : 0, p);
+                            const int target = charged ? charged_stack(a, p.E) : 0;
+                            if (target == mode) active = true;
+                            else push_lane(c, target, p);
                         } else if (charged) {
                             absorb_charged(c, p);       // positrons annihilate
                         } else {
@@ -495,14 +502,24 @@ __global__ void __maxnreg__(NREG) k_transport(const __grid_constant__ TransportA
             __syncwarp();
             if (lane == 0) c.top[mode] = topm - take;
             __syncwarp();
-            if (mode) top1 = topm - take; else top0 = topm - take;
+            if (mode == 0) top0 = topm - take; else if (mode == 1) top1 = topm - take; else top2 = topm - take;
             act = __ballot_sync(FULL, active);
         }
         int nact = __popc(act);
-        int other = 1 - mode;
-        int topm = mode ? top1 : top0, topo = mode ? top0 : top1;
+        const int topm = mode == 0 ? top0 : (mode == 1 ? top1 : top2);
         bool m_avail = topm > 0 || ((ps_src || mode == src_mode) && !src_done);
-        bool o_avail = topo > 0 || ((ps_src || other == src_mode) && !src_done);
+        // the other mode: the fullest other stack that has work (or that the source feeds)
+        int other = -1, topo = 0;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const int tk = k == 0 ? top0 : (k == 1 ? top1 : top2);
+            if (k != mode && k < a.nstk && (tk > 0 || ((ps_src || k == src_mode) && !src_done)) &&
+                (other < 0 || tk > topo)) {
+                other = k;
+                topo = tk;
+            }
+        }
+        const bool o_avail = other >= 0;
         if (nact == 0) {
             if (m_avail) continue;
             if (o_avail) { mode = other; continue; }
@@ -519,7 +536,7 @@ __global__ void __maxnreg__(NREG) k_transport(const __grid_constant__ TransportA
             else if (topo >= emergency && topo > topm) sw = true;
         }
         if (sw) {
-            if (active) { push_lane(c, mode, p); active = false; }
+            if (active) { push_lane(c, mode ? charged_stack(a, p.E) : 0, p); active = false; }
             mode = other;
             just_switched = true;
             continue;

@@ -31,7 +31,8 @@ class Params(C.Structure):
                 ("n_batches", C.c_int32), ("flags", C.c_int32),
                 ("block_threads", C.c_int32), ("blocks_per_sm", C.c_int32), ("stack_capacity", C.c_int32),
                 ("switch_high", C.c_int32), ("switch_low", C.c_int32), ("stream_tag", C.c_uint32),
-                ("beamlet_capacity_scale", C.c_float), ("refill_min", C.c_int32), ("max_registers", C.c_int32)]
+                ("beamlet_capacity_scale", C.c_float), ("refill_min", C.c_int32), ("max_registers", C.c_int32),
+                ("e_class_split", C.c_float)]
 
 
 class Beamlet(C.Structure):

@@ -38,10 +38,12 @@ def test_default_params(lib):
     assert abs(p.e_abs_e - 0.2) < 1e-7 and abs(p.e_abs_g - 0.01) < 1e-9
     assert abs(p.w_cc - 0.2) < 1e-7 and abs(p.w_cb - 0.01) < 1e-9
     assert p.n_batches == 10 and p.flags == 0
+    assert abs(p.e_class_split - 2.0) < 1e-7
 
 
 @pytest.mark.parametrize("field,value", [("e_abs_e", 0.0), ("f_maxe", 0.9), ("n_batches", 0),
-                                         ("block_threads", 100), ("stack_capacity", 8)])
+                                         ("block_threads", 100), ("stack_capacity", 8), ("e_class_split", -1.0),
+                                         ("e_class_split", 40.0)])
 def test_invalid_params_rejected_before_device(lib, field, value):
     from paper_1503_01722_gb300 import ocmc
     p = ocmc.default_params()

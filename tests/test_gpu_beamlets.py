@@ -120,6 +120,6 @@ def test_autotune_keeps_the_dose(ocmc):
         ref = e.raw_tally()
         p = e.autotune(100_000)
         assert (p.max_registers, p.block_threads) in ((64, 1024), (64, 512), (80, 256), (56, 384))
-        assert p.switch_high in (2048, 4096, 7680)
+        assert p.switch_high in (2048, 4096, 7680) and p.e_class_split in (0.0, 2.0)
         e.run(50_000, seed=2)
         assert np.array_equal(e.raw_tally(), ref)
