@@ -78,7 +78,7 @@ typedef struct {
     float beamlet_capacity_scale; /* scales the pilot estimate of beamlet table    */
                             /* sizes (0 = 1); tables that fill up are enlarged and */
                             /* the run repeated, so any value gives the same dose  */
-    int32_t refill_min;     /* free lanes a warp waits for before refilling (0=1)  */
+    int32_t refill_min;     /* free lanes a warp waits for before refilling (0=6)  */
     int32_t max_registers;  /* register cap of the transport kernel: 56, 64 or 80; */
                             /* 0 = 64 (with 1024-thread blocks)                    */
     float e_class_split;    /* MeV; > 0: charged particles waiting below this      */

@@ -576,7 +576,7 @@ ocmc_status ocmc_run_range(ocmc_ctx* c, uint64_t first, uint64_t count, uint64_t
     a.e_split = c->p.e_class_split;
     a.switch_high = c->p.switch_high ? c->p.switch_high : cap - cap / 16;
     a.switch_low = c->p.switch_low ? c->p.switch_low : 8;
-    a.refill_min = c->p.refill_min ? c->p.refill_min : 1;
+    a.refill_min = c->p.refill_min ? c->p.refill_min : 6;
     CK(cudaMemsetAsync(c->d_counter, 0, sizeof(unsigned long long), s), "counter reset");
     CK(cudaEventRecord(c->ev0, s), "event");
     CK(launch_transport(a, blocks, threads, transport_smem_bytes(c->t.n_mat), s, nreg), "transport launch");

@@ -113,7 +113,7 @@ ocmc_status beamlet_args(ocmc_ctx* c, unsigned long long total, uint64_t seed, T
     a.e_split = c->p.e_class_split;
     a.switch_high = c->p.switch_high ? c->p.switch_high : cap - cap / 16;
     a.switch_low = c->p.switch_low ? c->p.switch_low : 8;
-    a.refill_min = c->p.refill_min ? c->p.refill_min : 1;
+    a.refill_min = c->p.refill_min ? c->p.refill_min : 6;
     return OCMC_OK;
 }
 

@@ -209,7 +209,7 @@ extern "C" ocmc_status ocmc_run_noalloc(int device, int nx, int ny, int nz, cons
     a.e_split = p.e_class_split;
     a.switch_high = p.switch_high ? p.switch_high : 256;
     a.switch_low = p.switch_low ? p.switch_low : 8;
-    a.refill_min = p.refill_min ? p.refill_min : 1;
+    a.refill_min = p.refill_min ? p.refill_min : 6;
     a.hist_counter = counter;
     a.stats = stats;
     a.err = err;

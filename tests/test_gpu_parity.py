@@ -98,7 +98,7 @@ def test_bit_reproducible_across_runs_and_launch_shapes(ocmc):
     for kw in ({}, {}, {"block_threads": 128}, {"block_threads": 64, "blocks_per_sm": 2, "stack_capacity": 256},
                {"switch_high": 1 << 20, "switch_low": 0}, {"switch_high": 33, "switch_low": 31},
                {"max_registers": 80, "block_threads": 256}, {"max_registers": 56, "block_threads": 384},
-               {"refill_min": 6}, {"e_class_split": 1.0}, {"e_class_split": 3.0, "stack_capacity": 256},
+               {"refill_min": 1}, {"refill_min": 12}, {"e_class_split": 1.0}, {"e_class_split": 3.0, "stack_capacity": 256},
                {"e_class_split": 0.5, "switch_high": 40, "switch_low": 2}):
         with ocmc.Engine(0, **kw) as e:
             e.create_phantom(ph)
