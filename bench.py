@@ -244,10 +244,7 @@ def run_beamlets_bench(args, make, desc):
         e2.create_phantom(ph)
         e2.set_beamlets(0, spec[0], spec[1], bl)
         e2.run_beamlets(seed=1)
-        nnz_bytes = 0
-        for b in range(len(bl)):
-            idx, dose, _ = e2.beamlet_dose(b)
-            nnz_bytes += idx.nbytes + dose.nbytes
+        nnz_bytes = sum(idx.nbytes + dose.nbytes for idx, dose in e2.beamlet_doses())
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
         e2.close()
     clocks = clk.summary()

@@ -329,6 +329,29 @@ class Engine:
                                               C.byref(nnz)))
         return idx, dose, raw
 
+    def beamlet_doses(self, raw=False):
+        """Every beamlet's sparse dose, [(voxel indices int32, dose float32 MeV/g per history
+        [, raw int64])] in beamlet order: one extraction per beamlet into reusable pinned host
+        buffers of one phantom's size (no size query, no pageable copies)."""
+        import torch
+        if self.shape is None:
+            raise OcmcError(ERR_STATE, "no phantom")
+        nvox = int(np.prod(self.shape))
+        if getattr(self, "_bl_buf", None) is None or self._bl_buf[0].numel() < nvox:
+            self._bl_buf = (torch.empty(nvox, dtype=torch.int32).pin_memory(),
+                            torch.empty(nvox, dtype=torch.float32).pin_memory(),
+                            torch.empty(nvox, dtype=torch.int64).pin_memory())
+        bi, bd, br = self._bl_buf
+        nnz = C.c_int64()
+        out = []
+        for b in range(self.n_beamlets):
+            self._check(lib.ocmc_get_beamlet_dose(self._c, b, C.c_void_p(bi.data_ptr()), C.c_void_p(bd.data_ptr()),
+                                                  C.c_void_p(br.data_ptr()) if raw else None, nvox, C.byref(nnz)))
+            n = nnz.value
+            item = (bi[:n].numpy().copy(), bd[:n].numpy().copy())
+            out.append(item + (br[:n].numpy().copy(),) if raw else item)
+        return out
+
     def autotune(self, pilot_histories):
         p = Params()
         self._check(lib.ocmc_autotune(self._c, int(pilot_histories), C.byref(p)))

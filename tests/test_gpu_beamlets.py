@@ -56,8 +56,12 @@ def test_beamlets_match_dense_runs_and_replay(ocmc, setup):
         e.run_beamlets(seed=5)           # graph replay
         outs2 = [e.beamlet_dose(b) for b in range(len(bl))]
         st2 = e.stats()
-    for (i1, d1, r1), (i2, d2, r2) in zip(outs, outs2):
+        batch = e.beamlet_doses(raw=True)     # every beamlet through reused pinned buffers
+        plain = e.beamlet_doses()
+    for (i1, d1, r1), (i2, d2, r2), (i3, d3, r3), (i4, d4) in zip(outs, outs2, batch, plain):
         assert np.array_equal(i1, i2) and np.array_equal(r1, r2) and np.array_equal(d1, d2)
+        assert np.array_equal(i1, i3) and np.array_equal(r1, r3) and np.array_equal(d1, d3)
+        assert np.array_equal(i1, i4) and np.array_equal(d1, d4)
     # a beamlet run replaces its tallies and its statistics
     assert st2["histories"] == st1["histories"] == sum(b["n_histories"] for b in bl)
     assert st2["lane_steps"] == st1["lane_steps"]
