@@ -150,12 +150,28 @@ void fill_args(const ocmc_ctx* c, TransportArgs& a)
     }
 }
 
+bool same_defs(const std::vector<MatDef>& a, const std::vector<MatDef>& b)
+{
+    if (a.size() != b.size()) return false;
+    for (size_t i = 0; i < a.size(); ++i) {
+        const MatDef &x = a[i], &y = b[i];
+        if (x.n != y.n || x.I_eV != y.I_eV || x.rho0 != y.rho0) return false;
+        for (int k = 0; k < x.n; ++k)
+            if (x.Z[k] != y.Z[k] || x.A[k] != y.A[k] || x.w[k] != y.w[k]) return false;
+    }
+    return true;
+}
+
 ocmc_status ensure_tables(ocmc_ctx* c, cudaStream_t s)
 {
     if (c->tables_valid) return OCMC_OK;
-    PhysParams pp{c->p.e_abs_e, c->p.e_abs_g, c->p.w_cc, c->p.w_cb, c->p.d_maxs, c->p.f_maxe, c->p.s_min,
-                  c->p.flags, c->p.n_batches};
-    CK(build_tables(c->t, pp, c->d_density, c->d_material, c->nvox, c->d_err, c->staged.data(), s), "table build");
+    if (!c->mat_tables_valid) {
+        PhysParams pp{c->p.e_abs_e, c->p.e_abs_g, c->p.w_cc, c->p.w_cb, c->p.d_maxs, c->p.f_maxe, c->p.s_min,
+                      c->p.flags, c->p.n_batches};
+        CK(build_material_tables(c->t, pp, c->staged.data(), s), "table build");
+        c->mat_tables_valid = true;
+    }
+    CK(build_phantom_tables(c->t, c->d_density, c->d_material, c->nvox, c->d_err, s), "table build");
     c->tables_valid = true;
     return OCMC_OK;
 }
@@ -322,7 +338,7 @@ ocmc_status ocmc_set_params(ocmc_ctx* c, const ocmc_params* p)
     CK(cudaSetDevice(c->device), "cudaSetDevice");
     bool phys = memcmp(&c->p, p, offsetof(ocmc_params, block_threads)) != 0;
     c->p = *p;
-    if (phys) c->tables_valid = false;
+    if (phys) c->tables_valid = c->mat_tables_valid = false;
     if (c->have_phantom && c->tally_B != p->n_batches) return ensure_tally(c);
     return OCMC_OK;
 }
@@ -359,7 +375,7 @@ ocmc_status ocmc_set_materials(ocmc_ctx* c, int n, const ocmc_material* defs)
     if (c->last_stream || c->ran) cudaDeviceSynchronize();
     c->mats = mats;
     c->have_phantom = false;       // the phantom's material indices refer to the old set
-    c->tables_valid = false;
+    c->tables_valid = c->mat_tables_valid = false;
     return OCMC_OK;
 }
 
@@ -418,6 +434,7 @@ ocmc_status ocmc_create_phantom(ocmc_ctx* c, int nx, int ny, int nz, const float
     c->dx = dx; c->dy = dy; c->dz = dz;
     CK(cudaMemcpy(c->d_density, density, n * sizeof(float), cudaMemcpyHostToDevice), "phantom upload");
     CK(cudaMemcpy(c->d_material, material, n, cudaMemcpyHostToDevice), "phantom upload");
+    if (!same_defs(staged, c->staged)) c->mat_tables_valid = false;   // else only the phantom part is rebuilt
     c->staged = staged;
     c->slot_of = slot;
     c->t.n_mat = (int)staged.size();

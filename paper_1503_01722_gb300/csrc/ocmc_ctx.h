@@ -34,7 +34,8 @@ struct ocmc_ctx {
     std::vector<int> slot_of;                // defined index -> staged slot, -1 if not staged
     // tables
     ocmc::Tables t{};
-    bool tables_valid = false;
+    bool tables_valid = false;               // material and phantom parts both current
+    bool mat_tables_valid = false;           // material part current (kept across phantoms of the same staged set)
     // tally and its history counts per batch
     long long* d_tally = nullptr;
     int tally_B = 0;

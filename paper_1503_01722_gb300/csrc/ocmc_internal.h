@@ -176,6 +176,9 @@ struct TransportArgs {
 // kernels / launchers (defined in the .cu files)
 cudaError_t build_tables(const Tables& t, const PhysParams& pp, const float* density, const uint8_t* material,
                          long long nvox, int* d_err, const MatDef* defs, cudaStream_t s);
+cudaError_t build_material_tables(const Tables& t, const PhysParams& pp, const MatDef* defs, cudaStream_t s);
+cudaError_t build_phantom_tables(const Tables& t, const float* density, const uint8_t* material, long long nvox,
+                                 int* d_err, cudaStream_t s);
 cudaError_t launch_transport(const TransportArgs& a, int blocks, int threads, size_t smem, cudaStream_t s,
                              int nreg);
 size_t transport_smem_bytes(int n_mat);

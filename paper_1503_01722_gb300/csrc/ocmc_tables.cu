@@ -330,9 +330,9 @@ void material_defs(MatDef out[NMAT_DEFAULT])
     out[2] = lung;
 }
 
-// Tables for the t.n_mat staged materials defs[0 .. n_mat) (table row m = defs[m]).
-cudaError_t build_tables(const Tables& t, const PhysParams& pp, const float* density, const uint8_t* material,
-                         long long nvox, int* d_err, const MatDef* defs, cudaStream_t s)
+// Material tables for the t.n_mat staged materials defs[0 .. n_mat) (table row m = defs[m]):
+// they depend on the compositions and the physics parameters only, not on the phantom.
+cudaError_t build_material_tables(const Tables& t, const PhysParams& pp, const MatDef* defs, cudaStream_t s)
 {
     if (t.n_mat < 1 || t.n_mat > MAX_STAGED) return cudaErrorInvalidValue;
     cudaError_t e = cudaMemcpyAsync(t.mats, defs, sizeof(MatDef) * t.n_mat, cudaMemcpyHostToDevice, s);
@@ -341,10 +341,26 @@ cudaError_t build_tables(const Tables& t, const PhysParams& pp, const float* den
     k_range_scan<<<1, 32, 0, s>>>(t);
     k_range_inverse<<<(t.n_mat * NR + 127) / 128, 128, 0, s>>>(t, pp);
     k_ms_table<<<(NG + 127) / 128, 128, 0, s>>>(t);
-    cudaMemsetAsync(t.rho_max, 0, t.n_mat * sizeof(unsigned int), s);
+    return cudaGetLastError();
+}
+
+// Phantom-dependent part: per-material maximum density (with the phantom's validity check) and
+// the photon majorant built from it.
+cudaError_t build_phantom_tables(const Tables& t, const float* density, const uint8_t* material, long long nvox,
+                                 int* d_err, cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(t.rho_max, 0, t.n_mat * sizeof(unsigned int), s);
+    if (e != cudaSuccess) return e;
     k_phantom_scan<<<1024, 256, 0, s>>>(density, material, nvox, t.n_mat, t.rho_max, d_err);
     k_photon_majorant<<<(NE + 127) / 128, 128, 0, s>>>(t);
     return cudaGetLastError();
+}
+
+cudaError_t build_tables(const Tables& t, const PhysParams& pp, const float* density, const uint8_t* material,
+                         long long nvox, int* d_err, const MatDef* defs, cudaStream_t s)
+{
+    cudaError_t e = build_material_tables(t, pp, defs, s);
+    return e != cudaSuccess ? e : build_phantom_tables(t, density, material, nvox, d_err, s);
 }
 
 }  // namespace ocmc
