@@ -247,6 +247,39 @@ def test_full_size_workload(ocmc):
     assert abs(e_gpu - e_orc) < 4 * sd + 1e-3 * e_orc, (e_gpu, e_orc, sd)
 
 
+def test_tables_kept_across_phantoms(ocmc):
+    """A second phantom on the same engine (same materials, other densities, other size) reuses
+    the material tables and rebuilds only its own majorant: the tally equals a fresh engine's;
+    new physics parameters rebuild everything."""
+    ph1 = I.scaled(I.half_slab(), 4)
+    ph2 = I.random_phantom()
+    beam = lambda ph: I.beam_on(ph, 0, I.spectrum_6mv(), (6, 6), 100.0)
+    with ocmc.Engine(0) as e:
+        e.create_phantom(ph1)
+        e.set_source(beam(ph1))
+        e.run(20_000, seed=4)
+        e.create_phantom(ph2)
+        e.set_source(beam(ph2))
+        e.run(20_000, seed=4)
+        reused = e.raw_tally()
+        e.set_params(e_abs_e=0.3, w_cc=0.3)
+        e.reset()
+        e.run(20_000, seed=4)
+        changed = e.raw_tally()
+    with ocmc.Engine(0) as e:
+        e.create_phantom(ph2)
+        e.set_source(beam(ph2))
+        e.run(20_000, seed=4)
+        fresh = e.raw_tally()
+    with ocmc.Engine(0, e_abs_e=0.3, w_cc=0.3) as e:
+        e.create_phantom(ph2)
+        e.set_source(beam(ph2))
+        e.run(20_000, seed=4)
+        fresh_changed = e.raw_tally()
+    assert np.array_equal(reused, fresh) and fresh.sum() > 0
+    assert np.array_equal(changed, fresh_changed) and not np.array_equal(changed, fresh)
+
+
 def test_emergency_switch_prevents_overflow(ocmc):
     """Small stacks with a switch threshold just below their capacity: a warp switches type
     when the other stack nears its capacity, so nothing overflows and the tally equals the
