@@ -289,11 +289,12 @@ def run_denoiser_bench(args, desc):
     study = None
     weights = None
     if not args.no_study:
-        wpath = os.path.join(ROOT, "gpurun_out", "denoiser_bench_weights.npy") if os.path.isdir(
-            os.path.join(ROOT, "gpurun_out")) else None
+        # the trained weights also serve the inference timing below (and are kept if asked)
+        import tempfile
+        wpath = args.weights_out or os.path.join(tempfile.mkdtemp(prefix="ocmc_denoiser_"), "weights.npy")
         study = D.run_study(n_train=args.study_train, steps=args.study_steps, log=lambda m: print(m, file=sys.stderr),
                             weights_out=wpath)
-        weights = np.load(wpath) if wpath else None
+        weights = np.load(wpath)
     ph, beam = I.denoiser_case(424242)
     eng = ocmc.Engine(0)
     eng.create_phantom(ph)
@@ -436,6 +437,7 @@ def main():
     ap.add_argument("--beamlet-scale", type=float, default=1.0, help="beamlets_ct: scale every beamlet's histories")
     ap.add_argument("--study-train", type=int, default=200, help="denoiser_128: training cases")
     ap.add_argument("--study-steps", type=int, default=12000, help="denoiser_128: training steps")
+    ap.add_argument("--weights-out", default=None, help="denoiser_128: keep the trained weights (.npy) here")
     ap.add_argument("--e-class-split", type=float, default=None,
                     help="energy-class boundary (MeV) of the charged stacks; default: the engine's")
     args = ap.parse_args()

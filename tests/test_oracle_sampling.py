@@ -2,8 +2,8 @@
 
 Bin probabilities come from quadrature of the textbook differential cross
 sections (written out here), not from the oracle. Seeds are fixed, so the
-statistics are deterministic; the bound p > 0.01 follows the north-star
-requirement for the Klein-Nishina test and is reused for the other samplers.
+statistics are deterministic; the bound p > 0.01 is the acceptance level
+required of the Klein-Nishina test and is reused for the other samplers.
 """
 import math
 
