@@ -69,10 +69,11 @@ typedef struct {
     int32_t block_threads;  /* threads per block of the transport kernel           */
     int32_t blocks_per_sm;  /* resident transport blocks per SM                    */
     int32_t stack_capacity; /* per-warp capacity of each secondary stack (8192)   */
-    int32_t switch_high;    /* other-type stack size that makes a warp switch type */
+    int32_t switch_high;    /* size of another stack that makes a warp move to it  */
                             /* (15/16 of the capacity); at or above the capacity   */
                             /* it disables switching on stack size                 */
-    int32_t switch_low;     /* active lanes at or below which a warp switches type */
+    int32_t switch_low;     /* active lanes at or below which a warp whose own     */
+                            /* stack and source are empty moves to another stack   */
     uint32_t stream_tag;    /* XORed into the high word of every history's random  */
                             /* stream (0); 0x80000000|b reproduces beamlet b       */
     float beamlet_capacity_scale; /* scales the pilot estimate of beamlet table    */

@@ -12,12 +12,14 @@
 // Scheduling (Sec. 2.2.1, Table 1): the paper launches batches of up to M
 // particles of one type, taken from the photon stack, the electron stack or
 // the source. Here every warp runs that loop by itself inside one persistent
-// launch: its 32 lanes always hold particles of one type (warp mode); free
-// lanes refill from the warp's own stack of that type, then from the source
-// (energy-sorted history ids from a global counter); the warp switches type
-// when its lanes run dry or the other stack grows large. Secondaries are
-// pushed to the warp's stacks. A warp ends when the source is exhausted and
-// its stacks are empty; no warp ever waits on another.
+// launch: its 32 lanes always hold particles of one kind (warp mode: photons,
+// or charged particles, which wait on two stacks split by energy class); once
+// enough lanes are free they refill from the warp's own stack of that kind,
+// then from the source (energy-sorted history ids from a global counter); the
+// warp moves to the fullest other stack when its lanes run dry or that stack
+// grows large. Secondaries are pushed to the warp's stacks. A warp ends when
+// the source is exhausted and its stacks are empty; no warp ever waits on
+// another.
 //
 // Dose tally (Sec. 2.2.2): 64-bit fixed-point integer atomics (2^-28 MeV
 // units) into the tally of batch (history id mod B). Integer addition is
@@ -439,7 +441,7 @@ __global__ void __maxnreg__(NREG) k_transport(const __grid_constant__ TransportA
     int mode = src_mode;
     bool src_done = a.count == 0;
     // with switch_high >= cap, switching on stack size is off (stacks may then overflow, which
-    // is reported); otherwise a warp also switches when the other stack nears its capacity
+    // is reported); otherwise a warp also switches when another stack nears its capacity
     const int emergency = a.switch_high < a.cap ? a.cap - 128 : 0x7FFFFFFF;
     bool active = false, just_switched = false;
     Lane p;
