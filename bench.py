@@ -31,12 +31,12 @@ import ocmc_inputs as I  # noqa: E402
 # smsp__thread_inst_executed.sum divided by the kernel's own lane-step counter)
 # and DRAM bytes per history, from the ncu capture summarised in
 # profiles/k_transport_photon_slab_120.md (re-measured whenever the kernel changes).
-INST_PER_LANE_STEP = 715.2
+INST_PER_LANE_STEP = 700.1
 # DRAM bytes of one transport launch measured by ncu on the full default workload
-DRAM_BYTES_PER_LAUNCH = {("photon_slab_120", 100_000_000): 21.167e9}
+DRAM_BYTES_PER_LAUNCH = {("photon_slab_120", 100_000_000): 20.983e9}
 # the same for the beamlet-mode kernel (hash tallies) on the 512-beamlet CT workload, measured by
 # ncu on the same workload with every beamlet's histories scaled by 0.02
-INST_PER_LANE_STEP_BEAMLETS = 751.7
+INST_PER_LANE_STEP_BEAMLETS = 742.9
 
 WORKLOADS = {
     "photon_slab_120": (I.photon_slab_120, 100_000_000,

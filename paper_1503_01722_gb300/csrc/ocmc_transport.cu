@@ -94,7 +94,7 @@ template <class C>
 __device__ __forceinline__ void deposit(C& c, const Lane& p, int ix, int iy, int iz, float dE)
 {
     if (dE > 0.f) {
-        long long v = ix + (long long)c.a.nx * (iy + (long long)c.a.ny * iz);
+        const int v = ix + c.a.nx * (iy + c.a.ny * iz);     // grids have at most 1024^3 voxels
         if constexpr (C::beamlets) hash_add(c.a, p.r.h1 & ~BL_TAG, (uint32_t)v, fx(dE));
         else atomicAdd(c.a.tally + (long long)p.batch * c.a.nvox + v, fx(dE));
     }
@@ -235,7 +235,7 @@ __device__ __forceinline__ bool photon_step(C& c, Lane& p, unsigned& n_fict)
     p.ix = min((int)(p.x * c.inv_dx), a.nx - 1);
     p.iy = min((int)(p.y * c.inv_dy), a.ny - 1);
     p.iz = min((int)(p.z * c.inv_dz), a.nz - 1);
-    long long vox = p.ix + (long long)a.nx * (p.iy + (long long)a.ny * p.iz);
+    const int vox = p.ix + a.nx * (p.iy + a.ny * p.iz);
     float rho = __ldg(a.density + vox);
     int m = __ldg(a.material + vox);
     float4 pa = T.ph[m * MS4 + ei.i], pb = T.ph[m * MS4 + ei.i + 1];
@@ -336,7 +336,7 @@ __device__ __forceinline__ bool charged_step(C& c, Lane& p, unsigned& n_hfict)
     const TransportArgs& a = c.a;
     const SmemTables& T = c.T;
     const uint32_t k0 = a.key0, k1 = a.key1;
-    long long vox = p.ix + (long long)a.nx * (p.iy + (long long)a.ny * p.iz);
+    const int vox = p.ix + a.nx * (p.iy + a.ny * p.iz);
     float rho = __ldg(a.density + vox);
     int m = __ldg(a.material + vox);
     int face;
