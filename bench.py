@@ -167,7 +167,7 @@ def run_reference(args, ph, beam, desc):
     t = time.perf_counter()
     O.run(ph, beam, pilot, seed=1, threads=threads)
     rate = pilot / (time.perf_counter() - t)
-    budget = 150.0 / max(1, args.steps + args.warmup)
+    budget = args.ref_seconds / max(1, args.steps + args.warmup)
     n = int(min(max(rate * budget, pilot), 5_000_000))
     for _ in range(args.warmup):
         O.run(ph, beam, n, seed=1, threads=threads)
@@ -438,6 +438,8 @@ def main():
     ap.add_argument("--study-train", type=int, default=200, help="denoiser_128: training cases")
     ap.add_argument("--study-steps", type=int, default=12000, help="denoiser_128: training steps")
     ap.add_argument("--weights-out", default=None, help="denoiser_128: keep the trained weights (.npy) here")
+    ap.add_argument("--ref-seconds", type=float, default=150.0,
+                    help="--impl reference: CPU seconds the oracle's timed and warm-up steps may take together")
     ap.add_argument("--e-class-split", type=float, default=None,
                     help="energy-class boundary (MeV) of the charged stacks; default: the engine's")
     args = ap.parse_args()
