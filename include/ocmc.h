@@ -354,6 +354,13 @@ ocmc_status ocmc_test_philox(int device, uint32_t key0, uint32_t key1, uint32_t 
                              uint32_t c3, uint32_t first_block, uint32_t n_blocks,
                              uint32_t* out_host);
 
+/* The transport kernel's rotation of a direction (Sec. 2.1: new directions after Compton,
+ * Moller and bremsstrahlung events and multiple scattering): for j in [0, n), the unit vector
+ * dir_host[3j..3j+2] turned by polar cosine mu_host[j] and azimuth 2 pi xi_host[j] about
+ * itself, written to out_host[3j..3j+2]. Host arrays; OCMC_ERR_ARG on NULL or n <= 0. */
+ocmc_status ocmc_test_rotate(int device, const float* dir_host, const float* mu_host,
+                             const float* xi_host, int n, float* out_host);
+
 /* Source particles of histories [first, first+count) of a run of n_total:
  * out_host[8j..8j+7] = x, y, z, u, v, w, E, entered (1/0). */
 ocmc_status ocmc_test_source(ocmc_ctx* ctx, uint64_t n_total, uint64_t first, uint64_t count,
@@ -401,13 +408,16 @@ ocmc_status ocmc_test_csda(ocmc_ctx* ctx, int material, const float* T_host, con
  * with that device current and caches it: make it before any stream capture.
  *
  * density_dev, material_dev: device arrays as in ocmc_create_phantom, with the built-in
- * materials 0 water, 1 cortical bone, 2 lung (values are checked on the device; bad values
- * give OCMC_ERR_ARG). Source arguments as in
- * ocmc_set_source (host arrays). params: NULL for defaults; a launch shape
- * (block_threads, blocks_per_sm, stack_capacity) whose stacks do not fit in the
- * static array is rejected with OCMC_ERR_ARG. Runs on cuda_stream and
- * synchronises it before returning. err_msg (host, may be NULL) receives a message
- * of at most err_len bytes on failure. */
+ * materials 0 water, 1 cortical bone, 2 lung (values are checked on the device after the
+ * table build and before any transport; bad values give OCMC_ERR_ARG and leave the tally
+ * untouched). Source arguments as in ocmc_set_source (host arrays). params: NULL for
+ * defaults (256-record stacks, 256-thread blocks; the type-switch threshold defaults to
+ * capacity - capacity/16 as in ocmc_run_range); a launch shape (block_threads,
+ * blocks_per_sm, stack_capacity) whose stacks do not fit in the static array is rejected
+ * with OCMC_ERR_ARG. Runs on cuda_stream and waits for it twice before returning (after the
+ * table build and after the transport, to read the error flag). The caller's current device
+ * is restored on return. err_msg (host, may be NULL) receives a message of at most err_len
+ * bytes on failure. */
 #define OCMC_NOALLOC_SCRATCH_BYTES (64ull * 1024ull * 1024ull)
 ocmc_status ocmc_run_noalloc(int device, int nx, int ny, int nz, const float* density_dev,
                              const uint8_t* material_dev, float dx, float dy, float dz, int particle,

@@ -101,6 +101,8 @@ def lib():
                 ("orc_csda_loss", d, [i, d, d, C.POINTER(Params)]),
                 ("orc_philox", None, [C.POINTER(C.c_uint32), C.POINTER(C.c_uint32), C.POINTER(C.c_uint32)]),
                 ("orc_sample", i, [i, i, d, d, u64, u64, C.POINTER(Params), C.POINTER(d)]),
+                ("orc_event", i, [i, i, d, d, C.POINTER(d), u64, u64, C.POINTER(Params), C.POINTER(d)]),
+                ("orc_rotate", None, [C.POINTER(d), d, d, C.POINTER(d)]),
                 ("orc_stratify", i, [i, C.POINTER(C.c_float), C.POINTER(C.c_float), u64,
                                      C.POINTER(u64), C.POINTER(C.c_int32)]),
                 ("orc_source_sample", i, [C.POINTER(_Phantom), C.POINTER(_Source), u64, u64, u64, u64,
@@ -196,6 +198,37 @@ def philox(ctr, key):
 
 
 SAMPLE_KN_MU, SAMPLE_MOLLER_EPS, SAMPLE_BREMS_K, SAMPLE_MS_MU = 0, 1, 2, 3
+
+
+EVENT_KINDS = {"compton": 0, "moller": 1, "brems": 2, "annihilation": 3, "rotation": 4}
+
+
+def event(kind, E, d0, n, seed=1, m=0, aux=0.0, p=None):
+    """n single interactions of one kind from unit direction d0 (see orc_event). Returns
+    (Ea, da, Eb, db): energies (n,) and unit directions (n, 3) of the two outgoing particles."""
+    p = params() if p is None else p
+    out = np.zeros((n, 8), np.float64)
+    d = np.ascontiguousarray(np.asarray(d0, np.float64).reshape(3))
+    rc = lib().orc_event(EVENT_KINDS[kind], m, float(E), float(aux), _ptr(d, C.c_double), n, seed,
+                         C.byref(p), _ptr(out, C.c_double))
+    if rc != 0:
+        raise ValueError("orc_event failed")
+    return out[:, 0], out[:, 1:4], out[:, 4], out[:, 5:8]
+
+
+def rotate(dirs, mu, phi):
+    """Rows of dirs turned by polar cosine mu and azimuth phi (the rotation every event uses)."""
+    dirs = np.asarray(dirs, np.float64).reshape(-1, 3)
+    mu = np.broadcast_to(np.asarray(mu, np.float64), (len(dirs),))
+    phi = np.broadcast_to(np.asarray(phi, np.float64), (len(dirs),))
+    out = np.empty_like(dirs)
+    L = lib()
+    o = np.empty(3, np.float64)
+    for j in range(len(dirs)):
+        dj = np.ascontiguousarray(dirs[j])
+        L.orc_rotate(_ptr(dj, C.c_double), float(mu[j]), float(phi[j]), _ptr(o, C.c_double))
+        out[j] = o
+    return out
 
 
 def sample(kind, E, n, seed=1, m=0, aux=0.0, p=None):

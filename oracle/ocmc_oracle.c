@@ -461,7 +461,7 @@ static void normalize3(double* a)
 static void rotate(double* d, double mu, double phi)
 {
     double st = sqrt(fmax(0.0, 1.0 - mu * mu)), cp = cos(phi), sp = sin(phi);
-    double u = d[0], v = d[1], w = d[2], s = sqrt(fmax(0.0, 1.0 - w * w));
+    double u = d[0], v = d[1], w = d[2], s = sqrt(u * u + v * v);   /* not sqrt(1 - w^2): no cancellation near the poles */
     if (s > 1e-10) {
         d[0] = u * mu + st * (u * w * cp - v * sp) / s;
         d[1] = v * mu + st * (v * w * cp + u * sp) / s;
@@ -471,6 +471,66 @@ static void rotate(double* d, double mu, double phi)
         d[0] = st * cp; d[1] = st * sp; d[2] = sg * mu;
     }
     normalize3(d);
+}
+
+/* ---- event kinematics (Sec. 2.1) ------------------------------------------ */
+/* Each function draws its random numbers from the particle's stream in a fixed order and
+   returns the outgoing energies and unit directions; d0 is the incoming unit direction. */
+
+/* Compton scattering of a photon of energy E0: polar cosine mu from Klein-Nishina, uniform
+   azimuth; the scattered photon energy follows from mu, and the recoil electron carries the
+   kinetic energy T = E0 - E1 along the momentum balance E0 d0 - E1 d1 (units MeV/c). */
+static void compton_event(double E0, const double* d0, stream* rs,
+                          double* E1, double* d1, double* T, double* de)
+{
+    double mu = sample_kn_mu(E0, rs), phi = 2.0 * PI * rnd(rs);
+    *E1 = E0 / (1.0 + E0 / MC2 * (1.0 - mu));
+    *T = E0 - *E1;
+    d1[0] = d0[0]; d1[1] = d0[1]; d1[2] = d0[2];
+    rotate(d1, mu, phi);
+    de[0] = E0 * d0[0] - *E1 * d1[0];
+    de[1] = E0 * d0[1] - *E1 * d1[1];
+    de[2] = E0 * d0[2] - *E1 * d1[2];
+    if (*T > 0.0) normalize3(de);
+}
+
+/* Moller event of an electron of kinetic energy T0 above the threshold w_cc: energy fraction
+   eps of the knock-on electron, uniform azimuth; both polar cosines follow from energy and
+   momentum conservation for a free electron at rest, and the two outgoing electrons lie in one
+   plane with the incoming direction, on opposite sides of it. */
+static void moller_event(double T0, double w_cc, const double* d0, stream* rs,
+                         double* T1, double* d1, double* W, double* d2)
+{
+    double eps = sample_moller_eps(T0, w_cc, rs), phi = 2.0 * PI * rnd(rs);
+    *W = eps * T0;
+    *T1 = T0 - *W;
+    double mu1 = sqrt(fmin(1.0, *T1 * (T0 + 2.0 * MC2) / (T0 * (*T1 + 2.0 * MC2))));
+    double mu2 = sqrt(fmin(1.0, *W * (T0 + 2.0 * MC2) / (T0 * (*W + 2.0 * MC2))));
+    d2[0] = d0[0]; d2[1] = d0[1]; d2[2] = d0[2];
+    rotate(d2, mu2, phi + PI);
+    d1[0] = d0[0]; d1[1] = d0[1]; d1[2] = d0[2];
+    rotate(d1, mu1, phi);
+}
+
+/* Bremsstrahlung event of an electron of kinetic energy T0 in material m: photon energy k
+   on [w_cb, T0]; the photon leaves at the fixed polar angle mc^2 / (T0 + mc^2) with uniform
+   azimuth, and the electron keeps its direction. */
+static void brems_event(int m, double T0, double w_cb, const double* d0, stream* rs,
+                        double* k, double* dg)
+{
+    *k = sample_brems_k(m, T0, w_cb, rs);
+    double th = MC2 / (T0 + MC2), phi = 2.0 * PI * rnd(rs);
+    dg[0] = d0[0]; dg[1] = d0[1]; dg[2] = d0[2];
+    rotate(dg, cos(th), phi);
+}
+
+/* Annihilation of a positron at rest: two photons of mc^2 back to back, the first one's
+   direction isotropic (uniform polar cosine and azimuth). */
+static void annihilation_event(stream* rs, double* d1, double* d2)
+{
+    double w = 2.0 * rnd(rs) - 1.0, phi = 2.0 * PI * rnd(rs), st = sqrt(fmax(0.0, 1.0 - w * w));
+    d1[0] = st * cos(phi); d1[1] = st * sin(phi); d1[2] = w;
+    d2[0] = -d1[0]; d2[1] = -d1[1]; d2[2] = -d1[2];
 }
 
 /* ---- transport ----------------------------------------------------------- */
@@ -572,8 +632,8 @@ static particle make_child(const particle* parent, uint32_t slot, int type, doub
 /* Positron at rest: two photons of mc^2, back to back, isotropic. */
 static void annihilate(run_ctx* c, particle* q)
 {
-    double w = 2.0 * rnd(&q->rs) - 1.0, phi = 2.0 * PI * rnd(&q->rs), st = sqrt(fmax(0.0, 1.0 - w * w));
-    double d1[3] = { st * cos(phi), st * sin(phi), w }, d2[3] = { -d1[0], -d1[1], -d1[2] };
+    double d1[3], d2[3];
+    annihilation_event(&q->rs, d1, d2);
     c->cnt[ORC_C_ANNIH]++;
     c->ledger[ORC_L_ANNIHMASS] += 2.0 * MC2;
     if (MC2 >= c->p->e_abs_g) {
@@ -630,13 +690,10 @@ static void transport_photon(run_ctx* c, particle* q)
         double x = rnd(&q->rs) * (muC + muP + muQ);
         if (x < muC) {
             c->cnt[ORC_C_COMPTON]++;
-            double mu = sample_kn_mu(q->E, &q->rs), phi = 2.0 * PI * rnd(&q->rs);
-            double E0 = q->E, E1 = E0 / (1.0 + E0 / MC2 * (1.0 - mu)), T = E0 - E1;
-            double d0[3] = { q->d[0], q->d[1], q->d[2] };
-            rotate(q->d, mu, phi);
-            double pe[3] = { E0 * d0[0] - E1 * q->d[0], E0 * d0[1] - E1 * q->d[1], E0 * d0[2] - E1 * q->d[2] };
+            double E1, T, d1[3], pe[3];
+            compton_event(q->E, q->d, &q->rs, &E1, d1, &T, pe);
+            q->d[0] = d1[0]; q->d[1] = d1[1]; q->d[2] = d1[2];
             if (T > 0.0) {
-                normalize3(pe);
                 particle e = make_child(q, 0, ELECTRON, T, pe);
                 emit_charged(c, &e);
             }
@@ -727,22 +784,16 @@ static void transport_charged(run_ctx* c, particle* q)
             if (rnd(&q->rs) * sig_hat < tot) {
                 if (rnd(&q->rs) * tot < sM) {
                     c->cnt[ORC_C_MOLLER]++;
-                    double T0 = q->E, eps = sample_moller_eps(T0, p->w_cc, &q->rs), W = eps * T0, T1 = T0 - W;
-                    double phi = 2.0 * PI * rnd(&q->rs);
-                    double mu1 = sqrt(fmin(1.0, T1 * (T0 + 2.0 * MC2) / (T0 * (T1 + 2.0 * MC2))));
-                    double mu2 = sqrt(fmin(1.0, W * (T0 + 2.0 * MC2) / (T0 * (W + 2.0 * MC2))));
-                    double d2[3] = { q->d[0], q->d[1], q->d[2] };
-                    rotate(d2, mu2, phi + PI);
+                    double T1, W, d1[3], d2[3];
+                    moller_event(q->E, p->w_cc, q->d, &q->rs, &T1, d1, &W, d2);
                     particle e = make_child(q, 2, ELECTRON, W, d2);
-                    rotate(q->d, mu1, phi);
+                    q->d[0] = d1[0]; q->d[1] = d1[1]; q->d[2] = d1[2];
                     q->E = T1;
                     emit_charged(c, &e);
                 } else {
                     c->cnt[ORC_C_BREMS]++;
-                    double T0 = q->E, k = sample_brems_k(m, T0, p->w_cb, &q->rs);
-                    double th = MC2 / (T0 + MC2), phi = 2.0 * PI * rnd(&q->rs);
-                    double dg[3] = { q->d[0], q->d[1], q->d[2] };
-                    rotate(dg, cos(th), phi);
+                    double T0 = q->E, k, dg[3];
+                    brems_event(m, T0, p->w_cb, q->d, &q->rs, &k, dg);
                     particle g = make_child(q, 3, PHOTON, k, dg);
                     q->E = T0 - k;
                     if (k >= p->e_abs_g) push(c, &g); else deposit(c, q->i, k);
@@ -1036,4 +1087,46 @@ int orc_sample(int kind, int m, double E, double aux, uint64_t n, uint64_t seed,
         }
     }
     return 0;
+}
+
+/* ---- event kinematics access for conservation and angle tests ------------- */
+/* n events of one kind from the incoming unit direction d0 (normalised here), each on its own
+   random stream. out holds 8 doubles per event: energy and unit direction of the first and of
+   the second outgoing particle --
+     kind 0 Compton:      scattered photon (E1, d1), recoil electron (T, de);  E = photon energy
+     kind 1 Moller:       primary electron (T1, d1), knock-on electron (W, d2); E = kinetic energy
+     kind 2 brems:        electron (E - k, unchanged direction), photon (k, dg); E = kinetic energy
+     kind 3 annihilation: two photons (mc^2, d1), (mc^2, d2)
+     kind 4 rotation:     (aux, d0 rotated by polar cosine aux), (azimuth, d0) */
+int orc_event(int kind, int m, double E, double aux, const double* d_in, uint64_t n, uint64_t seed,
+              const orc_params* p, double* out)
+{
+    double d0[3] = { d_in[0], d_in[1], d_in[2] };
+    double nn = sqrt(d0[0] * d0[0] + d0[1] * d0[1] + d0[2] * d0[2]);
+    if (!(nn > 0.0) || kind < 0 || kind > 4) return -1;
+    d0[0] /= nn; d0[1] /= nn; d0[2] /= nn;
+    for (uint64_t j = 0; j < n; ++j) {
+        stream s = { { (uint32_t)seed, (uint32_t)(seed >> 32) }, j, 0xE7E7u + (uint32_t)kind, 0 };
+        double* o = out + 8 * j;
+        double a = 0.0, b = 0.0, da[3] = { d0[0], d0[1], d0[2] }, db[3] = { d0[0], d0[1], d0[2] };
+        switch (kind) {
+        case 0: compton_event(E, d0, &s, &a, da, &b, db); break;
+        case 1: moller_event(E, p->w_cc, d0, &s, &a, da, &b, db); break;
+        case 2: brems_event(m, E, p->w_cb, d0, &s, &b, db); a = E - b; break;
+        case 3: annihilation_event(&s, da, db); a = b = MC2; break;
+        case 4: b = 2.0 * PI * rnd(&s); a = aux; rotate(da, aux, b); break;
+        }
+        o[0] = a; o[1] = da[0]; o[2] = da[1]; o[3] = da[2];
+        o[4] = b; o[5] = db[0]; o[6] = db[1]; o[7] = db[2];
+    }
+    return 0;
+}
+
+/* The rotation itself, for direction-by-direction comparisons: d (normalised here) turned by
+   polar cosine mu and azimuth phi. */
+void orc_rotate(const double* d, double mu, double phi, double* out)
+{
+    double nn = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+    out[0] = d[0] / nn; out[1] = d[1] / nn; out[2] = d[2] / nn;
+    rotate(out, mu, phi);
 }

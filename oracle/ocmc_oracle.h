@@ -123,6 +123,11 @@ double orc_csda_loss(int m, double T, double mass_thickness, const orc_params* p
 void   orc_philox(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
 int    orc_sample(int kind, int m, double E, double aux, uint64_t n, uint64_t seed,
                   const orc_params* p, double* out);
+/* One interaction's outgoing energies and directions (tests of the kinematics; layout in the
+   source file): kind 0 Compton, 1 Moller, 2 bremsstrahlung, 3 annihilation, 4 rotation. */
+int    orc_event(int kind, int m, double E, double aux, const double* d0, uint64_t n, uint64_t seed,
+                 const orc_params* p, double* out);
+void   orc_rotate(const double* d, double mu, double phi, double* out);
 int    orc_stratify(int n_bins, const float* edges, const float* weights,
                     uint64_t n_total, uint64_t* bounds, int32_t* order);
 int    orc_source_sample(const orc_phantom* ph, const orc_source* src, uint64_t seed,

@@ -794,6 +794,24 @@ ocmc_status ocmc_test_philox(int device, uint32_t key0, uint32_t key1, uint32_t 
     return OCMC_OK;
 }
 
+ocmc_status ocmc_test_rotate(int device, const float* dir, const float* mu, const float* xi, int n, float* out)
+{
+    ocmc_ctx* c = nullptr;
+    if (!dir || !mu || !xi || !out || n <= 0) return fail(nullptr, OCMC_ERR_ARG, "bad arguments");
+    CK(cudaSetDevice(device), "cudaSetDevice");
+    float* d = nullptr;
+    const size_t nb = sizeof(float) * (size_t)n;
+    CK(cudaMalloc(&d, 8 * nb), "allocation");   // dir (3n), mu (n), xi (n), out (3n)
+    cudaError_t e = cudaMemcpy(d, dir, 3 * nb, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(d + 3 * (size_t)n, mu, nb, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(d + 4 * (size_t)n, xi, nb, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = launch_test_rotate(d, d + 3 * (size_t)n, d + 4 * (size_t)n, n, d + 5 * (size_t)n, nullptr);
+    if (e == cudaSuccess) e = cudaMemcpy(out, d + 5 * (size_t)n, 3 * nb, cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "rotation test");
+    return OCMC_OK;
+}
+
 ocmc_status ocmc_test_source(ocmc_ctx* c, uint64_t n_total, uint64_t first, uint64_t count, uint64_t seed, float* out)
 {
     if (!c || !out || count == 0 || first + count > n_total) return fail(c, OCMC_ERR_ARG, "bad arguments");

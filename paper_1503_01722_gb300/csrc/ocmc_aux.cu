@@ -54,6 +54,17 @@ __global__ void k_test_philox(uint32_t k0, uint32_t k1, uint32_t c1, uint32_t c2
     out[4 * j + 3] = r.w;
 }
 
+__global__ void k_test_rotate(const float* dir, const float* mu, const float* xi, int n, float* out)
+{
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    float u = dir[3 * j], v = dir[3 * j + 1], w = dir[3 * j + 2];
+    rotate(u, v, w, mu[j], xi[j]);
+    out[3 * j] = u;
+    out[3 * j + 1] = v;
+    out[3 * j + 2] = w;
+}
+
 __global__ void k_test_source(const TransportArgs a, unsigned long long first, unsigned long long count, float* out)
 {
     unsigned long long j = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x;
@@ -306,6 +317,12 @@ cudaError_t launch_test_philox(uint32_t key0, uint32_t key1, uint32_t c1, uint32
                                uint32_t first_block, uint32_t n_blocks, uint32_t* out, cudaStream_t s)
 {
     k_test_philox<<<(n_blocks + 255) / 256, 256, 0, s>>>(key0, key1, c1, c2, c3, first_block, n_blocks, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_test_rotate(const float* dir, const float* mu, const float* xi, int n, float* out, cudaStream_t s)
+{
+    k_test_rotate<<<(n + 255) / 256, 256, 0, s>>>(dir, mu, xi, n, out);
     return cudaGetLastError();
 }
 

@@ -221,9 +221,11 @@ __device__ __forceinline__ void rotate(float& u, float& v, float& w, float mu, f
     float st = sqrtf(fmaxf(0.f, 1.f - mu * mu));
     float sp, cp;
     __sincosf(6.283185307179586f * xi, &sp, &cp);
-    float s = sqrtf(fmaxf(0.f, 1.f - w * w));
+    // sin of the polar angle of (u, v, w) from its own components: 1 - w^2 would cancel near
+    // the poles and give the frame a wrong scale there
+    float s = sqrtf(fmaf(u, u, v * v));
     float nu, nv, nw;
-    if (s > 1e-5f) {
+    if (s > 1e-10f) {
         float is = 1.f / s;
         nu = u * mu + st * (u * w * cp - v * sp) * is;
         nv = v * mu + st * (v * w * cp + u * sp) * is;

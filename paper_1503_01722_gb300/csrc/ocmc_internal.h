@@ -188,6 +188,7 @@ cudaError_t launch_finalize(const long long* tally, const float* density, int B,
                             const double* inv_nb, double inv_n, float* dose, float* sigma, cudaStream_t s);
 cudaError_t launch_test_philox(uint32_t key0, uint32_t key1, uint32_t c1, uint32_t c2, uint32_t c3,
                                uint32_t first_block, uint32_t n_blocks, uint32_t* out, cudaStream_t s);
+cudaError_t launch_test_rotate(const float* dir, const float* mu, const float* xi, int n, float* out, cudaStream_t s);
 cudaError_t launch_test_source(const TransportArgs& a, unsigned long long n_total, unsigned long long first,
                                unsigned long long count, float* out, cudaStream_t s);
 cudaError_t launch_test_sample(const TransportArgs& a, int kind, int m, float E, float aux, unsigned long long n,

@@ -16,7 +16,8 @@
 // different host threads) race on the array and give wrong results; serialise
 // them. The first call on a device looks up the array's device address (with
 // that device current) and caches it; make that first call before any stream
-// capture.
+// capture. Every call waits for its stream before it returns (it reads the
+// error flag back), and it leaves the caller's current device as it found it.
 #include "ocmc.h"
 #include "ocmc_internal.h"
 
@@ -83,6 +84,15 @@ struct Carver {
     }
 };
 
+// Puts the caller's current device back when the call returns.
+struct DeviceGuard {
+    int prev = -1;
+    ~DeviceGuard()
+    {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
 }  // namespace
 
 extern "C" ocmc_status ocmc_run_noalloc(int device, int nx, int ny, int nz, const float* density_dev,
@@ -133,7 +143,10 @@ extern "C" ocmc_status ocmc_run_noalloc(int device, int nx, int ny, int nz, cons
     double nd = std::sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
     if (!(nd > 1e-6) || !std::isfinite(nd)) return M.fail(OCMC_ERR_ARG, "dir must be a non-zero vector");
 
-    cudaError_t e = cudaSetDevice(device);
+    DeviceGuard guard;
+    cudaError_t e = cudaGetDevice(&guard.prev);
+    if (e != cudaSuccess) return M.cuda(e, "cudaGetDevice");
+    e = cudaSetDevice(device);
     if (e != cudaSuccess) return M.cuda(e, "cudaSetDevice");
     unsigned char* base = nullptr;
     e = scratch_address(device, &base);
@@ -164,7 +177,8 @@ extern "C" ocmc_status ocmc_run_noalloc(int device, int nx, int ny, int nz, cons
     int threads = p.block_threads ? p.block_threads : NOALLOC_THREADS;
     int cap = p.stack_capacity ? p.stack_capacity : NOALLOC_CAP;
     int sms = 0;
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+    if (e != cudaSuccess) return M.cuda(e, "device attribute");
     size_t smem = transport_smem_bytes(NMAT_DEFAULT);
     const int nreg = p.max_registers ? p.max_registers : 80;
     int bps = p.blocks_per_sm ? p.blocks_per_sm : transport_max_blocks_per_sm(threads, smem, nreg);
@@ -187,6 +201,14 @@ extern "C" ocmc_status ocmc_run_noalloc(int device, int nx, int ny, int nz, cons
     long long nvox = (long long)nx * ny * nz;
     e = build_tables(t, pp, density_dev, material_dev, nvox, err, defs, s);
     if (e != cudaSuccess) return M.cuda(e, "table build");
+    // The phantom lives on the device, so its values are checked there (by the table build's
+    // scan); the transport kernel indexes tables by material, so it must not start on a bad one.
+    int flag = 0;
+    e = cudaMemcpyAsync(&flag, err, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return M.cuda(e, "table build");
+    if (flag & ERR_PHANTOM)
+        return M.fail(OCMC_ERR_ARG, "phantom contains invalid values (material >= 3 or density outside [0, 30])");
 
     TransportArgs a;
     std::memset(&a, 0, sizeof(a));
@@ -207,7 +229,7 @@ extern "C" ocmc_status ocmc_run_noalloc(int device, int nx, int ny, int nz, cons
     a.cap = cap;
     a.nstk = nstk;
     a.e_split = p.e_class_split;
-    a.switch_high = p.switch_high ? p.switch_high : 256;
+    a.switch_high = p.switch_high ? p.switch_high : cap - cap / 16;   // below the capacity: switching stays on
     a.switch_low = p.switch_low ? p.switch_low : 8;
     a.refill_min = p.refill_min ? p.refill_min : 6;
     a.hist_counter = counter;
@@ -251,7 +273,6 @@ extern "C" ocmc_status ocmc_run_noalloc(int device, int nx, int ny, int nz, cons
 
     e = launch_transport(a, (int)blocks, threads, smem, s, nreg);
     if (e != cudaSuccess) return M.cuda(e, "transport launch");
-    int flag = 0;
     e = cudaMemcpyAsync(&flag, err, sizeof(int), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return M.cuda(e, "transport");

@@ -78,6 +78,7 @@ def _load():
         "ocmc_destroy": (None, [P]),
         "ocmc_test_philox": (C.c_int, [C.c_int, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32,
                                        C.c_uint32, C.c_uint32, P]),
+        "ocmc_test_rotate": (C.c_int, [C.c_int, P, P, P, C.c_int, P]),
         "ocmc_test_source": (C.c_int, [P, C.c_uint64, C.c_uint64, C.c_uint64, C.c_uint64, P]),
         "ocmc_test_sample": (C.c_int, [P, C.c_int, C.c_int, C.c_float, C.c_float, C.c_uint64, C.c_uint64, P]),
         "ocmc_test_tables": (C.c_int, [P, C.c_int, P, C.c_int, P]),
@@ -396,6 +397,22 @@ def test_philox(key, c1, c2, c3, first_block, n_blocks, device=0):
     return out
 
 
+def test_rotate(dirs, mu, xi, device=0):
+    """The transport kernel's rotation (ocmc_test_rotate): rows of `dirs` turned by polar cosine
+    `mu` and azimuth 2 pi `xi`."""
+    d = np.ascontiguousarray(dirs, np.float32).reshape(-1, 3)
+    m = np.ascontiguousarray(mu, np.float32).reshape(-1)
+    x = np.ascontiguousarray(xi, np.float32).reshape(-1)
+    if not (len(d) == len(m) == len(x)):
+        raise ValueError("dirs, mu and xi must have the same length")
+    out = np.empty_like(d)
+    st = lib.ocmc_test_rotate(device, C.c_void_p(d.ctypes.data), C.c_void_p(m.ctypes.data),
+                              C.c_void_p(x.ctypes.data), len(d), C.c_void_p(out.ctypes.data))
+    if st != OK:
+        raise OcmcError(st, lib.ocmc_last_error(None).decode())
+    return out
+
+
 SAMPLE_COMPTON, SAMPLE_MOLLER, SAMPLE_BREMS, SAMPLE_MS = 0, 1, 2, 3
 
 
@@ -406,15 +423,24 @@ def run_noalloc(density, material, voxel, beam, tally, first, count, n_total, se
     n_batches x nz x ny x nx, added into) are CUDA tensors the caller owns; every
     scratch buffer is the library's fixed static device array. Calls that overlap on
     the GPU share that array and must be serialised by the caller."""
-    pd, dd = _ptr(density)
-    pm, dm = _ptr(material)
-    pt, dt = _ptr(tally)
-    if not (dd and dm and dt):
-        raise ValueError("density, material and tally must be CUDA tensors")
+    import torch
+    p = params if params is not None else default_params()
+    for name, t, dtype in (("density", density, torch.float32), ("material", material, torch.uint8),
+                           ("tally", tally, torch.int64)):
+        if not isinstance(t, torch.Tensor) or not t.is_cuda or t.device.index != device:
+            raise ValueError(f"{name} must be a CUDA tensor on device {device}")
+        if t.dtype != dtype or not t.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous {dtype} tensor")
+    if density.dim() != 3 or tuple(material.shape) != tuple(density.shape):
+        raise ValueError("density and material must have the same shape (nz, ny, nx)")
     nz, ny, nx = density.shape
+    if tuple(tally.shape) != (int(p.n_batches), nz, ny, nx):
+        raise ValueError(f"tally must have shape (n_batches={int(p.n_batches)}, {nz}, {ny}, {nx})")
+    pd, _ = _ptr(density)
+    pm, _ = _ptr(material)
+    pt, _ = _ptr(tally)
     e = np.ascontiguousarray(beam.edges, np.float32)
     w = np.ascontiguousarray(beam.weights, np.float32)
-    p = params if params is not None else default_params()
     msg = C.create_string_buffer(256)
     st = lib.ocmc_run_noalloc(device, nx, ny, nz, pd, pm, *map(float, voxel), int(beam.particle), len(w),
                               C.c_void_p(e.ctypes.data), C.c_void_p(w.ctypes.data), float(beam.field[0]),

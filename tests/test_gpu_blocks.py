@@ -45,6 +45,24 @@ def test_philox_bit_exact(ocmc):
         assert np.array_equal(got, ref)
 
 
+def test_rotation_vs_oracle(ocmc):
+    """The kernel's FP32 rotation against the oracle's (pinned by momentum and angle tests),
+    direction by direction, including the poles and FP32 directions a hair away from them."""
+    rng = np.random.default_rng(17)
+    n = 20000
+    d = rng.normal(size=(n, 3))
+    d[:8] = [[0, 0, 1], [0, 0, -1], [1e-7, 0, 1], [0, -3e-6, -1], [2e-4, 1e-4, 1], [-1e-3, 0, -1],
+             [1, 0, 0], [0, 1, 1e-6]]
+    d = (d / np.linalg.norm(d, axis=1)[:, None]).astype(np.float32)
+    mu = rng.uniform(-1, 1, n).astype(np.float32)
+    mu[:4000:7] = 1.0 - rng.uniform(0, 1e-3, len(mu[:4000:7])).astype(np.float32)   # small deflections
+    xi = rng.uniform(0, 1, n).astype(np.float32)
+    got = ocmc.test_rotate(d, mu, xi).astype(np.float64)
+    ref = O.rotate(d.astype(np.float64), mu.astype(np.float64), 2 * math.pi * xi.astype(np.float64))
+    assert np.max(np.abs(np.linalg.norm(got, axis=1) - 1)) < 1e-6
+    assert np.max(np.abs(got - ref)) < 2e-5
+
+
 @pytest.mark.parametrize("case", ["photon_point", "electron_parallel", "oblique_miss"])
 def test_source_elementwise(ocmc, case):
     if case == "photon_point":
