@@ -67,9 +67,9 @@ WORKLOADS = {
                      "(6 MV or 6-20 MeV e-, fields 2-20 cm); time to <=1% mean dose error above the 10% isodose, "
                      "plain vs denoised, on held-out cases"),
     "voxel_sweep": (None, 0,
-                    "voxel-size dependence of voxel-limited electron stepping: slab phantom 30x30x30 cm (water 0-3, "
-                    "bone 3-5, lung 5-12, water) at 1-5 mm voxels, 15 MeV electrons (1e7) and 6 MV photons (1e8), "
-                    "10x10 cm2 at SSD 100"),
+                    "voxel-size dependence of voxel-limited and voxel-crossing electron stepping: slab phantom "
+                    "30x30x30 cm (water 0-3, bone 3-5, lung 5-12, water) at 1-5 mm voxels, 15 MeV electrons (1e7) "
+                    "and 6 MV photons (1e8), 10x10 cm2 at SSD 100"),
     "beamlets_ct": (I.beamlets_ct, 0,
                     "512 6 MV pencil beamlets 0.5x0.5 cm2 at random gantry angles (SAD 100 cm), histories "
                     "10^N(5,0.5) clipped to [1e4,1e6], CT-like phantom 256x256x128 at 0.2 cm, one graph-captured "
@@ -393,9 +393,11 @@ def run_voxel_sweep(args, desc):
     for vox in (0.1, 0.15, 0.2, 0.25, 0.3, 0.4, 0.5):
         n_side = int(round(30.0 / vox))
         ph = I.slab((n_side,) * 3, (vox,) * 3)
-        for particle, spec, n in ((1, I.mono(15.0), 10_000_000), (0, I.spectrum_6mv(), 100_000_000)):
+        for (particle, spec, n), flags in [(c, f) for c in ((1, I.mono(15.0), 10_000_000),
+                                                          (0, I.spectrum_6mv(), 100_000_000))
+                                           for f in (0, ocmc.FLAG_CROSS_VOXELS)]:
             beam = I.beam_on(ph, particle, spec, (10.0, 10.0), 100.0)
-            with ocmc.Engine(0) as e:
+            with ocmc.Engine(0, flags=flags) as e:
                 e.create_phantom(ph)
                 e.set_source(beam)
                 for _ in range(max(args.warmup, 1)):
@@ -408,16 +410,18 @@ def run_voxel_sweep(args, desc):
                     ms.append(e.stats()["last_run_ms"])
                 st = e.stats()
             rows.append({"voxel_mm": vox * 10, "grid": n_side, "particle": "electron" if particle else "photon",
+                         "stepping": "voxel-crossing" if flags else "voxel-limited",
                          "histories": n, "kernel_ms": statistics.mean(ms),
                          "histories_per_s": n / (statistics.mean(ms) / 1e3),
                          "lane_steps_per_history": st["lane_steps"] / n,
                          "electron_steps_per_history": st["electron_steps"] / n})
             print(json.dumps(rows[-1]), file=sys.stderr)
-    ref = [r for r in rows if r["voxel_mm"] == 2.5 and r["particle"] == "electron"][0]
+    ref = [r for r in rows if r["voxel_mm"] == 2.5 and r["particle"] == "electron" and
+           r["stepping"] == "voxel-limited"][0]
     line = {"metric": "histories/s", "value": ref["histories_per_s"], "unit": "histories/s", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ref["kernel_ms"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": desc, "value_is": "15 MeV electrons at 2.5 mm",
+            "config": {"workload": desc, "value_is": "15 MeV electrons at 2.5 mm, voxel-limited steps",
                        "timing": "transport kernel (CUDA events inside the library)"},
             "gpu_launches": 2 * args.steps * len(rows), "sweep": rows}
     print(json.dumps(line))
@@ -539,11 +543,18 @@ def main():
         e2e_ms = []
         for k in range(args.warmup + args.steps):
             torch.cuda.synchronize()
+            if dist:
+                dist.barrier()
             t0 = time.perf_counter()
             e2e_eng.create_phantom(density=dens_h.numpy(), material=mat_h.numpy(), voxel=ph.voxel)
             e2e_eng.set_source(beam)
             first, count, total = sharding.shard(rank, world, n)
             e2e_eng.run_range(first, count, total, seed=1)
+            if dist:
+                # the method's one exchange step: every rank gets the summed tally
+                sharding.allreduce_tally(e2e_eng, tally, dist)
+                e2e_eng.reset()
+                e2e_eng.add_raw_tally(tally, 0, total)
             e2e_eng.dose(out=(dose_h, sig_h))
             dt = time.perf_counter() - t0
             if k >= args.warmup:

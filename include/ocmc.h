@@ -49,6 +49,14 @@ typedef enum {
 #define OCMC_FLAG_NO_MS            2  /* no multiple-scattering deflection          */
 #define OCMC_FLAG_KILL_FIRST_REAL  4  /* photons removed at first real interaction  */
 #define OCMC_FLAG_KERMA            8  /* e-/e+ deposit their energy where created   */
+/* Stepping variant (Sec. 4 Discussion): electron steps are not stopped at voxel faces but
+ * cross as many voxels as their length d = min(d_maxs, d_maxe, d_event) takes them through,
+ * depositing each voxel's own CSDA loss there; hard events are sampled against the
+ * phantom-wide majorant so that a candidate may fall in any voxel; the multiple-scattering
+ * angle of a step is that of its first voxel's medium; a step also ends where its energy has
+ * fallen by the fraction f_maxe. Analytic single-beam source only (ocmc_run_range returns
+ * OCMC_ERR_ARG with a phase-space source, ocmc_run_beamlets with beamlets). */
+#define OCMC_FLAG_CROSS_VOXELS    16
 
 /* Transport and execution parameters (Sec. 2.1: absorption energies, hard-event
  * cutoffs and the user-defined step limits d_maxs, d_maxe; Sec. 2.2.1: the
@@ -108,6 +116,11 @@ typedef struct {
     uint64_t lane_steps;       /* lane-steps executed (active lanes summed)         */
     double e_in, e_dep, e_esc, e_miss, pair_mass, annih_mass, e_killed, e_trans, e_dropped; /* MeV */
     double last_run_ms;        /* device time of the last ocmc_run (CUDA events)   */
+    /* transport-kernel timing (device timer): warp lifetimes summed over warps; the part
+     * of them after each warp found the source exhausted (work from its own stacks only);
+     * for the transport launches since the last reset, first warp start to last warp end,
+     * and the earliest source exhaustion seen by a warp to the last warp end */
+    double warp_ms, tail_warp_ms, span_ms, tail_span_ms;
 } ocmc_stats;
 
 /* Fill p with the defaults listed above. */
@@ -334,6 +347,13 @@ ocmc_status ocmc_unet_layer_times(ocmc_unet* net, const float* dose_dev, const f
 ocmc_status ocmc_unet_test_layer(int device, int mode, int nx, int ny, int nz, int cin, int cout,
                                  const float* x_host, const float* w_host, const float* dy_host, float* y_host,
                                  float* dx_host, float* dw_host);
+/* Test hook of the tensor-memory convolution's bounded waits (no counterpart in the paper;
+ * process-wide, off by default): with tile >= 0, every later launch's MMA-issuing thread waits,
+ * at its block-local tile number `tile`, up to `wait_ns` nanoseconds (at most the normal 2 s
+ * limit) on a barrier that nothing completes; the wait runs out, the block stops issuing, lets
+ * its copies and MMAs in flight finish, frees its tensor memory and sets the network's error
+ * flag, so the call returns OCMC_ERR_TIMEOUT. tile = -1 turns the hook off. */
+ocmc_status ocmc_unet_test_stall(int tile, uint64_t wait_ns);
 /* Denoise the context's current dose (and its batch sigma, the network's third input) with the
  * network; where the denoised value
  * differs from the plain Monte Carlo value by more than k_sigma times the plain dose's

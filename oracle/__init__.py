@@ -32,7 +32,7 @@ COUNTERS = ["flights", "fictitious", "compton", "photo", "pair", "esteps", "moll
 LEDGER = ["e_in", "e_dep", "e_esc", "e_miss", "pair_mass", "annih_mass", "e_killed",
           "e_path", "e_trans"]
 
-NO_HARD, NO_MS, KILL_FIRST_REAL, KERMA = 1, 2, 4, 8
+NO_HARD, NO_MS, KILL_FIRST_REAL, KERMA, CROSS_VOXELS = 1, 2, 4, 8, 16
 TALLY_SCALE = 2.0 ** 28
 
 

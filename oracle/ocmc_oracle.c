@@ -716,6 +716,29 @@ static void transport_photon(run_ctx* c, particle* q)
     }
 }
 
+/* An accepted hard event of a charged particle in material m: Moller with probability
+   sM / tot, else bremsstrahlung (Sec. 2.1); secondaries are emitted or absorbed. */
+static void hard_event(run_ctx* c, particle* q, int m, double sM, double tot)
+{
+    const orc_params* p = c->p;
+    if (rnd(&q->rs) * tot < sM) {
+        c->cnt[ORC_C_MOLLER]++;
+        double T1, W, d1[3], d2[3];
+        moller_event(q->E, p->w_cc, q->d, &q->rs, &T1, d1, &W, d2);
+        particle e = make_child(q, 2, ELECTRON, W, d2);
+        q->d[0] = d1[0]; q->d[1] = d1[1]; q->d[2] = d1[2];
+        q->E = T1;
+        emit_charged(c, &e);
+    } else {
+        c->cnt[ORC_C_BREMS]++;
+        double T0 = q->E, k, dg[3];
+        brems_event(m, T0, p->w_cb, q->d, &q->rs, &k, dg);
+        particle g = make_child(q, 3, PHOTON, k, dg);
+        q->E = T0 - k;
+        if (k >= p->e_abs_g) push(c, &g); else deposit(c, q->i, k);
+    }
+}
+
 static void transport_charged(run_ctx* c, particle* q)
 {
     const orc_params* p = c->p;
@@ -782,26 +805,123 @@ static void transport_charged(run_ctx* c, particle* q)
             double tot = sM + sB;
             if (tot > sig_hat * (1.0 + 1e-12)) c->cnt[ORC_C_VIOL_ELECTRON]++;
             if (rnd(&q->rs) * sig_hat < tot) {
-                if (rnd(&q->rs) * tot < sM) {
-                    c->cnt[ORC_C_MOLLER]++;
-                    double T1, W, d1[3], d2[3];
-                    moller_event(q->E, p->w_cc, q->d, &q->rs, &T1, d1, &W, d2);
-                    particle e = make_child(q, 2, ELECTRON, W, d2);
-                    q->d[0] = d1[0]; q->d[1] = d1[1]; q->d[2] = d1[2];
-                    q->E = T1;
-                    emit_charged(c, &e);
-                } else {
-                    c->cnt[ORC_C_BREMS]++;
-                    double T0 = q->E, k, dg[3];
-                    brems_event(m, T0, p->w_cb, q->d, &q->rs, &k, dg);
-                    particle g = make_child(q, 3, PHOTON, k, dg);
-                    q->E = T0 - k;
-                    if (k >= p->e_abs_g) push(c, &g); else deposit(c, q->i, k);
-                }
+                hard_event(c, q, m, sM, tot);
                 if (q->E < p->e_abs_e) { absorb_charged(c, q); return; }
             } else {
                 c->cnt[ORC_C_HARD_FICT]++;
             }
+        }
+    }
+}
+
+/* ---- voxel-crossing (fixed-step) electron transport ------------------------------------
+   The stepping scheme the paper contrasts with its own in the Discussion (Sec. 4): an electron
+   step is not stopped at voxel faces, so it crosses as many voxels as its length takes it
+   through. Reading implemented here (the same on the GPU):
+   - step length s = min(d_maxs, d_maxe, d_event): d_maxe is the path in the step's first voxel
+     over which the CSDA energy falls by the fraction f_maxe; d_event is sampled by Woodcock
+     tracking against the phantom-wide majorant max_m rho_max(m) sigma_hard,m over the step's
+     energy interval, so a candidate event may fall in any voxel;
+   - random hinge at xi s; the multiple-scattering angle is that of the whole step in the
+     medium of its first voxel (the scaling assumption of fixed-step schemes);
+   - along both straight parts the energy loss is the CSDA loss in each traversed voxel's own
+     material and density, deposited there; if the energy reaches T (1 - f_maxe) before the
+     end (denser voxels on the way), the step ends there (before the hinge: deflected there,
+     with the angle of the path travelled);
+   - at the end of an event-limited step the candidate is real with probability
+     rho sigma_hard(E) / majorant in the voxel where it ends. */
+enum { SEG_DONE, SEG_FLOOR, SEG_ESCAPED, SEG_ABSORBED };
+
+/* Move q a path length L along its direction through the voxels with CSDA loss deposited in
+   each; stops early at the energy floor Tfloor, on absorption or on escape. *done: path moved. */
+static int cross_segment(run_ctx* c, particle* q, double L, double Tfloor, double* done)
+{
+    const orc_params* p = c->p;
+    double left = L;
+    *done = 0.0;
+    while (left > 0.0) {
+        int m, face;
+        double rho = voxel_rho(c, q->i, &m);
+        double sv = dist_to_face(c, q->r, q->d, q->i, &face);
+        double l = left, T_end = q->E;
+        int cross = 0, floor_hit = 0;
+        if (sv < l) { l = sv; cross = 1; }
+        if (rho > 0.0) {
+            double lf = range_between(m, Tfloor, q->E, p) / rho;
+            if (lf <= l) { l = lf; cross = 0; floor_hit = 1; T_end = Tfloor; }
+            else T_end = orc_csda_loss(m, q->E, rho * l, p);
+        }
+        for (int a = 0; a < 3; ++a) q->r[a] += l * q->d[a];
+        deposit(c, q->i, q->E - T_end);
+        q->E = T_end;
+        c->ledger[ORC_L_EPATH] += l;
+        left -= l;
+        *done += l;
+        if (q->E < p->e_abs_e) { absorb_charged(c, q); return SEG_ABSORBED; }
+        if (floor_hit) return SEG_FLOOR;
+        if (cross) {
+            cross_face(c, q, face);
+            if (!inside_index(c, q->i)) { escape(c, q); return SEG_ESCAPED; }
+        }
+    }
+    return SEG_DONE;
+}
+
+static void transport_charged_cross(run_ctx* c, particle* q)
+{
+    const orc_params* p = c->p;
+    enum { LIM_MAXS, LIM_MAXE, LIM_EVENT };
+    for (;;) {
+        int m0, face;
+        double rho0 = voxel_rho(c, q->i, &m0);
+        if (rho0 <= 0.0) {                     /* no matter here: fly to the next voxel */
+            double sv = dist_to_face(c, q->r, q->d, q->i, &face);
+            for (int a = 0; a < 3; ++a) q->r[a] += sv * q->d[a];
+            cross_face(c, q, face);
+            c->cnt[ORC_C_GEO_CROSS]++;
+            if (!inside_index(c, q->i)) { escape(c, q); return; }
+            continue;
+        }
+        double T = q->E, Tlo = T * (1.0 - p->f_maxe);
+        double s_maxe = range_between(m0, Tlo, T, p) / rho0;
+        double maj = 0.0;
+        if (!(p->flags & ORC_NO_HARD)) {
+            for (int m = 0; m < N_MAT; ++m) {
+                if (!c->present[m]) continue;
+                for (int j = 0; j <= 16; ++j)
+                    maj = fmax(maj, c->rho_max[m] * orc_sigma_hard(m, Tlo + (T - Tlo) * j / 16.0, p));
+            }
+            maj *= 1.02;
+        }
+        double d_ev = maj > 0.0 ? -log(rnd(&q->rs)) / maj : INFINITY;
+        double s = p->d_maxs;
+        int lim = LIM_MAXS;
+        if (s_maxe < s) { s = s_maxe; lim = LIM_MAXE; }
+        if (d_ev < s)   { s = d_ev;   lim = LIM_EVENT; }
+        double s1 = rnd(&q->rs) * s, done;
+        double T_full = orc_csda_loss(m0, T, rho0 * s, p);
+        c->cnt[ORC_C_ESTEPS]++;
+        int r = cross_segment(c, q, s1, Tlo, &done);
+        if (r == SEG_ESCAPED || r == SEG_ABSORBED) return;
+        if (!(p->flags & ORC_NO_MS)) {
+            double G1 = rho0 * (r == SEG_FLOOR ? done : s) * orc_lambda1_inv(m0, 0.5 * (T + T_full));
+            double mu = sample_ms_mu(G1, &q->rs), phi = 2.0 * PI * rnd(&q->rs);
+            rotate(q->d, mu, phi);
+        }
+        if (r == SEG_FLOOR) continue;
+        r = cross_segment(c, q, s - s1, Tlo, &done);
+        if (r == SEG_ESCAPED || r == SEG_ABSORBED) return;
+        if (r == SEG_FLOOR || lim != LIM_EVENT) continue;
+        int m;
+        double rho = voxel_rho(c, q->i, &m);
+        double sM = rho * orc_sigma_moller(m, q->E, p->w_cc), sB = rho * orc_sigma_brems(m, q->E, p->w_cb);
+        double tot = sM + sB;
+        if (tot > maj * (1.0 + 1e-12)) c->cnt[ORC_C_VIOL_ELECTRON]++;
+        if (rnd(&q->rs) * maj < tot) {
+            hard_event(c, q, m, sM, tot);
+            if (q->E < p->e_abs_e) { absorb_charged(c, q); return; }
+        } else {
+            c->cnt[ORC_C_HARD_FICT]++;
         }
     }
 }
@@ -969,6 +1089,7 @@ int orc_run(const orc_phantom* ph, const orc_source* src, const orc_params* p,
         while (c->top > 0) {
             particle r = c->stack[--c->top];
             if (r.type == PHOTON) transport_photon(c, &r);
+            else if (p->flags & ORC_CROSS_VOXELS) transport_charged_cross(c, &r);
             else transport_charged(c, &r);
         }
     }
@@ -1065,6 +1186,7 @@ int orc_run_ps(const orc_phantom* ph, const orc_ps_particle* ps, uint64_t n_ps,
         while (c->top > 0) {
             particle r = c->stack[--c->top];
             if (r.type == PHOTON) transport_photon(c, &r);
+            else if (p->flags & ORC_CROSS_VOXELS) transport_charged_cross(c, &r);
             else transport_charged(c, &r);
         }
     }

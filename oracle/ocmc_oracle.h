@@ -24,6 +24,7 @@ extern "C" {
 #define ORC_NO_MS            2  /* no multiple-scattering deflection               */
 #define ORC_KILL_FIRST_REAL  4  /* photons removed at their first real interaction */
 #define ORC_KERMA            8  /* e-/e+ deposit their kinetic energy at creation  */
+#define ORC_CROSS_VOXELS    16  /* electron steps cross voxel faces (fixed-step variant, Sec. 4) */
 
 typedef struct {
     double e_abs_e;   /* MeV, electron/positron absorption energy              */

@@ -61,7 +61,7 @@ const char* check_params(const ocmc_params* p)
     if (!(p->f_maxe > 0.f && p->f_maxe <= 0.5f)) return "f_maxe must be in (0, 0.5]";
     if (!(p->s_min >= 0.f && p->s_min <= 0.01f)) return "s_min must be in [0, 0.01] cm";
     if (p->n_batches < 1 || p->n_batches > 1000) return "n_batches must be in [1, 1000]";
-    if (p->flags < 0 || p->flags > 15) return "unknown flags";
+    if (p->flags < 0 || p->flags > 31) return "unknown flags";
     if (p->block_threads != 0 && (p->block_threads < 32 || p->block_threads > 1024 || p->block_threads % 32))
         return "block_threads must be 0 or a multiple of 32 in [32, 1024]";
     if (p->blocks_per_sm < 0 || p->blocks_per_sm > 32) return "blocks_per_sm must be in [0, 32]";
@@ -299,6 +299,7 @@ ocmc_status ocmc_init(ocmc_ctx** out, int device, const ocmc_params* p)
     if (r == cudaSuccess) r = dalloc(&c->t.el, MAX_STAGED * NE * 4);
     if (r == cudaSuccess) r = dalloc(&c->t.el2, MAX_STAGED * NE * 2);
     if (r == cudaSuccess) r = dalloc(&c->t.phmaj, NE);
+    if (r == cudaSuccess) r = dalloc(&c->t.elmaj, NE);
     if (r == cudaSuccess) r = dalloc(&c->t.rinv, MAX_STAGED * NR);
     if (r == cudaSuccess) r = dalloc(&c->t.msA, NG);
     if (r == cudaSuccess) r = dalloc(&c->t.rmeta, 2 * MAX_STAGED);
@@ -564,6 +565,8 @@ ocmc_status ocmc_run_range(ocmc_ctx* c, uint64_t first, uint64_t count, uint64_t
     if (!c->have_source) return fail(c, OCMC_ERR_STATE, "no source (call ocmc_set_source)");
     if (count == 0 || n_total == 0 || first + count > n_total || first + count < first)
         return fail(c, OCMC_ERR_ARG, "need 0 < count and first + count <= n_total");
+    if ((c->p.flags & FLAG_CROSS_VOXELS) && c->src_kind == 1)
+        return fail(c, OCMC_ERR_ARG, "voxel-crossing electron steps need the analytic source (not a phase space)");
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     CK(cudaSetDevice(c->device), "cudaSetDevice");
     ocmc_status st = ensure_tally(c);
@@ -733,6 +736,13 @@ ocmc_status ocmc_get_stats(ocmc_ctx* c, ocmc_stats* out)
     out->e_killed = st[ST_E_KILLED] * S;
     out->e_trans = st[ST_E_TRANS] * S;
     out->e_dropped = st[ST_E_DROPPED] * S;
+    out->warp_ms = st[ST_WARP_NS] * 1e-6;
+    out->tail_warp_ms = st[ST_TAIL_NS] * 1e-6;
+    if (st[ST_T_END]) {
+        const unsigned long long t0 = ~st[ST_T_START_INV], ts = ~st[ST_T_SRC_INV];
+        out->span_ms = (st[ST_T_END] - t0) * 1e-6;
+        out->tail_span_ms = (st[ST_T_END] - ts) * 1e-6;
+    }
     out->pair_mass = 2.0 * MC2 * (double)st[ST_PAIR];
     out->annih_mass = 2.0 * MC2 * (double)st[ST_ANNIH];
     if (c->d_tally) {
@@ -766,7 +776,7 @@ void ocmc_destroy(ocmc_ctx* c)
     dfree(&c->d_density); dfree(&c->d_material); dfree(&c->d_tally); dfree(&c->d_stats);
     dfree(&c->d_counter); dfree(&c->d_sum); dfree(&c->d_err); dfree(&c->d_stacks); dfree(&c->d_dose);
     dfree(&c->d_sigma); dfree(&c->d_invnb);
-    dfree(&c->t.ph); dfree(&c->t.el); dfree(&c->t.el2); dfree(&c->t.phmaj); dfree(&c->t.rinv); dfree(&c->t.msA);
+    dfree(&c->t.ph); dfree(&c->t.el); dfree(&c->t.el2); dfree(&c->t.phmaj); dfree(&c->t.elmaj); dfree(&c->t.rinv); dfree(&c->t.msA);
     dfree(&c->t.rmeta); dfree(&c->t.msc); dfree(&c->t.scratch); dfree(&c->t.rho_max);
     dfree(&c->d_bl); dfree(&c->d_bl_prefix); dfree(&c->d_bl_offs); dfree(&c->d_bl_caps); dfree(&c->d_bl_nnz);
     dfree(&c->d_bl_over); dfree(&c->d_bl_keys); dfree(&c->d_bl_vals); dfree(&c->d_dense); dfree(&c->d_chunks);

@@ -288,6 +288,8 @@ ocmc_status ocmc_run_beamlets(ocmc_ctx* c, uint64_t seed, void* stream)
     if (!c) return ctx_fail(c, OCMC_ERR_ARG, "ctx is NULL");
     if (!c->have_phantom) return ctx_fail(c, OCMC_ERR_STATE, "no phantom (call ocmc_create_phantom)");
     if (c->bl_n < 1) return ctx_fail(c, OCMC_ERR_STATE, "no beamlets (call ocmc_set_beamlets)");
+    if (c->p.flags & FLAG_CROSS_VOXELS)
+        return ctx_fail(c, OCMC_ERR_ARG, "voxel-crossing electron steps are not available for beamlets");
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     BCK(cudaSetDevice(c->device), "cudaSetDevice");
     ocmc_status st = ctx_ensure_tables(c, s);

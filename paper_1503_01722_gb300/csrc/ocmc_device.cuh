@@ -215,6 +215,14 @@ __device__ __forceinline__ float sample_ms(const SmemTables& T, float G1, Rng& r
     return fmaxf(-1.f, 1.f - u);
 }
 
+// The GPU's global nanosecond timer (consistent across SMs).
+__device__ __forceinline__ unsigned long long globaltimer_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
 // Rotate unit direction (u,v,w) by polar cosine mu and azimuth phi = 2 pi xi.
 __device__ __forceinline__ void rotate(float& u, float& v, float& w, float mu, float xi)
 {
@@ -222,8 +230,10 @@ __device__ __forceinline__ void rotate(float& u, float& v, float& w, float mu, f
     float sp, cp;
     __sincosf(6.283185307179586f * xi, &sp, &cp);
     // sin of the polar angle of (u, v, w) from its own components: 1 - w^2 would cancel near
-    // the poles and give the frame a wrong scale there
-    float s = sqrtf(fmaf(u, u, v * v));
+    // the poles and give the frame a wrong scale there. Correctly rounded intrinsics: the
+    // compiler may not contract or approximate them differently in different instantiations of
+    // the transport kernel, which keeps the tally bit-identical across launch shapes.
+    float s = __fsqrt_rn(__fmaf_rn(u, u, __fmul_rn(v, v)));
     float nu, nv, nw;
     if (s > 1e-10f) {
         float is = 1.f / s;

@@ -31,6 +31,9 @@ constexpr double MC2 = 0.51099895000;
 constexpr float TALLY_SCALE = 268435456.0f;   // 2^28 fixed-point units per MeV
 constexpr int MAX_DIM = 1024;
 
+// transport flags (ocmc_params.flags)
+constexpr int FLAG_CROSS_VOXELS = 16;   // electron steps cross voxel faces (fixed-step variant)
+
 // error bits written by kernels
 constexpr int ERR_OVERFLOW = 1;
 constexpr int ERR_LIMIT = 2;
@@ -43,6 +46,11 @@ enum Stat {
     ST_WARP_ITERS, ST_LANES_PHOTON, ST_LANES_CHARGED, ST_HISTORIES,
     // fixed-point energies (2^28 units per MeV)
     ST_E_IN, ST_E_ESC, ST_E_MISS, ST_E_KILLED, ST_E_TRANS, ST_E_DROPPED,
+    // transport-kernel timing from %globaltimer (ns): summed warp lifetimes, summed warp time
+    // after the warp saw the source exhausted, and (max-reduced, written directly) the bitwise
+    // complement of the earliest warp start and of the earliest source exhaustion, and the
+    // latest warp end
+    ST_WARP_NS, ST_TAIL_NS, ST_T_START_INV, ST_T_SRC_INV, ST_T_END,
     ST_COUNT
 };
 
@@ -53,6 +61,7 @@ struct Tables {
     MatDef* mats;   // their definitions (device, MAX_STAGED)
     float4* ph;     // n_mat*NE
     float* phmaj;   // NE
+    float* elmaj;   // NE: phantom-wide majorant of rho * sigma_hard over a step (voxel-crossing steps)
     float4* el;     // n_mat*NE
     float2* el2;    // n_mat*NE
     float* rinv;    // n_mat*NR

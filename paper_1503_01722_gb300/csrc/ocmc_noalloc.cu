@@ -160,6 +160,7 @@ extern "C" ocmc_status ocmc_run_noalloc(int device, int nx, int ny, int nz, cons
     t.el = cv.take<float4>(NMAT_DEFAULT * NE);
     t.el2 = cv.take<float2>(NMAT_DEFAULT * NE);
     t.phmaj = cv.take<float>(NE);
+    t.elmaj = cv.take<float>(NE);
     t.rinv = cv.take<float>(NMAT_DEFAULT * NR);
     t.msA = cv.take<float>(NG);
     t.rmeta = cv.take<float>(2 * NMAT_DEFAULT);

@@ -308,6 +308,11 @@ __global__ void k_photon_majorant(Tables t)
         if (r > 0.f) best = fmaxf(best, (float)log((double)r) + t.ph[m * NE + i].x);
     }
     t.phmaj[i] = best > -1e29f ? best + 1e-6f : best;   // small margin over FP32 rounding
+    // voxel-crossing electron steps: max over materials of rho_max * (hard-event majorant of a
+    // step starting in [E_i, E_i+1)), so a step's candidate events may fall in any voxel
+    float hm = 0.f;
+    for (int m = 0; m < t.n_mat; ++m) hm = fmaxf(hm, __uint_as_float(t.rho_max[m]) * t.el2[m * NE + i].y);
+    t.elmaj[i] = hm * 1.00001f;
 }
 
 }  // namespace

@@ -415,20 +415,151 @@ __device__ __forceinline__ bool charged_step(C& c, Lane& p, unsigned& n_hfict)
     return true;
 }
 
+// ---- voxel-crossing (fixed-step) electron steps ------------------------------------------
+// The stepping scheme the paper contrasts with its own (Sec. 4): a step is not stopped at voxel
+// faces. s = min(d_maxs, d_maxe, d_event) with d_maxe from the step's first voxel and d_event
+// sampled against the phantom-wide majorant of rho * sigma_hard (so a candidate may fall in any
+// voxel); random hinge at xi s with the multiple-scattering angle of the whole step in the first
+// voxel's medium; along both straight parts the CSDA loss of each traversed voxel's own
+// material and density is deposited there; the step ends early where the energy reaches
+// E (1 - f_maxe) (before the hinge: deflected there, for the path travelled); a candidate at the
+// end of an event-limited step is real with probability rho sigma_hard(E) / majorant in the
+// voxel where it ends.
+enum { SEG_DONE = 0, SEG_FLOOR, SEG_OUT };   // SEG_OUT: the particle escaped or was absorbed
+
+__device__ __forceinline__ float range_R(const SmemTables& T, int m, float E)
+{
+    const EIdx ei = e_index(E);
+    return __expf(lerp1(T.el[m * MS4 + ei.i].x, T.el[m * MS4 + ei.i + 1].x, ei.f));
+}
+
+// Moves p a path length L along its direction through the voxels, losing and depositing the
+// CSDA energy of each voxel it crosses; stops early at the energy floor Ef, on absorption or on
+// escape. *done receives the path length travelled.
+template <class C>
+__device__ __forceinline__ int cross_segment(C& c, Lane& p, float L, float Ef, float* done)
+{
+    const TransportArgs& a = c.a;
+    const SmemTables& T = c.T;
+    float left = L, moved = 0.f;
+    for (int guard = 0; left > 0.f; ++guard) {
+        if (guard > 4 * (a.nx + a.ny + a.nz)) { c.ok = false; break; }   // cannot happen: bounded crossings
+        const int vox = p.ix + a.nx * (p.iy + a.ny * p.iz);
+        const float rho = __ldg(a.density + vox);
+        const int m = __ldg(a.material + vox);
+        int face;
+        const float sv = dist_to_face(p.x, p.y, p.z, p.u, p.v, p.w, p.ix, p.iy, p.iz, a.dx, a.dy, a.dz, &face);
+        float l = left, Eend = p.E;
+        bool cross = false, flo = false;
+        if (sv < l) { l = sv; cross = true; }
+        if (rho > 0.f) {
+            const EIdx ei = e_index(p.E);
+            const float lnR = lerp1(T.el[m * MS4 + ei.i].x, T.el[m * MS4 + ei.i + 1].x, ei.f);
+            const float R = __expf(lnR);
+            const float lf = (R - range_R(T, m, Ef)) / rho;
+            if (lf <= l) { l = fmaxf(lf, 0.f); cross = false; flo = true; Eend = Ef; }
+            else Eend = csda_end2(T, m, p.E, R, range_to_lnE(T, m, lnR), rho * l);
+        }
+        p.x = fmaf(l, p.u, p.x);
+        p.y = fmaf(l, p.v, p.y);
+        p.z = fmaf(l, p.w, p.z);
+        deposit(c, p, p.ix, p.iy, p.iz, p.E - Eend);
+        p.E = Eend;
+        left -= l;
+        moved += l;
+        if (p.E < a.pp.e_abs_e) { absorb_charged(c, p); *done = moved; return SEG_OUT; }
+        if (flo) { *done = moved; return SEG_FLOOR; }
+        if (cross && !cross_face(c, p, face)) { escape(c, p); *done = moved; return SEG_OUT; }
+    }
+    *done = moved;
+    return SEG_DONE;
+}
+
+template <class C>
+__device__ __forceinline__ bool charged_step_cross(C& c, Lane& p, unsigned& n_hfict)
+{
+    const TransportArgs& a = c.a;
+    const SmemTables& T = c.T;
+    const uint32_t k0 = a.key0, k1 = a.key1;
+    const int vox = p.ix + a.nx * (p.iy + a.ny * p.iz);
+    const float rho0 = __ldg(a.density + vox);
+    const int m0 = __ldg(a.material + vox);
+    if (!(rho0 > 0.f)) {                       // no matter here: fly to the next voxel
+        int face;
+        float sv = dist_to_face(p.x, p.y, p.z, p.u, p.v, p.w, p.ix, p.iy, p.iz, a.dx, a.dy, a.dz, &face);
+        p.x = fmaf(sv, p.u, p.x);
+        p.y = fmaf(sv, p.v, p.y);
+        p.z = fmaf(sv, p.w, p.z);
+        stat_add(c, ST_GEO, 1);
+        if (!cross_face(c, p, face)) { escape(c, p); return false; }
+        return true;
+    }
+    rng_step_start(p.r, k0, k1);
+    const float E0 = p.E;
+    const EIdx ei = e_index(E0);
+    const int mb = m0 * MS4, mb2 = m0 * MS2;
+    const float lnR = lerp1(T.el[mb + ei.i].x, T.el[mb + ei.i + 1].x, ei.f);
+    const float s_maxe = lerp1(T.el2[mb2 + ei.i].x, T.el2[mb2 + ei.i + 1].x, ei.f) / rho0;
+    const float maj = (a.pp.flags & 1) ? 0.f : __ldg(a.t.elmaj + ei.i);
+    const float d_ev = maj > 0.f ? -__logf(rng_u(p.r, k0, k1)) / maj : 3.0e38f;
+    float s = a.pp.d_maxs;
+    int lim = 1;
+    if (s_maxe < s) { s = s_maxe; lim = 2; }
+    if (d_ev < s) { s = d_ev; lim = 3; }
+    const float s1 = rng_u(p.r, k0, k1) * s;
+    const float Ef = E0 * (1.f - a.pp.f_maxe);
+    const float Efull = csda_end2(T, m0, E0, __expf(lnR), range_to_lnE(T, m0, lnR), rho0 * s);
+    float done;
+    int r = cross_segment(c, p, s1, Ef, &done);
+    if (r == SEG_OUT) return false;
+    if (!(a.pp.flags & 2)) {
+        EIdx em = e_index(0.5f * (E0 + Efull));
+        float l1 = lerp1(T.el[mb + em.i].y, T.el[mb + em.i + 1].y, em.f);
+        float cth = sample_ms(T, rho0 * (r == SEG_FLOOR ? done : s) * l1, p.r, k0, k1);
+        float xphi = rng_u(p.r, k0, k1);
+        rotate(p.u, p.v, p.w, cth, xphi);
+    }
+    if (r == SEG_FLOOR) return true;
+    r = cross_segment(c, p, s - s1, Ef, &done);
+    if (r == SEG_OUT) return false;
+    if (r == SEG_FLOOR || lim != 3) return true;
+    // candidate hard event where the step ended
+    const int v2 = p.ix + a.nx * (p.iy + a.ny * p.iz);
+    const float rho = __ldg(a.density + v2);
+    const int m = __ldg(a.material + v2);
+    const EIdx e2 = e_index(p.E);
+    const float4 A2 = T.el[m * MS4 + e2.i], B2 = T.el[m * MS4 + e2.i + 1];
+    const float sM = p.E > 2.f * a.pp.w_cc ? rho * lerp1(A2.z, B2.z, e2.f) : 0.f;
+    const float sB = p.E > a.pp.w_cb ? rho * lerp1(A2.w, B2.w, e2.f) : 0.f;
+    const float tot = sM + sB;
+    if (tot > maj * 1.00001f) stat_add(c, ST_VIOL, 1);
+    if (rng_u(p.r, k0, k1) * maj < tot) {
+        hard_event(c, p, m, sM, tot);
+        if (p.E < a.pp.e_abs_e) { absorb_charged(c, p); return false; }
+    } else {
+        n_hfict++;
+    }
+    return true;
+}
+
 // NREG: register cap per thread. More registers spill less; fewer registers let more
 // warps share an SM (80: 3 x 256 threads, 64: 2 x 512, 56: 3 x 384 on GB300).
 // PS: the source is a phase space (per-history records of mixed particle types); a separate
 // instantiation, so that the analytic-source kernel carries none of its code.
-template <bool BL, bool PS, int NREG>
+// XV: electron steps cross voxel faces (the fixed-step variant); a separate instantiation of the
+// analytic-source kernel, so the voxel-limited kernels carry none of its code.
+template <bool BL, bool PS, int NREG, bool XV = false>
 __global__ void __maxnreg__(NREG) k_transport(const __grid_constant__ TransportArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_top[MAX_WARPS][3];
     __shared__ unsigned long long s_st[ST_COUNT];
+    __shared__ unsigned long long s_time[MAX_WARPS][2];   // per warp: start, source seen exhausted
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     for (int i = threadIdx.x; i < ST_COUNT; i += blockDim.x) s_st[i] = 0ull;
     if (lane == 0) { s_top[wib][0] = 0; s_top[wib][1] = 0; s_top[wib][2] = 0; }
     SmemTables T = stage_tables(a.t, smem);   // ends with __syncthreads()
+    if (lane == 0) { s_time[wib][0] = globaltimer_ns(); s_time[wib][1] = 0ull; }
 
     const long long gw = (long long)blockIdx.x * (blockDim.x >> 5) + wib;
     CtxT<BL> c{a, T, a.stacks + (size_t)gw * a.nstk * a.cap, s_top[wib], s_st,
@@ -470,7 +601,10 @@ __global__ void __maxnreg__(NREG) k_transport(const __grid_constant__ TransportA
                 unsigned long long base = 0;
                 if (lane == 0) base = atomicAdd(a.hist_counter, (unsigned long long)want);
                 base = __shfl_sync(FULL, base, 0);
-                if (base + want >= a.count) src_done = true;
+                if (base + want >= a.count) {
+                    src_done = true;
+                    if (lane == 0) s_time[wib][1] = globaltimer_ns();
+                }
                 int r2 = rank - take;
                 if (!active && r2 >= 0 && r2 < want && base + r2 < a.count) {
                     hist++;
@@ -549,7 +683,8 @@ __global__ void __maxnreg__(NREG) k_transport(const __grid_constant__ TransportA
             if (mode) lanes_ch += nact; else lanes_ph += nact;
         }
         if (active) {
-            active = mode ? charged_step(c, p, n_hfict) : photon_step(c, p, n_fict);
+            if constexpr (XV) active = mode ? charged_step_cross(c, p, n_hfict) : photon_step(c, p, n_fict);
+            else active = mode ? charged_step(c, p, n_hfict) : photon_step(c, p, n_fict);
             if (active && ++p.steps > STEP_LIMIT) {
                 atomicOr(a.err, ERR_LIMIT);
                 stat_add(c, ST_DROPPED, 1);
@@ -573,6 +708,14 @@ __global__ void __maxnreg__(NREG) k_transport(const __grid_constant__ TransportA
         atomicAdd(s_st + ST_WARP_ITERS, iters);
         atomicAdd(s_st + ST_LANES_PHOTON, lanes_ph);
         atomicAdd(s_st + ST_LANES_CHARGED, lanes_ch);
+        // tail: how long this warp ran on its own stacks after the source ran dry
+        const unsigned long long t_end = globaltimer_ns(), t0 = s_time[wib][0];
+        const unsigned long long ts = s_time[wib][1] ? s_time[wib][1] : t0;
+        atomicAdd(s_st + ST_WARP_NS, t_end - t0);
+        atomicAdd(s_st + ST_TAIL_NS, t_end - ts);
+        atomicMax(a.stats + ST_T_START_INV, ~t0);
+        atomicMax(a.stats + ST_T_SRC_INV, ~ts);
+        atomicMax(a.stats + ST_T_END, t_end);
     }
     __syncthreads();
     for (int i = threadIdx.x; i < ST_COUNT; i += blockDim.x)
@@ -584,13 +727,13 @@ __global__ void __maxnreg__(NREG) k_transport(const __grid_constant__ TransportA
 size_t transport_smem_bytes(int n_mat) { return smem_table_bytes(n_mat); }
 
 namespace {
-template <bool BL, bool PS, int R>
+template <bool BL, bool PS, int R, bool XV = false>
 cudaError_t launch_variant(const TransportArgs& a, int blocks, int threads, size_t smem, cudaStream_t s)
 {
     cudaError_t e =
-        cudaFuncSetAttribute(k_transport<BL, PS, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_transport<BL, PS, R, XV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_transport<BL, PS, R><<<blocks, threads, smem, s>>>(a);
+    k_transport<BL, PS, R, XV><<<blocks, threads, smem, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -623,6 +766,9 @@ int transport_max_blocks_per_sm(int threads, size_t smem, int nreg)
     occupancy<false, true, 56>(threads, smem);
     occupancy<false, true, 64>(threads, smem);
     occupancy<false, true, 80>(threads, smem);
+    cudaFuncSetAttribute(k_transport<false, false, 56, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_transport<false, false, 64, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_transport<false, false, 80, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (nreg == 56) return occupancy<false, false, 56>(threads, smem);
     if (nreg == 64) return occupancy<false, false, 64>(threads, smem);
     return occupancy<false, false, 80>(threads, smem);
@@ -630,6 +776,13 @@ int transport_max_blocks_per_sm(int threads, size_t smem, int nreg)
 
 cudaError_t launch_transport(const TransportArgs& a, int blocks, int threads, size_t smem, cudaStream_t s, int nreg)
 {
+    if (a.pp.flags & FLAG_CROSS_VOXELS) {
+        // voxel-crossing electron steps: analytic single-beam source only (callers check)
+        if (a.beamlets || a.ps) return cudaErrorInvalidValue;
+        if (nreg == 56) return launch_variant<false, false, 56, true>(a, blocks, threads, smem, s);
+        if (nreg == 64) return launch_variant<false, false, 64, true>(a, blocks, threads, smem, s);
+        return launch_variant<false, false, 80, true>(a, blocks, threads, smem, s);
+    }
     if (a.beamlets) return launch_source<true, false>(a, blocks, threads, smem, s, nreg);
     if (a.ps) return launch_source<false, true>(a, blocks, threads, smem, s, nreg);
     return launch_source<false, false>(a, blocks, threads, smem, s, nreg);

@@ -865,6 +865,13 @@ ocmc_status ocmc_unet_layer_times(ocmc_unet* u, const float* dose, const float* 
     return OCMC_OK;
 }
 
+ocmc_status ocmc_unet_test_stall(int tile, uint64_t wait_ns)
+{
+    if (tile < -1) return OCMC_ERR_ARG;
+    conv3_tc_test_stall(tile, wait_ns);
+    return OCMC_OK;
+}
+
 // Single layer through the network's kernels, for the gradient tests: x (input grid,
 // cin channels), w [taps][cin][cout], dy (output grid, cout) host arrays in FP32 (rounded
 // to BF16); y = layer(x) without bias/ReLU, dx, dw (FP32) out.

@@ -44,6 +44,10 @@ constexpr int TX = 8, TY = 16, HX = TX + 2, HY = TY + 2;
 constexpr int TC_THREADS = 192;
 constexpr uint64_t WAIT_NS = 2000000000ull;
 
+// test hook of the bounded waits (process-wide; off by default)
+int g_stall_tile = -1;
+uint64_t g_stall_ns = 0;
+
 struct TcArgs {
     Grid3 g;
     Slice out;
@@ -54,6 +58,10 @@ struct TcArgs {
     int mask_stride, mask_c0;
     int tiles_x, tiles_y, ntiles;
     int* err;
+    // test hook: at its block-local tile number stall_tile (>= 0) the MMA thread waits stall_ns
+    // on a barrier that nothing completes, so that this wait runs out like a real timeout
+    int stall_tile;
+    uint64_t stall_ns;
 };
 
 template <int CIN, int NSL, int TZ, int NS_>
@@ -164,6 +172,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv3_tc(const __grid_constan
                 int it = 0, lt = 0;
                 for (int tile = blockIdx.x; tile < a.ntiles && !*abort; tile += gridDim.x, ++lt) {
                     const int acc = lt & 1, ua = lt >> 1;
+                    if (lt == a.stall_tile) {   // drain's phase 0 completes only in the abort path below
+                        mbar_wait(drain, 0, abort, a.stall_ns);
+                        break;
+                    }
                     if (!mbar_wait(&t_empty[acc], (ua & 1) ^ 1, abort, WAIT_NS)) break;
                     fence_after_sync();
                     const uint32_t d0 = tmem + (uint32_t)(acc * TZ * NSL);
@@ -339,6 +351,8 @@ cudaError_t launch_cfg(const ConvArgs& a, const __nv_bfloat16* wpack, int* err, 
     const int tiles_z = (g.nz + TZ - 1) / TZ;
     t.ntiles = t.tiles_x * t.tiles_y * tiles_z;
     t.err = err;
+    t.stall_tile = g_stall_tile;
+    t.stall_ns = g_stall_ns;
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -364,6 +378,12 @@ long long tc_blocks(Grid3 g, int tz, int slices)
 }
 
 }  // namespace
+
+void conv3_tc_test_stall(int tile, uint64_t ns)
+{
+    g_stall_tile = tile;
+    g_stall_ns = std::min<uint64_t>(ns, WAIT_NS);
+}
 
 bool conv3_tc_supported(int cin, int cout)
 {

@@ -8,6 +8,11 @@
 namespace ocmc {
 namespace unet {
 
+// Test hook: from now on every launch's MMA thread, at its block-local tile number `tile`
+// (>= 0; -1 turns the hook off), waits `ns` (at most the normal limit) on a barrier that nothing
+// completes, so that the wait runs out and the block takes its timeout path.
+void conv3_tc_test_stall(int tile, uint64_t ns);
+
 // Channel counts the tensor-memory kernel covers (16 to 128; each block holds the weights of a
 // slice of the output channels in shared memory).
 bool conv3_tc_supported(int cin, int cout);

@@ -15,7 +15,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_HERE, "libocmc.so")
 
 OK, ERR_ARG, ERR_CUDA, ERR_OOM, ERR_OVERFLOW, ERR_TIMEOUT, ERR_STATE = range(7)
-FLAG_NO_HARD, FLAG_NO_MS, FLAG_KILL_FIRST_REAL, FLAG_KERMA = 1, 2, 4, 8
+FLAG_NO_HARD, FLAG_NO_MS, FLAG_KILL_FIRST_REAL, FLAG_KERMA, FLAG_CROSS_VOXELS = 1, 2, 4, 8, 16
 TALLY_SCALE = 2.0 ** 28
 
 
@@ -51,7 +51,8 @@ class Stats(C.Structure):
         "brems", "hard_fictitious", "annihilations", "escaped", "missed", "geo_crossings",
         "majorant_violations", "dropped", "transmitted", "warp_iterations", "lane_steps")] + \
         [(n, C.c_double) for n in ("e_in", "e_dep", "e_esc", "e_miss", "pair_mass", "annih_mass", "e_killed",
-                                   "e_trans", "e_dropped", "last_run_ms")]
+                                   "e_trans", "e_dropped", "last_run_ms", "warp_ms", "tail_warp_ms", "span_ms",
+                                   "tail_span_ms")]
 
 
 def _load():
@@ -102,6 +103,7 @@ def _load():
         "ocmc_unet_test_layer": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
                                            P, P, P, P, P, P]),
         "ocmc_denoise": (C.c_int, [P, P, C.c_float, P, P, C.c_int]),
+        "ocmc_unet_test_stall": (C.c_int, [C.c_int, C.c_uint64]),
         "ocmc_run_noalloc": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, P, P, C.c_float, C.c_float, C.c_float,
                                        C.c_int, C.c_int, P, P, C.c_float, C.c_float, C.c_float,
                                        C.POINTER(C.c_float), C.POINTER(C.c_float), C.POINTER(Params),
@@ -395,6 +397,14 @@ def test_philox(key, c1, c2, c3, first_block, n_blocks, device=0):
     if st != OK:
         raise OcmcError(st, lib.ocmc_last_error(None).decode())
     return out
+
+
+def unet_test_stall(tile=-1, wait_ns=0):
+    """Test hook of the tensor-memory convolution's bounded waits (ocmc_unet_test_stall):
+    tile >= 0 makes every later launch time out at that block-local tile; -1 turns it off."""
+    st = lib.ocmc_unet_test_stall(int(tile), int(wait_ns))
+    if st != OK:
+        raise OcmcError(st, "ocmc_unet_test_stall failed")
 
 
 def test_rotate(dirs, mu, xi, device=0):

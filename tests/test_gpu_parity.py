@@ -40,15 +40,18 @@ def agreement(D, S, Dr, Sr):
     }
 
 
-def run_both(ocmc, ph, beam, n, seed=1, B=50, **kw):
+def run_both(ocmc, ph, beam, n, seed=1, B=50, orc=None, **kw):
+    """GPU and oracle doses at n histories each, on independent random streams (the GPU run's
+    seed differs from the oracle's, so the two samples share no noise and sigma_combined is the
+    right yardstick)."""
     with ocmc.Engine(0, n_batches=B, **kw) as e:
         e.create_phantom(ph)
         e.set_source(beam)
-        e.run(n, seed=seed)
+        e.run(n, seed=seed + 1000)
         D, S = e.dose()
         st = e.stats()
         tally = e.raw_tally()
-    r = O.run(ph, beam, n, seed=seed, p=O.params(n_batches=B))
+    r = O.run(ph, beam, n, seed=seed, p=O.params(n_batches=B, **(orc or {})))
     Dr, Sr = r.dose()
     return D, S, Dr, Sr, st, tally, r
 
@@ -89,6 +92,25 @@ def test_dose_parity(ocmc, case):
     e_gpu, e_orc = st["e_dep"] / n, r.ledger["e_dep"] / n
     sd = math.sqrt(((tally.sum(axis=(1, 2, 3)) / 2 ** 28 / (n / 50) - e_gpu) ** 2).sum() / (50 * 49)) * 1.5
     assert abs(e_gpu - e_orc) < 4 * sd + 1e-3 * e_orc, (e_gpu, e_orc, sd)
+
+
+PAPER_CUTS = dict(e_abs_e=0.2, e_abs_g=0.05, w_cc=0.2, w_cb=0.05)
+
+
+@pytest.mark.parametrize("particle,kind,n", [(1, "slab", 20_000), (0, "slab", 300_000), (0, "half", 300_000)])
+def test_paper_preset_parity(ocmc, particle, kind, n):
+    """The paper's own setup (Sec. 2.2 "Materials", Tables 2-3): 2x2 cm^2 at SSD 100, the
+    32 cm phantoms (here at 0.5 cm voxels, 64^3), absorption energies 200 keV (e) / 50 keV
+    (gamma) and hard-event thresholds W_cc = 200 keV, W_cb = 50 keV."""
+    ph, beam = I.paper_preset(particle, kind)
+    ph = I.scaled(ph, 2)
+    D, S, Dr, Sr, st, tally, r = run_both(ocmc, ph, beam, n, orc=PAPER_CUTS, **PAPER_CUTS)
+    a = agreement(D, S, Dr, Sr)
+    print(particle, kind, a)
+    check_conservation(st)
+    assert st["histories"] == n
+    assert a["within3"] >= 0.99, a
+    assert abs(a["mean_signed"]) < 0.005, a
 
 
 def test_bit_reproducible_across_runs_and_launch_shapes(ocmc):

@@ -227,3 +227,32 @@ def test_denoise_fallback(ocmc):
         f = flag.cpu().numpy() == 1
         assert 0 < f.sum() < f.size and np.array_equal(f, expect)
         assert np.array_equal(out.cpu().numpy(), np.where(expect, D, r))
+
+
+def test_tensor_memory_wait_timeout_is_reported_and_recoverable(ocmc):
+    """The bounded waits of the tcgen05 convolution: the test hook makes one wait per block run
+    out (a barrier that nothing completes, 1 ms limit) after the block's first tile, so copies
+    and MMAs are in flight when it gives up. A training step (learning rate 0: the weights stay)
+    must return OCMC_ERR_TIMEOUT, and with the hook off the same network gives the same output
+    as before, bit for bit."""
+    import torch
+    shape = (64, 64, 64)
+    rng = np.random.default_rng(5)
+    dose = torch.from_numpy(rng.random(shape, dtype=np.float32)).cuda()
+    dens = torch.from_numpy(np.full(shape, 1.0, np.float32)).cuda()
+    net = ocmc.UNet(shape, seed=3)
+    out0 = torch.empty_like(dose)
+    net.forward(dose, dens, out0)
+    torch.cuda.synchronize()
+    try:
+        ocmc.unet_test_stall(1, 1_000_000)
+        with pytest.raises(ocmc.OcmcError) as x:
+            net.train_step(dose, dens, dose, 0.0)
+        assert x.value.status == ocmc.ERR_TIMEOUT
+    finally:
+        ocmc.unet_test_stall(-1, 0)
+    out2 = torch.empty_like(dose)
+    net.forward(dose, dens, out2)
+    torch.cuda.synchronize()
+    assert torch.equal(out0, out2)
+    net.close()
