@@ -41,7 +41,10 @@ typedef enum {
                             /* tally misses the dropped particles                 */
     OCMC_ERR_TIMEOUT = 5,   /* a particle exceeded the step limit or a sampling   */
                             /* loop its iteration limit; that particle was dropped*/
-    OCMC_ERR_STATE = 6      /* call out of order (no phantom, no source, ...)     */
+    OCMC_ERR_STATE = 6,     /* call out of order (no phantom, no source, ...)     */
+    OCMC_ERR_BOUNDS = 7     /* checks build only (libocmc_checks.so, built with   */
+                            /* -DOCMC_CHECKS=1): a voxel index, tally address or  */
+                            /* stack slot was out of range; the access was skipped*/
 } ocmc_status;
 
 /* Test modes of ocmc_params.flags (used by the physics tests, 0 in production). */
@@ -119,8 +122,11 @@ typedef struct {
     /* transport-kernel timing (device timer): warp lifetimes summed over warps; the part
      * of them after each warp found the source exhausted (work from its own stacks only);
      * for the transport launches since the last reset, first warp start to last warp end,
-     * and the earliest source exhaustion seen by a warp to the last warp end */
+     * and the earliest source exhaustion seen by a warp to the last warp end. With `warps`
+     * (warps launched), 1 - warp_ms / (warps * span_ms) is the share of warp slots left idle
+     * by warps that finished before the last one (the end-of-launch imbalance). */
     double warp_ms, tail_warp_ms, span_ms, tail_span_ms;
+    uint64_t warps;
 } ocmc_stats;
 
 /* Fill p with the defaults listed above. */

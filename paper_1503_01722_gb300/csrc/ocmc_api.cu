@@ -620,6 +620,7 @@ static ocmc_status check_err_flag(ocmc_ctx* c)
     int e = 0;
     CK(cudaMemcpy(&e, c->d_err, sizeof(int), cudaMemcpyDeviceToHost), "error flag");
     if (e & ERR_PHANTOM) return fail(c, OCMC_ERR_ARG, "phantom contains invalid values");
+    if (e & ERR_BOUNDS) return fail(c, OCMC_ERR_BOUNDS, "a bounds check failed (checks build); the access was skipped");
     if (e & ERR_OVERFLOW) return fail(c, OCMC_ERR_OVERFLOW, "a secondary stack overflowed; particles were dropped");
     if (e & ERR_LIMIT) return fail(c, OCMC_ERR_TIMEOUT, "a particle hit the step or sampling iteration limit");
     return OCMC_OK;
@@ -737,6 +738,7 @@ ocmc_status ocmc_get_stats(ocmc_ctx* c, ocmc_stats* out)
     out->e_trans = st[ST_E_TRANS] * S;
     out->e_dropped = st[ST_E_DROPPED] * S;
     out->warp_ms = st[ST_WARP_NS] * 1e-6;
+    out->warps = st[ST_WARPS];
     out->tail_warp_ms = st[ST_TAIL_NS] * 1e-6;
     if (st[ST_T_END]) {
         const unsigned long long t0 = ~st[ST_T_START_INV], ts = ~st[ST_T_SRC_INV];

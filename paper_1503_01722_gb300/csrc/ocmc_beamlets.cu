@@ -326,6 +326,7 @@ ocmc_status ocmc_run_beamlets(ocmc_ctx* c, uint64_t seed, void* stream)
     c->bl_ran = true;
     int e = 0;
     BCK(cudaMemcpy(&e, c->d_err, sizeof(int), cudaMemcpyDeviceToHost), "error flag");
+    if (e & ERR_BOUNDS) return ctx_fail(c, OCMC_ERR_BOUNDS, "a bounds check failed (checks build)");
     if (e & ERR_OVERFLOW) return ctx_fail(c, OCMC_ERR_OVERFLOW, "a secondary stack overflowed");
     if (e & ERR_LIMIT) return ctx_fail(c, OCMC_ERR_TIMEOUT, "a particle hit the step or sampling limit");
     return OCMC_OK;

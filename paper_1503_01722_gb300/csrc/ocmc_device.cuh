@@ -230,13 +230,14 @@ __device__ __forceinline__ void rotate(float& u, float& v, float& w, float mu, f
     float sp, cp;
     __sincosf(6.283185307179586f * xi, &sp, &cp);
     // sin of the polar angle of (u, v, w) from its own components: 1 - w^2 would cancel near
-    // the poles and give the frame a wrong scale there. Correctly rounded intrinsics: the
-    // compiler may not contract or approximate them differently in different instantiations of
-    // the transport kernel, which keeps the tally bit-identical across launch shapes.
-    float s = __fsqrt_rn(__fmaf_rn(u, u, __fmul_rn(v, v)));
+    // the poles and give the frame a wrong scale there. Explicitly rounded products and an
+    // explicit reciprocal square root: the compiler may not contract or rewrite them differently
+    // in different instantiations of the transport kernel, which keeps the tally bit-identical
+    // across launch shapes.
+    const float s2 = __fmaf_rn(u, u, __fmul_rn(v, v));
+    const float is = rsqrtf(s2), s = __fmul_rn(s2, is);
     float nu, nv, nw;
-    if (s > 1e-10f) {
-        float is = 1.f / s;
+    if (s2 > 1e-20f) {
         nu = u * mu + st * (u * w * cp - v * sp) * is;
         nv = v * mu + st * (v * w * cp + u * sp) * is;
         nw = w * mu - s * st * cp;

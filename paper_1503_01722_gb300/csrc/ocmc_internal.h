@@ -38,6 +38,13 @@ constexpr int FLAG_CROSS_VOXELS = 16;   // electron steps cross voxel faces (fix
 constexpr int ERR_OVERFLOW = 1;
 constexpr int ERR_LIMIT = 2;
 constexpr int ERR_PHANTOM = 4;
+constexpr int ERR_BOUNDS = 8;     // a bounds check of the checks build failed (the access was skipped)
+
+// Checks build (-DOCMC_CHECKS=1): voxel indices, tally addresses and stack slots are checked
+// before use; a failure sets ERR_BOUNDS and the access is skipped. Off in the normal build.
+#ifndef OCMC_CHECKS
+#define OCMC_CHECKS 0
+#endif
 
 // run statistics slots (uint64, device)
 enum Stat {
@@ -50,7 +57,7 @@ enum Stat {
     // after the warp saw the source exhausted, and (max-reduced, written directly) the bitwise
     // complement of the earliest warp start and of the earliest source exhaustion, and the
     // latest warp end
-    ST_WARP_NS, ST_TAIL_NS, ST_T_START_INV, ST_T_SRC_INV, ST_T_END,
+    ST_WARP_NS, ST_TAIL_NS, ST_T_START_INV, ST_T_SRC_INV, ST_T_END, ST_WARPS,
     ST_COUNT
 };
 

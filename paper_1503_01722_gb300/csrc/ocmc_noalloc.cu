@@ -278,6 +278,7 @@ extern "C" ocmc_status ocmc_run_noalloc(int device, int nx, int ny, int nz, cons
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return M.cuda(e, "transport");
     if (flag & ERR_PHANTOM) return M.fail(OCMC_ERR_ARG, "phantom contains invalid values");
+    if (flag & ERR_BOUNDS) return M.fail(OCMC_ERR_BOUNDS, "a bounds check failed (checks build)");
     if (flag & ERR_OVERFLOW) return M.fail(OCMC_ERR_OVERFLOW, "a secondary stack overflowed; particles were dropped");
     if (flag & ERR_LIMIT) return M.fail(OCMC_ERR_TIMEOUT, "a particle hit the step or sampling iteration limit");
     return OCMC_OK;

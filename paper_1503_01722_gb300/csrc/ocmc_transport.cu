@@ -52,6 +52,20 @@ struct CtxT {
 template <class C>
 __device__ __forceinline__ void stat_add(C& c, int k, unsigned long long v) { atomicAdd(c.st + k, v); }
 
+// Checks build: a lane whose voxel index lies outside the grid flags ERR_BOUNDS (and its
+// particle is ended by the caller before any access). Always false in the normal build.
+template <class C>
+__device__ __forceinline__ bool vox_bad(const C& c, const Lane& p)
+{
+    if constexpr (OCMC_CHECKS) {
+        if (p.ix < 0 || p.iy < 0 || p.iz < 0 || p.ix >= c.a.nx || p.iy >= c.a.ny || p.iz >= c.a.nz) {
+            atomicOr(c.a.err, ERR_BOUNDS);
+            return true;
+        }
+    }
+    return false;
+}
+
 // Stack of a waiting charged particle: 1, or 2 below the energy-class boundary (e_split is 0
 // when the warps keep a single charged stack, so that everything then goes to stack 1).
 __device__ __forceinline__ int charged_stack(const TransportArgs& a, float E) { return E < a.e_split ? 2 : 1; }
@@ -95,6 +109,13 @@ __device__ __forceinline__ void deposit(C& c, const Lane& p, int ix, int iy, int
 {
     if (dE > 0.f) {
         const int v = ix + c.a.nx * (iy + c.a.ny * iz);     // grids have at most 1024^3 voxels
+        if constexpr (OCMC_CHECKS) {
+            if (ix < 0 || iy < 0 || iz < 0 || ix >= c.a.nx || iy >= c.a.ny || iz >= c.a.nz ||
+                (!C::beamlets && (p.batch < 0 || p.batch >= c.a.pp.n_batches))) {
+                atomicOr(c.a.err, ERR_BOUNDS);
+                return;
+            }
+        }
         if constexpr (C::beamlets) hash_add(c.a, p.r.h1 & ~BL_TAG, (uint32_t)v, fx(dE));
         else atomicAdd(c.a.tally + (long long)p.batch * c.a.nvox + v, fx(dE));
     }
@@ -140,6 +161,13 @@ __device__ __forceinline__ void push_lane(C& c, int t, const Lane& p)
 template <class C>
 __device__ __forceinline__ void pop_lane(const C& c, int t, int slot, Lane& p)
 {
+    if constexpr (OCMC_CHECKS) {
+        if (slot < 0 || slot >= c.a.cap || t < 0 || t >= c.a.nstk) {
+            atomicOr(c.a.err, ERR_BOUNDS);
+            slot = 0;
+            t = 0;
+        }
+    }
     const uint4* q = reinterpret_cast<const uint4*>(c.stk + (size_t)t * c.a.cap + slot);
     uint4 a = q[0], b = q[1], d = q[2];
     p.x = __uint_as_float(a.x); p.y = __uint_as_float(a.y); p.z = __uint_as_float(a.z); p.E = __uint_as_float(a.w);
@@ -336,6 +364,7 @@ __device__ __forceinline__ bool charged_step(C& c, Lane& p, unsigned& n_hfict)
     const TransportArgs& a = c.a;
     const SmemTables& T = c.T;
     const uint32_t k0 = a.key0, k1 = a.key1;
+    if (vox_bad(c, p)) return false;
     const int vox = p.ix + a.nx * (p.iy + a.ny * p.iz);
     float rho = __ldg(a.density + vox);
     int m = __ldg(a.material + vox);
@@ -444,6 +473,7 @@ __device__ __forceinline__ int cross_segment(C& c, Lane& p, float L, float Ef, f
     float left = L, moved = 0.f;
     for (int guard = 0; left > 0.f; ++guard) {
         if (guard > 4 * (a.nx + a.ny + a.nz)) { c.ok = false; break; }   // cannot happen: bounded crossings
+        if (vox_bad(c, p)) { *done = moved; return SEG_OUT; }
         const int vox = p.ix + a.nx * (p.iy + a.ny * p.iz);
         const float rho = __ldg(a.density + vox);
         const int m = __ldg(a.material + vox);
@@ -481,6 +511,7 @@ __device__ __forceinline__ bool charged_step_cross(C& c, Lane& p, unsigned& n_hf
     const TransportArgs& a = c.a;
     const SmemTables& T = c.T;
     const uint32_t k0 = a.key0, k1 = a.key1;
+    if (vox_bad(c, p)) return false;
     const int vox = p.ix + a.nx * (p.iy + a.ny * p.iz);
     const float rho0 = __ldg(a.density + vox);
     const int m0 = __ldg(a.material + vox);
@@ -524,6 +555,7 @@ __device__ __forceinline__ bool charged_step_cross(C& c, Lane& p, unsigned& n_hf
     if (r == SEG_OUT) return false;
     if (r == SEG_FLOOR || lim != 3) return true;
     // candidate hard event where the step ended
+    if (vox_bad(c, p)) return false;
     const int v2 = p.ix + a.nx * (p.iy + a.ny * p.iz);
     const float rho = __ldg(a.density + v2);
     const int m = __ldg(a.material + v2);
@@ -712,6 +744,7 @@ __global__ void __maxnreg__(NREG) k_transport(const __grid_constant__ TransportA
         const unsigned long long t_end = globaltimer_ns(), t0 = s_time[wib][0];
         const unsigned long long ts = s_time[wib][1] ? s_time[wib][1] : t0;
         atomicAdd(s_st + ST_WARP_NS, t_end - t0);
+        atomicAdd(s_st + ST_WARPS, 1ull);
         atomicAdd(s_st + ST_TAIL_NS, t_end - ts);
         atomicMax(a.stats + ST_T_START_INV, ~t0);
         atomicMax(a.stats + ST_T_SRC_INV, ~ts);

@@ -188,8 +188,8 @@ def _cases(seeds, shape, voxel, workers=8):
         return list(ex.map(lambda s: inputs.denoiser_case(s, shape, voxel), seeds))
 
 
-def run_study(n_train=200, n_eval=8, lows=(10**5, 10**6, 10**7), n_high=10**8,
-              n_ref=(2 * 10**9, 3 * 10**8), steps=12000, lr=5e-4, shape=(128, 128, 128),
+def run_study(n_train=200, n_eval=8, lows=(10**5, 10**6, 10**7), n_high=10**9,
+              n_ref=(10**10, 10**9), steps=12000, lr=5e-4, shape=(128, 128, 128),
               voxel=(0.25, 0.25, 0.25), target=0.01, k_sigma=4.0, device=0, seed=1, log=print,
               weights_out=None, warmup=300, flips=True):
     """Generate training pairs on random cases, train the network, then on held-out cases
@@ -307,7 +307,9 @@ def main(argv=None):
     ap.add_argument("--eval", type=int, default=8)
     ap.add_argument("--steps", type=int, default=12000)
     ap.add_argument("--no-flips", action="store_true", help="train without mirrored copies of the pairs")
-    ap.add_argument("--n-high", type=float, default=1e8)
+    ap.add_argument("--n-high", type=float, default=1e9, help="histories of each training target")
+    ap.add_argument("--n-ref-photon", type=float, default=1e10, help="histories of a photon case's judge")
+    ap.add_argument("--n-ref-electron", type=float, default=1e9, help="histories of an electron case's judge")
     ap.add_argument("--grid", type=int, default=128)
     ap.add_argument("--voxel", type=float, default=0.25)
     ap.add_argument("--lr", type=float, default=5e-4)
@@ -321,6 +323,7 @@ def main(argv=None):
         print(json.dumps({"grid": g, "train_step_ms": time_training((g, g, g), steps=a.time_steps)}))
         return
     rep = run_study(n_train=a.train, n_eval=a.eval, n_high=int(a.n_high), steps=a.steps, lr=a.lr, flips=not a.no_flips,
+                    n_ref=(int(a.n_ref_photon), int(a.n_ref_electron)),
                     shape=(g, g, g), voxel=(a.voxel,) * 3, weights_out=a.weights_out,
                     log=lambda m: print(m, flush=True))
     s = json.dumps(rep)

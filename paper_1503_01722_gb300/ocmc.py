@@ -12,9 +12,11 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_LIB_PATH = os.path.join(_HERE, "libocmc.so")
+# OCMC_CHECKS=1 selects the checks build (bounds checks on voxel indices, tally addresses and
+# stack slots; build it with paper_1503_01722_gb300.build.build(checks=True))
+_LIB_PATH = os.path.join(_HERE, "libocmc_checks.so" if os.environ.get("OCMC_CHECKS") == "1" else "libocmc.so")
 
-OK, ERR_ARG, ERR_CUDA, ERR_OOM, ERR_OVERFLOW, ERR_TIMEOUT, ERR_STATE = range(7)
+OK, ERR_ARG, ERR_CUDA, ERR_OOM, ERR_OVERFLOW, ERR_TIMEOUT, ERR_STATE, ERR_BOUNDS = range(8)
 FLAG_NO_HARD, FLAG_NO_MS, FLAG_KILL_FIRST_REAL, FLAG_KERMA, FLAG_CROSS_VOXELS = 1, 2, 4, 8, 16
 TALLY_SCALE = 2.0 ** 28
 
@@ -52,7 +54,7 @@ class Stats(C.Structure):
         "majorant_violations", "dropped", "transmitted", "warp_iterations", "lane_steps")] + \
         [(n, C.c_double) for n in ("e_in", "e_dep", "e_esc", "e_miss", "pair_mass", "annih_mass", "e_killed",
                                    "e_trans", "e_dropped", "last_run_ms", "warp_ms", "tail_warp_ms", "span_ms",
-                                   "tail_span_ms")]
+                                   "tail_span_ms")] + [("warps", C.c_uint64)]
 
 
 def _load():
