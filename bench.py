@@ -398,7 +398,6 @@ def denoiser_record(args, peaks):
     trained by `python -m paper_1503_01722_gb300.denoiser`, weights committed with the package),
     each judged by a long plain run (10^10 histories for photons, 10^9 for electrons) whose own
     error is reported; plus the inference time and the dominant layer's tensor roofline."""
-    import math
     import torch
     from paper_1503_01722_gb300 import denoiser as D
     from paper_1503_01722_gb300 import ocmc
@@ -442,17 +441,9 @@ def denoiser_record(args, peaks):
         dom = max(layers, key=lambda r: r[4])
         peak = peaks.get("bf16_tflops")
         for k, (ph, beam) in zip(ks, cases):
-            eng.create_phantom(ph)
-            eng.set_source(beam)
-            eng.reset()
             nr = args.judge_photon if beam.particle == 0 else args.judge_electron
-            eng.run(int(nr), seed=99_991 + k)
-            ref = torch.empty(shape, dtype=torch.float32, device=dev)
-            sig = torch.empty_like(ref)
-            eng.dose(out=(ref, sig))
-            m = ref.max()
-            sel = ref >= 0.1 * m
-            judge_err = float(sig[sel].mean() / m * math.sqrt(2 / math.pi))
+            # the judge: 1e10 / 1e9 histories, more if its own error estimate is above 0.1 %
+            ref, judge_err, nr = D.judge(eng, ph, beam, int(nr), 99_991 + k, shape, max_err=1e-3, n_cap=5 * 10**10)
             r = D.time_to_error(eng, net, ph, beam, ref, target=0.01, k_sigma=4.0, seed=31 + k, device=0)
             row = {"case": k, "particle": "photon" if beam.particle == 0 else "electron",
                    "energy_MeV": "6MV" if beam.particle == 0 else round(float(beam.edges[0]), 2),

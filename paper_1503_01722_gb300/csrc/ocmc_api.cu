@@ -192,7 +192,16 @@ void launch_shape(const ocmc_ctx* c, int* threads, int* blocks, int* cap, int* n
     *nreg = c->p.max_registers ? c->p.max_registers : 64;
     *threads = c->p.block_threads ? c->p.block_threads : (*nreg == 64 ? 1024 : *nreg == 56 ? 384 : 256);
     size_t smem = transport_smem_bytes(c->t.n_mat);
-    int bps = c->p.blocks_per_sm ? c->p.blocks_per_sm : transport_max_blocks_per_sm(*threads, smem, *nreg);
+    int bps = c->p.blocks_per_sm;
+    if (!bps) {
+        if (c->occ_threads != *threads || c->occ_nreg != *nreg || c->occ_smem != smem) {
+            c->occ_bps = transport_max_blocks_per_sm(*threads, smem, *nreg);
+            c->occ_threads = *threads;
+            c->occ_nreg = *nreg;
+            c->occ_smem = smem;
+        }
+        bps = c->occ_bps;
+    }
     if (bps < 1) bps = 1;
     *blocks = c->sms * bps;
     *cap = c->p.stack_capacity ? c->p.stack_capacity : 8192;
@@ -590,6 +599,7 @@ ocmc_status ocmc_run_range(ocmc_ctx* c, uint64_t first, uint64_t count, uint64_t
     a.n_total = n_total;
     a.key0 = (uint32_t)seed;
     a.key1 = (uint32_t)(seed >> 32);
+    a.rk = round_keys(seed);
     a.stacks = c->d_stacks;
     a.cap = cap;
     a.nstk = nstk;
@@ -834,6 +844,7 @@ ocmc_status ocmc_test_source(ocmc_ctx* c, uint64_t n_total, uint64_t first, uint
     if (c->src_kind == 0) stratify(c, n_total, a.src);
     a.key0 = (uint32_t)seed;
     a.key1 = (uint32_t)(seed >> 32);
+    a.rk = round_keys(seed);
     float* d = nullptr;
     CK(cudaMalloc(&d, sizeof(float) * 8 * count), "allocation");
     cudaError_t e = launch_test_source(a, n_total, first, count, d, nullptr);
@@ -857,6 +868,7 @@ ocmc_status ocmc_test_sample(ocmc_ctx* c, int kind, int m, float E, float aux, u
     fill_args(c, a);
     a.key0 = (uint32_t)seed;
     a.key1 = (uint32_t)(seed >> 32);
+    a.rk = round_keys(seed);
     float* d = nullptr;
     CK(cudaMalloc(&d, sizeof(float) * n), "allocation");
     cudaError_t e = launch_test_sample(a, kind, m, E, aux, n, d, nullptr);

@@ -9,6 +9,10 @@
 struct ocmc_ctx {
     int device = 0;
     int sms = 0;
+    // blocks per SM of the last launch shape asked for (the occupancy query costs host time on
+    // every run otherwise)
+    mutable int occ_threads = -1, occ_nreg = -1, occ_bps = 0;
+    mutable size_t occ_smem = 0;
     ocmc_params p{};
     std::string err;
     // phantom

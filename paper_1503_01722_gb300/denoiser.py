@@ -188,68 +188,96 @@ def _cases(seeds, shape, voxel, workers=8):
         return list(ex.map(lambda s: inputs.denoiser_case(s, shape, voxel), seeds))
 
 
+def judge(engine, ph, beam, n_ref, seed, shape, device=0, max_err=None, n_cap=2 * 10**11):
+    """The reference dose of one case: plain MC at n_ref histories; with max_err, more
+    histories (independent seeds, accumulated in the same tally) until the judge's own error
+    estimate (mean sigma / max over the 10 % isodose, times sqrt(2/pi)) is at most max_err, or
+    n_cap. Returns (reference dose, its error estimate, histories)."""
+    dev = torch.device("cuda", device)
+    engine.create_phantom(ph)
+    engine.set_source(beam)
+    engine.reset()
+    done, k = 0, 0
+    want = int(n_ref)
+    while True:
+        engine.run(want - done, seed=seed + 7919 * k)
+        done, k = want, k + 1
+        ref = torch.empty(shape, dtype=torch.float32, device=dev)
+        sig = torch.empty_like(ref)
+        engine.dose(out=(ref, sig))
+        m = ref.max()
+        sel = ref >= 0.1 * m
+        err = float(sig[sel].mean() / m * math.sqrt(2 / math.pi))
+        if max_err is None or err <= max_err or done >= n_cap:
+            return ref, err, done
+        want = min(n_cap, int(math.ceil(done * (err / max_err) ** 2 * 1.1)))
+
+
+def train_on_cases(eng, net, cases, lows, n_high, steps, lr, warmup, seed, flips, shape, device, log, rep):
+    """Training data from the engine (several input noise levels per case, one target of
+    n_high histories), then Adam on the network; timings and losses go into rep."""
+    dev = torch.device("cuda", device)
+    t0 = time.perf_counter()
+    pairs = []
+    for k, (ph, beam) in enumerate(cases):
+        eng.create_phantom(ph)
+        eng.set_source(beam)
+        dens = torch.from_numpy(np.ascontiguousarray(ph.density)).to(dev)
+        eng.reset()
+        eng.run(n_high, seed=7 * k + seed)
+        high = _dose(eng, shape, dev)
+        for j, n in enumerate(lows):
+            eng.reset()
+            eng.run(n, seed=7 * k + seed + 1 + j)
+            low, low_sigma = _dose_sigma(eng, shape, dev)
+            pairs.append((low, low_sigma, dens, high))
+        if (k + 1) % 25 == 0:
+            log(f"pairs: case {k + 1}/{len(cases)} ({time.perf_counter() - t0:.0f} s)")
+    torch.cuda.synchronize()
+    rep["t_pairs_s"] = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    losses = train(net, pairs, steps, lr=lr, warmup=warmup, seed=seed, log_every=max(steps // 10, 1), log=log,
+                   flips=flips)
+    torch.cuda.synchronize()
+    rep["t_train_s"] = time.perf_counter() - t0
+    rep["loss_first_100"] = float(np.mean(losses[:100]))
+    rep["loss_last_100"] = float(np.mean(losses[-100:]))
+
+
 def run_study(n_train=200, n_eval=8, lows=(10**5, 10**6, 10**7), n_high=10**9,
               n_ref=(10**10, 10**9), steps=12000, lr=5e-4, shape=(128, 128, 128),
               voxel=(0.25, 0.25, 0.25), target=0.01, k_sigma=4.0, device=0, seed=1, log=print,
-              weights_out=None, warmup=300, flips=True):
+              weights_out=None, warmup=300, flips=True, weights_in=None, judge_max_err=None):
     """Generate training pairs on random cases, train the network, then on held-out cases
     compare plain and denoised Monte Carlo by the wall time each needs to reach `target`
-    against a reference of n_ref histories (photon, electron beams). Returns a report dict."""
-    dev = torch.device("cuda", device)
+    against a reference of n_ref histories (photon, electron beams; with judge_max_err, more
+    until the reference's own error estimate is at most that). With weights_in the training is
+    skipped and the given weights are evaluated. Returns a report dict."""
     t0 = time.perf_counter()
-    train_cases = _cases([100_000 + seed * 10_000 + k for k in range(n_train)], shape, voxel)
+    train_cases = [] if weights_in is not None else _cases([100_000 + seed * 10_000 + k for k in range(n_train)],
+                                                            shape, voxel)
     eval_cases = _cases([900_000 + seed * 10_000 + k for k in range(n_eval)], shape, voxel)
     t_cases = time.perf_counter() - t0
     eng = ocmc.Engine(device)
     net = ocmc.UNet(shape, device=device, seed=seed)
     rep = {"shape": list(shape), "voxel_cm": list(voxel), "n_train": n_train, "n_eval": n_eval,
            "lows": list(lows), "n_high": n_high, "n_ref": list(n_ref), "steps": steps, "flips": flips, "target": target,
-           "k_sigma": k_sigma, "t_case_generation_s": t_cases}
+           "k_sigma": k_sigma, "t_case_generation_s": t_cases, "judge_max_err": judge_max_err,
+           "weights_in": weights_in}
     try:
-        # training data: several input noise levels per case, one target
-        t0 = time.perf_counter()
-        pairs = []
-        for k, (ph, beam) in enumerate(train_cases):
-            eng.create_phantom(ph)
-            eng.set_source(beam)
-            dens = torch.from_numpy(np.ascontiguousarray(ph.density)).to(dev)
-            eng.reset()
-            eng.run(n_high, seed=7 * k + seed)
-            high = _dose(eng, shape, dev)
-            for j, n in enumerate(lows):
-                eng.reset()
-                eng.run(n, seed=7 * k + seed + 1 + j)
-                low, low_sigma = _dose_sigma(eng, shape, dev)
-                pairs.append((low, low_sigma, dens, high))
-            if (k + 1) % 25 == 0:
-                log(f"pairs: case {k + 1}/{n_train} ({time.perf_counter() - t0:.0f} s)")
-        torch.cuda.synchronize()
-        rep["t_pairs_s"] = time.perf_counter() - t0
-        t0 = time.perf_counter()
-        losses = train(net, pairs, steps, lr=lr, warmup=warmup, seed=seed, log_every=max(steps // 10, 1), log=log,
-                       flips=flips)
-        torch.cuda.synchronize()
-        rep["t_train_s"] = time.perf_counter() - t0
-        rep["loss_first_100"] = float(np.mean(losses[:100]))
-        rep["loss_last_100"] = float(np.mean(losses[-100:]))
-        del pairs
-        if weights_out:
-            np.save(weights_out, net.params())
+        if weights_in is not None:
+            net.set_params(np.load(weights_in))
+        else:
+            train_on_cases(eng, net, train_cases, lows, n_high, steps, lr, warmup, seed, flips, shape, device, log,
+                           rep)
+            if weights_out:
+                np.save(weights_out, net.params())
         # evaluation on held-out cases
         rows = []
         for k, (ph, beam) in enumerate(eval_cases):
-            eng.create_phantom(ph)
-            eng.set_source(beam)
-            eng.reset()
-            nr = n_ref[0] if beam.particle == 0 else n_ref[1]
             t1 = time.perf_counter()
-            eng.run(nr, seed=99_991 + k)
-            ref = _dose(eng, shape, dev)
-            sig = torch.empty_like(ref)
-            eng.dose(out=(ref, sig))
-            m = ref.max()
-            sel = ref >= 0.1 * m
-            ref_err = float(sig[sel].mean() / m * math.sqrt(2 / math.pi))
+            ref, ref_err, nr = judge(eng, ph, beam, n_ref[0] if beam.particle == 0 else n_ref[1], 99_991 + k,
+                                     shape, device=device, max_err=judge_max_err)
             t_ref = time.perf_counter() - t1
             r = time_to_error(eng, net, ph, beam, ref, target=target, k_sigma=k_sigma, seed=31 + k,
                               device=device)
@@ -261,7 +289,8 @@ def run_study(n_train=200, n_eval=8, lows=(10**5, 10**6, 10**7), n_high=10**9,
             if r["plain"] and r["denoised"]:
                 row["speedup"] = r["plain"]["time_s"] / r["denoised"]["time_s"]
             rows.append(row)
-            log(f"eval {k}: {row['particle']} field {row['field_cm']} plain {r['plain']} denoised {r['denoised']}")
+            log(f"eval {k}: {row['particle']} field {row['field_cm']} judge {nr:.2e} ({100 * ref_err:.3f} %) "
+                f"plain {r['plain']} denoised {r['denoised']}")
         rep["cases"] = rows
         tp = [r["plain"]["time_s"] for r in rows if r["plain"]]
         td = [r["denoised"]["time_s"] for r in rows if r["denoised"]]
@@ -314,6 +343,9 @@ def main(argv=None):
     ap.add_argument("--voxel", type=float, default=0.25)
     ap.add_argument("--lr", type=float, default=5e-4)
     ap.add_argument("--weights-out", default=None)
+    ap.add_argument("--weights-in", default=None, help="evaluate these weights (.npy) instead of training")
+    ap.add_argument("--judge-max-err", type=float, default=None,
+                    help="raise a judge's histories until its own error estimate is at most this (e.g. 0.001)")
     ap.add_argument("--report", default=None)
     ap.add_argument("--time-steps", type=int, default=0,
                     help="only time this many training steps on synthetic input (after two warm-up steps)")
@@ -323,7 +355,8 @@ def main(argv=None):
         print(json.dumps({"grid": g, "train_step_ms": time_training((g, g, g), steps=a.time_steps)}))
         return
     rep = run_study(n_train=a.train, n_eval=a.eval, n_high=int(a.n_high), steps=a.steps, lr=a.lr, flips=not a.no_flips,
-                    n_ref=(int(a.n_ref_photon), int(a.n_ref_electron)),
+                    n_ref=(int(a.n_ref_photon), int(a.n_ref_electron)), weights_in=a.weights_in,
+                    judge_max_err=a.judge_max_err,
                     shape=(g, g, g), voxel=(a.voxel,) * 3, weights_out=a.weights_out,
                     log=lambda m: print(m, flush=True))
     s = json.dumps(rep)
