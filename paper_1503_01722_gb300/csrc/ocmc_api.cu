@@ -599,7 +599,6 @@ ocmc_status ocmc_run_range(ocmc_ctx* c, uint64_t first, uint64_t count, uint64_t
     a.n_total = n_total;
     a.key0 = (uint32_t)seed;
     a.key1 = (uint32_t)(seed >> 32);
-    a.rk = round_keys(seed);
     a.stacks = c->d_stacks;
     a.cap = cap;
     a.nstk = nstk;
@@ -844,7 +843,6 @@ ocmc_status ocmc_test_source(ocmc_ctx* c, uint64_t n_total, uint64_t first, uint
     if (c->src_kind == 0) stratify(c, n_total, a.src);
     a.key0 = (uint32_t)seed;
     a.key1 = (uint32_t)(seed >> 32);
-    a.rk = round_keys(seed);
     float* d = nullptr;
     CK(cudaMalloc(&d, sizeof(float) * 8 * count), "allocation");
     cudaError_t e = launch_test_source(a, n_total, first, count, d, nullptr);
@@ -868,7 +866,6 @@ ocmc_status ocmc_test_sample(ocmc_ctx* c, int kind, int m, float E, float aux, u
     fill_args(c, a);
     a.key0 = (uint32_t)seed;
     a.key1 = (uint32_t)(seed >> 32);
-    a.rk = round_keys(seed);
     float* d = nullptr;
     CK(cudaMalloc(&d, sizeof(float) * n), "allocation");
     cudaError_t e = launch_test_sample(a, kind, m, E, aux, n, d, nullptr);

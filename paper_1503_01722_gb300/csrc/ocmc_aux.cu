@@ -42,12 +42,12 @@ __global__ void k_finalize(const long long* __restrict__ tally, const float* __r
     }
 }
 
-__global__ void k_test_philox(const RoundKeys K, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t first,
+__global__ void k_test_philox(uint32_t k0, uint32_t k1, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t first,
                               uint32_t n, uint32_t* out)
 {
     uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n) return;
-    uint4 r = philox4x32_10(make_uint4(first + j, c1, c2, c3), K);
+    uint4 r = philox4x32_10(make_uint4(first + j, c1, c2, c3), k0, k1);
     out[4 * j] = r.x;
     out[4 * j + 1] = r.y;
     out[4 * j + 2] = r.z;
@@ -89,10 +89,10 @@ __global__ void k_test_sample(const TransportArgs a, int kind, int m, float E, f
         r.h0 = (uint32_t)j; r.h1 = (uint32_t)(j >> 32); r.sub = 0x5A5Au + (uint32_t)kind; r.n = 0; r.blk = 0xFFFFFFFFu;
         bool ok = true;
         float v = 0.f, eps;
-        if (kind == 0) v = sample_compton(E, r, a.rk, &eps, &ok);
-        else if (kind == 1) v = sample_moller(E, a.pp.w_cc, r, a.rk, &ok);
-        else if (kind == 2) v = sample_brems(E, a.pp.w_cb, T.msc[m * MS1], T.msc[m * MS1 + 1], r, a.rk, &ok);
-        else if (kind == 3) v = sample_ms(T, aux, r, a.rk);
+        if (kind == 0) v = sample_compton(E, r, a.key0, a.key1, &eps, &ok);
+        else if (kind == 1) v = sample_moller(E, a.pp.w_cc, r, a.key0, a.key1, &ok);
+        else if (kind == 2) v = sample_brems(E, a.pp.w_cb, T.msc[m * MS1], T.msc[m * MS1 + 1], r, a.key0, a.key1, &ok);
+        else if (kind == 3) v = sample_ms(T, aux, r, a.key0, a.key1);
         out[j] = ok ? v : __int_as_float(0x7FC00000);
     }
 }
@@ -316,8 +316,7 @@ cudaError_t launch_finalize(const long long* tally, const float* density, int B,
 cudaError_t launch_test_philox(uint32_t key0, uint32_t key1, uint32_t c1, uint32_t c2, uint32_t c3,
                                uint32_t first_block, uint32_t n_blocks, uint32_t* out, cudaStream_t s)
 {
-    k_test_philox<<<(n_blocks + 255) / 256, 256, 0, s>>>(round_keys(((uint64_t)key1 << 32) | key0), c1, c2, c3,
-                                                         first_block, n_blocks, out);
+    k_test_philox<<<(n_blocks + 255) / 256, 256, 0, s>>>(key0, key1, c1, c2, c3, first_block, n_blocks, out);
     return cudaGetLastError();
 }
 

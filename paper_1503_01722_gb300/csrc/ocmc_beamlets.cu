@@ -95,7 +95,6 @@ ocmc_status beamlet_args(ocmc_ctx* c, unsigned long long total, uint64_t seed, T
     a.n_total = total;
     a.key0 = (uint32_t)seed;
     a.key1 = (uint32_t)(seed >> 32);
-    a.rk = round_keys(seed);
     a.stream_tag = 0;
     a.beamlets = c->d_bl;
     a.bl_prefix = c->d_bl_prefix;

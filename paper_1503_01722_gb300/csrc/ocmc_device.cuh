@@ -7,16 +7,15 @@
 namespace ocmc {
 
 // ---- Philox4x32-10 (Salmon et al. 2011) -----------------------------------------------
-// Ten rounds of the multiply/XOR bijection on the counter c, round r keyed by (K.r0[r], K.r1[r])
-// (RoundKeys: the seed's Weyl sequence, precomputed on the host). When K is the kernel's
-// parameter, every key is a constant-bank operand of the XOR and no key addition is executed.
-__device__ __forceinline__ uint4 philox4x32_10(uint4 c, const RoundKeys& K)
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1)
 {
 #pragma unroll
     for (int r = 0; r < 10; ++r) {
         uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
         uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
-        c = make_uint4(hi1 ^ c.y ^ K.r0[r], lo1, hi0 ^ c.w ^ K.r1[r], lo0);
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
     }
     return c;
 }
@@ -32,27 +31,27 @@ struct Rng {
 
 // One out-of-line copy of the generator for draws beyond a step's first block:
 // call sites stay small, so the transport kernel's code fits the instruction cache.
-static __device__ __noinline__ uint4 philox_block(uint32_t b, uint32_t h0, uint32_t h1, uint32_t sub, const RoundKeys& K)
+static __device__ __noinline__ uint4 philox_block(uint32_t b, uint32_t h0, uint32_t h1, uint32_t sub, uint32_t k0, uint32_t k1)
 {
-    return philox4x32_10(make_uint4(b, h0, h1, sub), K);
+    return philox4x32_10(make_uint4(b, h0, h1, sub), k0, k1);
 }
 
 // Every transport step starts on a fresh block: n is rounded up to a multiple of 4
 // and that block is generated by all lanes of the warp together (no divergence for
 // the first four draws of a step). The rounding depends only on the particle's own
 // step sequence, so streams stay independent of scheduling.
-__device__ __forceinline__ void rng_step_start(Rng& r, const RoundKeys& K)
+__device__ __forceinline__ void rng_step_start(Rng& r, uint32_t k0, uint32_t k1)
 {
     r.n = (r.n + 3u) & ~3u;
     r.blk = r.n >> 2;
-    r.buf = philox4x32_10(make_uint4(r.blk, r.h0, r.h1, r.sub), K);
+    r.buf = philox4x32_10(make_uint4(r.blk, r.h0, r.h1, r.sub), k0, k1);
 }
 
-__device__ __forceinline__ float rng_u(Rng& r, const RoundKeys& K)
+__device__ __forceinline__ float rng_u(Rng& r, uint32_t k0, uint32_t k1)
 {
     uint32_t b = r.n >> 2;
     if (b != r.blk) {
-        r.buf = philox_block(b, r.h0, r.h1, r.sub, K);
+        r.buf = philox_block(b, r.h0, r.h1, r.sub, k0, k1);
         r.blk = b;
     }
     uint32_t i = r.n & 3u;
@@ -138,7 +137,7 @@ constexpr float MC2F = 0.51099895f;
 // Compton scattering: eps = E'/E from the Klein-Nishina cross section by the
 // Butcher-Messel decomposition (1/eps and eps envelopes with the rejection
 // factor 1 - eps sin^2 / (1 + eps^2)). Returns cos(theta); *eps_out = E'/E.
-__device__ __forceinline__ float sample_compton(float E, Rng& r, const RoundKeys& K, float* eps_out, bool* ok)
+__device__ __forceinline__ float sample_compton(float E, Rng& r, uint32_t k0, uint32_t k1, float* eps_out, bool* ok)
 {
     float k = E / MC2F;
     float e0 = 1.f / (1.f + 2.f * k);
@@ -146,7 +145,7 @@ __device__ __forceinline__ float sample_compton(float E, Rng& r, const RoundKeys
     float a2 = 0.5f * (1.f - e0 * e0);
     float eps = 1.f, t = 0.f;
     for (int it = 0; it < SAMPLE_LIMIT; ++it) {
-        float r1 = rng_u(r, K), r2 = rng_u(r, K), r3 = rng_u(r, K);
+        float r1 = rng_u(r, k0, k1), r2 = rng_u(r, k0, k1), r3 = rng_u(r, k0, k1);
         if (r1 * (a1 + a2) < a1) eps = __expf(-a1 * r2);
         else eps = sqrtf(e0 * e0 + (1.f - e0 * e0) * r2);
         eps = fminf(fmaxf(eps, e0), 1.f);
@@ -165,13 +164,13 @@ __device__ __forceinline__ float sample_compton(float E, Rng& r, const RoundKeys
 
 // Moller: eps = W/T on [w_cc/T, 1/2] from the 1/eps^2 envelope, accepted with
 // g(eps) / (2 + c/4), g = 1 + (eps/(1-eps))^2 + c eps^2 - d eps/(1-eps).
-__device__ __forceinline__ float sample_moller(float T, float wcc, Rng& r, const RoundKeys& K, bool* ok)
+__device__ __forceinline__ float sample_moller(float T, float wcc, Rng& r, uint32_t k0, uint32_t k1, bool* ok)
 {
     float tau = T / MC2F, g = tau + 1.f;
     float c = (tau / g) * (tau / g), d = (2.f * tau + 1.f) / (g * g);
     float e0 = wcc / T, gmax = 2.f + 0.25f * c;
     for (int it = 0; it < SAMPLE_LIMIT; ++it) {
-        float r1 = rng_u(r, K), r2 = rng_u(r, K);
+        float r1 = rng_u(r, k0, k1), r2 = rng_u(r, k0, k1);
         float eps = e0 / (1.f - r1 * (1.f - 2.f * e0));
         eps = fminf(fmaxf(eps, e0), 0.5f);
         float q = eps / (1.f - eps);
@@ -184,13 +183,13 @@ __device__ __forceinline__ float sample_moller(float T, float wcc, Rng& r, const
 
 // Bremsstrahlung photon energy on [w_cb, T] from the 1/k envelope, accepted with
 // [(4/3 - 4/3 y + y^2) S1 + (1 - y) S2] / (4/3 S1 + S2), y = k / (T + mc^2).
-__device__ __forceinline__ float sample_brems(float T, float wcb, float S1, float S2, Rng& r, const RoundKeys& K,
+__device__ __forceinline__ float sample_brems(float T, float wcb, float S1, float S2, Rng& r, uint32_t k0, uint32_t k1,
                                               bool* ok)
 {
     float E = T + MC2F, lr = __logf(T / wcb);
     float gmax = (4.f / 3.f) * S1 + S2;
     for (int it = 0; it < SAMPLE_LIMIT; ++it) {
-        float r1 = rng_u(r, K), r2 = rng_u(r, K);
+        float r1 = rng_u(r, k0, k1), r2 = rng_u(r, k0, k1);
         float k = fminf(wcb * __expf(r1 * lr), T);
         float y = k / E;
         float gv = (4.f / 3.f - (4.f / 3.f) * y + y * y) * S1 + (1.f - y) * S2;
@@ -202,10 +201,10 @@ __device__ __forceinline__ float sample_brems(float T, float wcb, float S1, floa
 
 // Multiple-scattering cos(theta) for G1 = s / lambda_1: Wentzel distribution with
 // screening A chosen so that <1 - cos> = 1 - exp(-G1) (table of ln A at ln G1).
-__device__ __forceinline__ float sample_ms(const SmemTables& T, float G1, Rng& r, const RoundKeys& K)
+__device__ __forceinline__ float sample_ms(const SmemTables& T, float G1, Rng& r, uint32_t k0, uint32_t k1)
 {
     if (!(G1 >= 1e-12f)) return 1.f;
-    float xi = rng_u(r, K);
+    float xi = rng_u(r, k0, k1);
     if (G1 >= 15.f) return 2.f * xi - 1.f;
     float x = (__logf(G1) - LN_G_LO) * INV_DLNG;
     x = fminf(fmaxf(x, 0.f), (float)(NG - 1) - 1e-3f);
@@ -395,8 +394,8 @@ __device__ __forceinline__ bool init_source(const TransportArgs& a, const G& g, 
     }
     int bin = s.order[lo];
     float e0 = s.lo[bin], e1 = s.hi[bin];
-    p.E = e0 + rng_u(p.r, a.rk) * (e1 - e0);
-    float fa = rng_u(p.r, a.rk) - 0.5f, fb = rng_u(p.r, a.rk) - 0.5f;
+    p.E = e0 + rng_u(p.r, a.key0, a.key1) * (e1 - e0);
+    float fa = rng_u(p.r, a.key0, a.key1) - 0.5f, fb = rng_u(p.r, a.key0, a.key1) - 0.5f;
     float P[3], O[3], d[3];
     for (int k = 0; k < 3; ++k) P[k] = g.iso[k] + fa * g.fx * g.e1[k] + fb * g.fy * g.e2[k];
     float tmin;

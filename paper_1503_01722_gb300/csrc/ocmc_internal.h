@@ -152,26 +152,6 @@ struct PsRec {
     int type;                            // 0 photon, 1 electron, 2 positron
 };
 
-// Philox4x32-10 round keys of a run: round r XORs (k0 + r W0, k1 + r W1) into the state, with the
-// Weyl constants W0 = 0x9E3779B9, W1 = 0xBB67AE85 and (k0, k1) the run's seed. Precomputed on the
-// host, so the kernels read them from the constant bank instead of adding them up per block.
-struct RoundKeys {
-    uint32_t r0[10], r1[10];
-};
-
-inline RoundKeys round_keys(uint64_t seed)
-{
-    RoundKeys K;
-    uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
-    for (int r = 0; r < 10; ++r) {
-        K.r0[r] = k0;
-        K.r1[r] = k1;
-        k0 += 0x9E3779B9u;
-        k1 += 0xBB67AE85u;
-    }
-    return K;
-}
-
 struct TransportArgs {
     // geometry
     int nx, ny, nz;
@@ -185,7 +165,6 @@ struct TransportArgs {
     // run
     unsigned long long first, count, n_total;
     uint32_t key0, key1;
-    RoundKeys rk;               // round_keys(seed)
     unsigned long long* tally;
     // scratch
     PRec* stacks;               // per warp: nstk stacks of `cap` records

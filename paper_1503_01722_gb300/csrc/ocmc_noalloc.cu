@@ -225,7 +225,6 @@ extern "C" ocmc_status ocmc_run_noalloc(int device, int nx, int ny, int nz, cons
     a.n_total = n_total;
     a.key0 = (uint32_t)seed;
     a.key1 = (uint32_t)(seed >> 32);
-    a.rk = round_keys(seed);
     a.tally = reinterpret_cast<unsigned long long*>(tally_dev);
     a.stacks = stacks;
     a.cap = cap;

@@ -195,7 +195,7 @@ __device__ void emit_charged(C& c, const Lane& p, int type, float E, float du, f
 template <class C>
 __device__ __forceinline__ void annihilate(C& c, const Lane& p, Rng& r)
 {
-    float wc = 2.f * rng_u(r, c.a.rk) - 1.f, xi = rng_u(r, c.a.rk);
+    float wc = 2.f * rng_u(r, c.a.key0, c.a.key1) - 1.f, xi = rng_u(r, c.a.key0, c.a.key1);
     float st = sqrtf(fmaxf(0.f, 1.f - wc * wc)), sp, cp;
     __sincosf(6.283185307179586f * xi, &sp, &cp);
     stat_add(c, ST_ANNIH, 1);
@@ -231,7 +231,7 @@ __device__ __forceinline__ void pair_event(C& c, Lane& p)
 {
     stat_add(c, ST_PAIR, 1);
     float avail = p.E - 2.f * MC2F;
-    float Tm = rng_u(p.r, c.a.rk) * avail, Tp = avail - Tm;
+    float Tm = rng_u(p.r, c.a.key0, c.a.key1) * avail, Tp = avail - Tm;
     emit_charged(c, p, ELECTRON, Tm, p.u, p.v, p.w, 0);
     emit_charged(c, p, POSITRON, Tp, p.u, p.v, p.w, 1);
 }
@@ -242,13 +242,13 @@ __device__ __forceinline__ bool photon_step(C& c, Lane& p, unsigned& n_fict)
 {
     const TransportArgs& a = c.a;
     const SmemTables& T = c.T;
-    const RoundKeys& K = a.rk;
-    rng_step_start(p.r, K);
+    const uint32_t k0 = a.key0, k1 = a.key1;
+    rng_step_start(p.r, k0, k1);
     EIdx ei = e_index(p.E);
     float lnmaj = lerp1(T.phmaj[ei.i], T.phmaj[ei.i + 1], ei.f);
     if (lnmaj < -1e29f) { escape(c, p); return false; }
     float mumax = __expf(lnmaj);
-    float s = -__logf(rng_u(p.r, K)) / mumax;
+    float s = -__logf(rng_u(p.r, k0, k1)) / mumax;
     p.x = fmaf(s, p.u, p.x);
     p.y = fmaf(s, p.v, p.y);
     p.z = fmaf(s, p.w, p.z);
@@ -269,10 +269,10 @@ __device__ __forceinline__ bool photon_step(C& c, Lane& p, unsigned& n_fict)
     float4 pa = T.ph[m * MS4 + ei.i], pb = T.ph[m * MS4 + ei.i + 1];
     float mu = rho * __expf(lerp1(pa.x, pb.x, ei.f));
     if (mu > mumax * 1.00001f) stat_add(c, ST_VIOL, 1);
-    if (rng_u(p.r, K) * mumax >= mu) { n_fict++; return true; }
+    if (rng_u(p.r, k0, k1) * mumax >= mu) { n_fict++; return true; }
     if (a.pp.flags & 4) { stat_add(c, ST_E_KILLED, fx(p.E)); return false; }
     float fC = lerp1(pa.y, pb.y, ei.f), fP = lerp1(pa.z, pb.z, ei.f);
-    float xi = rng_u(p.r, K);
+    float xi = rng_u(p.r, k0, k1);
     if (xi >= fC && xi < fC + fP) {
         stat_add(c, ST_PHOTO, 1);
         deposit(c, p, p.ix, p.iy, p.iz, p.E);
@@ -285,8 +285,8 @@ __device__ __forceinline__ bool photon_step(C& c, Lane& p, unsigned& n_fict)
     // Compton scattering (also the rare pair selection below threshold from table interpolation)
     stat_add(c, ST_COMPTON, 1);
     float eps;
-    float cth = sample_compton(p.E, p.r, K, &eps, &c.ok);
-    float xphi = rng_u(p.r, K);
+    float cth = sample_compton(p.E, p.r, k0, k1, &eps, &c.ok);
+    float xphi = rng_u(p.r, k0, k1);
     float E0 = p.E, E1 = eps * E0, Te = E0 - E1;
     float u0 = p.u, v0 = p.v, w0 = p.w;
     rotate(p.u, p.v, p.w, cth, xphi);
@@ -319,12 +319,12 @@ template <class C>
 __device__ __forceinline__ void hard_event(C& c, Lane& p, int m, float sM, float tot)
 {
     const SmemTables& T = c.T;
-    if (rng_u(p.r, c.a.rk) * tot < sM) {
+    if (rng_u(p.r, c.a.key0, c.a.key1) * tot < sM) {
         stat_add(c, ST_MOLLER, 1);
         float Tk = p.E;
-        float eps = sample_moller(Tk, c.a.pp.w_cc, p.r, c.a.rk, &c.ok);
+        float eps = sample_moller(Tk, c.a.pp.w_cc, p.r, c.a.key0, c.a.key1, &c.ok);
         float W = eps * Tk, T1 = Tk - W;
-        float xphi = rng_u(p.r, c.a.rk);
+        float xphi = rng_u(p.r, c.a.key0, c.a.key1);
         float mu1 = sqrtf(fminf(1.f, T1 * (Tk + 2.f * MC2F) / (Tk * (T1 + 2.f * MC2F))));
         float mu2 = sqrtf(fminf(1.f, W * (Tk + 2.f * MC2F) / (Tk * (W + 2.f * MC2F))));
         float su = p.u, sv2 = p.v, sw = p.w;
@@ -335,9 +335,9 @@ __device__ __forceinline__ void hard_event(C& c, Lane& p, int m, float sM, float
     } else {
         stat_add(c, ST_BREMS, 1);
         float Tk = p.E;
-        float k = sample_brems(Tk, c.a.pp.w_cb, T.msc[m * MS1], T.msc[m * MS1 + 1], p.r, c.a.rk, &c.ok);
+        float k = sample_brems(Tk, c.a.pp.w_cb, T.msc[m * MS1], T.msc[m * MS1 + 1], p.r, c.a.key0, c.a.key1, &c.ok);
         float th = MC2F / (Tk + MC2F);
-        float xphi = rng_u(p.r, c.a.rk);
+        float xphi = rng_u(p.r, c.a.key0, c.a.key1);
         float gu = p.u, gv = p.v, gw = p.w;
         rotate(gu, gv, gw, __cosf(th), xphi);
         if (k >= c.a.pp.e_abs_g)
@@ -363,7 +363,7 @@ __device__ __forceinline__ bool charged_step(C& c, Lane& p, unsigned& n_hfict)
 {
     const TransportArgs& a = c.a;
     const SmemTables& T = c.T;
-    const RoundKeys& K = a.rk;
+    const uint32_t k0 = a.key0, k1 = a.key1;
     if (vox_bad(c, p)) return false;
     const int vox = p.ix + a.nx * (p.iy + a.ny * p.iz);
     float rho = __ldg(a.density + vox);
@@ -379,7 +379,7 @@ __device__ __forceinline__ bool charged_step(C& c, Lane& p, unsigned& n_hfict)
         if (!cross_face(c, p, face)) { escape(c, p); return false; }
         return true;
     }
-    rng_step_start(p.r, K);
+    rng_step_start(p.r, k0, k1);
     EIdx ei = e_index(p.E);
     const int mb = m * MS4, mb2 = m * MS2;
     float4 A = T.el[mb + ei.i], B = T.el[mb + ei.i + 1];
@@ -387,14 +387,14 @@ __device__ __forceinline__ bool charged_step(C& c, Lane& p, unsigned& n_hfict)
     float lnR = lerp1(A.x, B.x, ei.f);
     float s_maxe = lerp1(C2.x, D2.x, ei.f) / rho;
     float sighat = (a.pp.flags & 1) ? 0.f : C2.y;
-    float d_ev = sighat > 0.f ? -__logf(rng_u(p.r, K)) / (rho * sighat) : 3.0e38f;
+    float d_ev = sighat > 0.f ? -__logf(rng_u(p.r, k0, k1)) / (rho * sighat) : 3.0e38f;
     float s = sv;
     int lim = 0;
     if (a.pp.d_maxs < s) { s = a.pp.d_maxs; lim = 1; }
     if (s_maxe < s) { s = s_maxe; lim = 2; }
     if (d_ev < s) { s = d_ev; lim = 3; }
     // random hinge: s1 straight, deflect, then the rest (clipped to this voxel)
-    float s1 = rng_u(p.r, K) * s;
+    float s1 = rng_u(p.r, k0, k1) * s;
     float hx = fmaf(s1, p.u, p.x), hy = fmaf(s1, p.v, p.y), hz = fmaf(s1, p.w, p.z);
     float E0 = p.E;
     const float R0 = __expf(lnR), g0 = range_to_lnE(T, m, lnR);
@@ -402,8 +402,8 @@ __device__ __forceinline__ bool charged_step(C& c, Lane& p, unsigned& n_hfict)
     if (!(a.pp.flags & 2)) {
         EIdx em = e_index(0.5f * (E0 + Efull));
         float l1 = lerp1(T.el[mb + em.i].y, T.el[mb + em.i + 1].y, em.f);
-        float cth = sample_ms(T, rho * s * l1, p.r, K);
-        float xphi = rng_u(p.r, K);
+        float cth = sample_ms(T, rho * s * l1, p.r, k0, k1);
+        float xphi = rng_u(p.r, k0, k1);
         rotate(p.u, p.v, p.w, cth, xphi);
     }
     int face2;
@@ -434,7 +434,7 @@ __device__ __forceinline__ bool charged_step(C& c, Lane& p, unsigned& n_hfict)
         float sB = p.E > a.pp.w_cb ? lerp1(A2.w, B2.w, e2.f) : 0.f;
         float tot = sM + sB;
         if (tot > sighat * 1.00001f) stat_add(c, ST_VIOL, 1);
-        if (rng_u(p.r, K) * sighat < tot) {
+        if (rng_u(p.r, k0, k1) * sighat < tot) {
             hard_event(c, p, m, sM, tot);
             if (p.E < a.pp.e_abs_e) { absorb_charged(c, p); return false; }
         } else {
@@ -510,7 +510,7 @@ __device__ __forceinline__ bool charged_step_cross(C& c, Lane& p, unsigned& n_hf
 {
     const TransportArgs& a = c.a;
     const SmemTables& T = c.T;
-    const RoundKeys& K = a.rk;
+    const uint32_t k0 = a.key0, k1 = a.key1;
     if (vox_bad(c, p)) return false;
     const int vox = p.ix + a.nx * (p.iy + a.ny * p.iz);
     const float rho0 = __ldg(a.density + vox);
@@ -525,19 +525,19 @@ __device__ __forceinline__ bool charged_step_cross(C& c, Lane& p, unsigned& n_hf
         if (!cross_face(c, p, face)) { escape(c, p); return false; }
         return true;
     }
-    rng_step_start(p.r, K);
+    rng_step_start(p.r, k0, k1);
     const float E0 = p.E;
     const EIdx ei = e_index(E0);
     const int mb = m0 * MS4, mb2 = m0 * MS2;
     const float lnR = lerp1(T.el[mb + ei.i].x, T.el[mb + ei.i + 1].x, ei.f);
     const float s_maxe = lerp1(T.el2[mb2 + ei.i].x, T.el2[mb2 + ei.i + 1].x, ei.f) / rho0;
     const float maj = (a.pp.flags & 1) ? 0.f : __ldg(a.t.elmaj + ei.i);
-    const float d_ev = maj > 0.f ? -__logf(rng_u(p.r, K)) / maj : 3.0e38f;
+    const float d_ev = maj > 0.f ? -__logf(rng_u(p.r, k0, k1)) / maj : 3.0e38f;
     float s = a.pp.d_maxs;
     int lim = 1;
     if (s_maxe < s) { s = s_maxe; lim = 2; }
     if (d_ev < s) { s = d_ev; lim = 3; }
-    const float s1 = rng_u(p.r, K) * s;
+    const float s1 = rng_u(p.r, k0, k1) * s;
     const float Ef = E0 * (1.f - a.pp.f_maxe);
     const float Efull = csda_end2(T, m0, E0, __expf(lnR), range_to_lnE(T, m0, lnR), rho0 * s);
     float done;
@@ -546,8 +546,8 @@ __device__ __forceinline__ bool charged_step_cross(C& c, Lane& p, unsigned& n_hf
     if (!(a.pp.flags & 2)) {
         EIdx em = e_index(0.5f * (E0 + Efull));
         float l1 = lerp1(T.el[mb + em.i].y, T.el[mb + em.i + 1].y, em.f);
-        float cth = sample_ms(T, rho0 * (r == SEG_FLOOR ? done : s) * l1, p.r, K);
-        float xphi = rng_u(p.r, K);
+        float cth = sample_ms(T, rho0 * (r == SEG_FLOOR ? done : s) * l1, p.r, k0, k1);
+        float xphi = rng_u(p.r, k0, k1);
         rotate(p.u, p.v, p.w, cth, xphi);
     }
     if (r == SEG_FLOOR) return true;
@@ -565,7 +565,7 @@ __device__ __forceinline__ bool charged_step_cross(C& c, Lane& p, unsigned& n_hf
     const float sB = p.E > a.pp.w_cb ? rho * lerp1(A2.w, B2.w, e2.f) : 0.f;
     const float tot = sM + sB;
     if (tot > maj * 1.00001f) stat_add(c, ST_VIOL, 1);
-    if (rng_u(p.r, K) * maj < tot) {
+    if (rng_u(p.r, k0, k1) * maj < tot) {
         hard_event(c, p, m, sM, tot);
         if (p.E < a.pp.e_abs_e) { absorb_charged(c, p); return false; }
     } else {
