@@ -648,15 +648,19 @@ ocmc_status ocmc_get_dose(ocmc_ctx* c, float* dose, float* sigma, int on_device)
         CK(dalloc(&c->d_invnb, c->tally_B), "allocation");
         c->invnb_cap = c->tally_B;
     }
-    std::vector<double> inv(c->tally_B);
-    for (int b = 0; b < c->tally_B; ++b) inv[b] = c->nb[b] > 0 ? 1.0 / c->nb[b] : 0.0;
-    CK(cudaMemcpyAsync(c->d_invnb, inv.data(), sizeof(double) * c->tally_B, cudaMemcpyHostToDevice, s), "upload");
+    std::vector<float> inv(c->tally_B);
+    for (int b = 0; b < c->tally_B; ++b) inv[b] = c->nb[b] > 0 ? (float)(n / c->nb[b]) : 0.f;
+    CK(cudaMemcpyAsync(c->d_invnb, inv.data(), sizeof(float) * c->tally_B, cudaMemcpyHostToDevice, s), "upload");
+    // device outputs are written in place; host outputs go through the context's buffers
+    float* dd = on_device ? dose : c->d_dose;
+    float* ds = sigma ? (on_device ? sigma : c->d_sigma) : nullptr;
     CK(launch_finalize(c->d_tally, c->d_density, c->tally_B, c->nvox, (double)c->dx * c->dy * c->dz, c->d_invnb,
-                       1.0 / n, c->d_dose, sigma ? c->d_sigma : nullptr, s),
+                       1.0 / n, dd, ds, s),
        "finalize launch");
-    cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
-    CK(cudaMemcpyAsync(dose, c->d_dose, sizeof(float) * c->nvox, k, s), "dose copy");
-    if (sigma) CK(cudaMemcpyAsync(sigma, c->d_sigma, sizeof(float) * c->nvox, k, s), "sigma copy");
+    if (!on_device) {
+        CK(cudaMemcpyAsync(dose, c->d_dose, sizeof(float) * c->nvox, cudaMemcpyDeviceToHost, s), "dose copy");
+        if (sigma) CK(cudaMemcpyAsync(sigma, c->d_sigma, sizeof(float) * c->nvox, cudaMemcpyDeviceToHost, s), "sigma copy");
+    }
     CK(cudaStreamSynchronize(s), "synchronize");
     return check_err_flag(c);
 }

@@ -8,36 +8,49 @@ namespace ocmc {
 
 namespace {
 
-// D_v = sum_b E_bv / (rho_v V N); sigma_v^2 = sum_b (D_bv - D_v)^2 / (B (B - 1)),
-// D_bv = E_bv / (rho_v V N_b)  (Sec. 2.2 "Materials": MeV/g per source particle;
-// Sec. 3.1: sigma_D, here by the batch method). Grid-stride over voxels.
+// int64 -> float without a 64-bit conversion (which runs on GB300's narrow FP64 pipe): the high
+// and low words convert exactly or to nearest, so the result is within 2 ulp of the exact value.
+__device__ __forceinline__ float i64_to_f32(long long x)
+{
+    const int hi = (int)(x >> 32);
+    const unsigned lo = (unsigned)x;
+    return fmaf(__int2float_rn(hi), 4294967296.f, __uint2float_rn(lo));
+}
+
+// D_v = sum_b tally / (2^28 rho_v V N) in MeV/g per source particle (Sec. 2.2 "Materials");
+// sigma_D by the batch method (Sec. 3.1): sqrt(sum_b (D_b - D)^2 / (B (B - 1))) with the batch
+// means D_b = tally_b / (2^28 rho_v V n_b). Grid-stride over voxels. The integer sum is exact; the
+// rest is FP32, like the outputs (FP64 here made this kernel 13x slower than its memory traffic on
+// GB300's narrow FP64 pipe).
 __global__ void k_finalize(const long long* __restrict__ tally, const float* __restrict__ density, int B, long long nvox,
-                           double voxel_volume, const double* __restrict__ inv_nb, double inv_n, float* dose,
+                           float voxel_volume, const float* __restrict__ w_nb, float inv_n, float* dose,
                            float* sigma)
 {
     for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < nvox;
          v += (long long)gridDim.x * blockDim.x) {
-        float rho = density[v];
+        const float rho = density[v];
         if (!(rho > 0.f)) {
             dose[v] = 0.f;
             if (sigma) sigma[v] = 0.f;
             continue;
         }
-        double inv_mass = 1.0 / ((double)rho * voxel_volume) / 268435456.0;
+        const float scale = inv_n / (rho * voxel_volume * 268435456.f);   // MeV/g per history per unit
         long long tot = 0;
         for (int b = 0; b < B; ++b) tot += tally[(long long)b * nvox + v];
-        double D = (double)tot * inv_mass * inv_n;
-        dose[v] = (float)D;
+        const float tf = i64_to_f32(tot);
+        dose[v] = tf * scale;
         if (sigma) {
-            double ss = 0.0;
+            // batch b's mean relative to the whole: tally_b * (N / n_b) - tot, in units of 2^32 tally
+            // units so that the squares stay in FP32's range for any int64 tally
+            float ss = 0.f;
             if (B > 1) {
                 for (int b = 0; b < B; ++b) {
-                    double Db = (double)tally[(long long)b * nvox + v] * inv_mass * inv_nb[b] - D;
-                    ss += Db * Db;
+                    const float d = fmaf(i64_to_f32(tally[(long long)b * nvox + v]), w_nb[b], -tf) * 2.3283064365386963e-10f;
+                    ss = fmaf(d, d, ss);
                 }
-                ss /= (double)B * (B - 1);
+                ss /= (float)B * (float)(B - 1);
             }
-            sigma[v] = (float)sqrt(ss);
+            sigma[v] = sqrtf(ss) * 4294967296.f * scale;
         }
     }
 }
@@ -306,10 +319,11 @@ cudaError_t launch_sum_tally(const long long* tally, long long n, unsigned long 
 }
 
 cudaError_t launch_finalize(const long long* tally, const float* density, int B, long long nvox, double voxel_volume,
-                            const double* inv_nb, double inv_n, float* dose, float* sigma, cudaStream_t s)
+                            const float* w_nb, double inv_n, float* dose, float* sigma, cudaStream_t s)
 {
     int blocks = (int)std::min<long long>((nvox + 255) / 256, 152 * 16);
-    k_finalize<<<blocks > 0 ? blocks : 1, 256, 0, s>>>(tally, density, B, nvox, voxel_volume, inv_nb, inv_n, dose, sigma);
+    k_finalize<<<blocks > 0 ? blocks : 1, 256, 0, s>>>(tally, density, B, nvox, (float)voxel_volume, w_nb,
+                                                       (float)inv_n, dose, sigma);
     return cudaGetLastError();
 }
 

@@ -54,7 +54,7 @@ struct ocmc_ctx {
     // outputs
     float* d_dose = nullptr;
     float* d_sigma = nullptr;
-    double* d_invnb = nullptr;
+    float* d_invnb = nullptr;       // N / n_b per batch (k_finalize)
     int invnb_cap = 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     bool timed = false;

@@ -201,7 +201,8 @@ size_t transport_smem_bytes(int n_mat);
 int transport_max_blocks_per_sm(int threads, size_t smem, int nreg);
 bool transport_nreg_supported(int nreg);
 cudaError_t launch_finalize(const long long* tally, const float* density, int B, long long nvox, double voxel_volume,
-                            const double* inv_nb, double inv_n, float* dose, float* sigma, cudaStream_t s);
+                            const float* w_nb, double inv_n, float* dose, float* sigma, cudaStream_t s);
+// (w_nb[b] = N / n_b: the whole run's histories over batch b's, 0 for an empty batch)
 cudaError_t launch_test_philox(uint32_t key0, uint32_t key1, uint32_t c1, uint32_t c2, uint32_t c3,
                                uint32_t first_block, uint32_t n_blocks, uint32_t* out, cudaStream_t s);
 cudaError_t launch_test_rotate(const float* dir, const float* mu, const float* xi, int n, float* out, cudaStream_t s);

@@ -341,3 +341,24 @@ def test_stack_overflow_is_reported_not_faulted(ocmc):
         e.set_params(stack_capacity=0, switch_high=0, block_threads=0, blocks_per_sm=0)
         e.run(2000, seed=2)
         e.dose()
+
+
+@pytest.mark.parametrize("n", [12_345, 300_000])
+def test_finalize_matches_the_batch_formula(ocmc, n):
+    """ocmc_get_dose (k_finalize: exact integer sum, FP32 arithmetic) against the batch-method
+    formula evaluated in FP64 on the host from the same raw tally (uneven batches when N mod B
+    is not 0): dose to FP32 rounding, sigma to 1e-4 relative plus 1e-6 of the dose."""
+    ph = I.scaled(I.slab(), 3)
+    beam = I.beam_on(ph, 0, I.spectrum_6mv(), (10, 10), 100.0)
+    with ocmc.Engine(0, n_batches=10) as e:
+        e.create_phantom(ph)
+        e.set_source(beam)
+        e.run(n, seed=4)
+        D, S = e.dose()
+        t = e.raw_tally()
+    Dr, Sr = O.finalize(t, ph, n)
+    m = Dr > 0
+    assert np.array_equal(D > 0, m)
+    assert np.max(np.abs(D[m] / Dr[m] - 1)) < 1e-6
+    # the FP32 difference of a batch mean and the whole carries ~1e-7 of the dose
+    assert np.all(np.abs(S - Sr) <= 1e-4 * Sr + 1e-6 * Dr)
