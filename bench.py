@@ -35,9 +35,10 @@ import ocmc_inputs as I  # noqa: E402
 INST_PER_LANE_STEP = 595.9
 # DRAM bytes of one transport launch measured by ncu on the full default workload
 DRAM_BYTES_PER_LAUNCH = {("photon_slab_120", 100_000_000): 20.947e9}
-# the same for the beamlet-mode kernel (hash tallies) on the 512-beamlet CT workload, measured by
-# ncu on the same workload with every beamlet's histories scaled by 0.02
-INST_PER_LANE_STEP_BEAMLETS = 742.9
+# the same (predicated-on) for the beamlet-mode kernel (hash tallies) on the 512-beamlet CT
+# workload, measured by ncu on full runs of the same workload with every beamlet's histories
+# scaled by 0.2
+INST_PER_LANE_STEP_BEAMLETS = 644.4
 
 WORKLOADS = {
     "photon_slab_120": (I.photon_slab_120, 100_000_000,

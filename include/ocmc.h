@@ -228,7 +228,9 @@ ocmc_status ocmc_run(ocmc_ctx* ctx, uint64_t n_histories, uint64_t seed, void* c
 /* Transport histories [first, first+count) of a run of n_total histories
  * (sharding over GPUs or resuming a run). The union of disjoint ranges with
  * the same n_total and seed gives the tally of one ocmc_run(n_total, seed),
- * bit for bit. */
+ * bit for bit. A range of more than 1e8 histories is transported in launches of
+ * 1e8 (on GB300 one launch of 1e9 histories ran 15 % slower per history than ten
+ * of 1e8); by the same composition rule the tally does not change. */
 ocmc_status ocmc_run_range(ocmc_ctx* ctx, uint64_t first, uint64_t count, uint64_t n_total,
                            uint64_t seed, void* cuda_stream);
 

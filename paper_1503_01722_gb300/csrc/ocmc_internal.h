@@ -30,6 +30,7 @@ constexpr double G1_ISO = 15.0;   // at and above: isotropic deflection
 constexpr double MC2 = 0.51099895000;
 constexpr float TALLY_SCALE = 268435456.0f;   // 2^28 fixed-point units per MeV
 constexpr int MAX_DIM = 1024;
+constexpr unsigned long long RUN_CHUNK = 100000000ull;   // histories per transport launch of a run
 
 // transport flags (ocmc_params.flags)
 constexpr int FLAG_CROSS_VOXELS = 16;   // electron steps cross voxel faces (fixed-step variant)

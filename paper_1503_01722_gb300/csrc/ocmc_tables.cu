@@ -284,18 +284,34 @@ __global__ void k_ms_table(Tables t)
     t.msA[j] = (float)wentzel_solve(exp(lg));
 }
 
+// Per-material maximum density and the validity check. Maxima are gathered in shared memory
+// first (one global atomic per material and block): with every voxel's atomic going to the same
+// few global words the scan took 1.3 ms on a 128^3 phantom.
 __global__ void k_phantom_scan(const float* density, const uint8_t* material, long long nvox, int n_mat,
                                unsigned int* rho_max, int* err)
 {
+    __shared__ unsigned int s_max[MAX_STAGED];
+    __shared__ int s_bad;
+    for (int m = threadIdx.x; m < MAX_STAGED; m += blockDim.x) s_max[m] = 0u;
+    if (threadIdx.x == 0) s_bad = 0;
+    __syncthreads();
+    bool bad = false;
     for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < nvox; v += (long long)gridDim.x * blockDim.x) {
         float r = density[v];
         int m = material[v];
-        if (m >= n_mat || !(r >= 0.f) || !(r <= 30.f)) {
-            atomicOr(err, ERR_PHANTOM);
-            continue;
-        }
-        if (r > 0.f) atomicMax(rho_max + m, __float_as_uint(r));   // non-negative floats order as their bits
+        const bool ok = m < n_mat && r >= 0.f && r <= 30.f;
+        bad |= !ok;
+        // lanes of one material take their maximum together; one shared atomic per material
+        const unsigned key = ok ? (unsigned)m : 0xFFu;
+        const unsigned grp = __match_any_sync(__activemask(), key);
+        const unsigned mx = __reduce_max_sync(grp, ok && r > 0.f ? __float_as_uint(r) : 0u);   // non-negative floats order as their bits
+        if (ok && mx && (threadIdx.x & 31) == __ffs(grp) - 1) atomicMax(s_max + m, mx);
     }
+    if (bad) s_bad = 1;
+    __syncthreads();
+    for (int m = threadIdx.x; m < n_mat; m += blockDim.x)
+        if (s_max[m]) atomicMax(rho_max + m, s_max[m]);
+    if (threadIdx.x == 0 && s_bad) atomicOr(err, ERR_PHANTOM);
 }
 
 __global__ void k_photon_majorant(Tables t)

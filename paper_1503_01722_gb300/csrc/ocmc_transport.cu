@@ -84,7 +84,7 @@ __device__ __forceinline__ unsigned long long fx(float e)
 // Batched-beamlet tally: add q to voxel v of beamlet b's open-addressing table
 // (linear probing, key claimed by compare-and-swap). A full table sets the
 // beamlet's overflow flag; the host then enlarges that table and runs again.
-__device__ __noinline__ void hash_add(const TransportArgs& a, uint32_t b, uint32_t v, unsigned long long q)
+__device__ __forceinline__ void hash_add(const TransportArgs& a, uint32_t b, uint32_t v, unsigned long long q)
 {
     const BeamletDev& B = a.beamlets[b];
     unsigned int* keys = a.bl_keys + B.table_off;
