@@ -587,6 +587,7 @@ __global__ void __maxnreg__(NREG) k_transport(const __grid_constant__ TransportA
     __shared__ int s_top[MAX_WARPS][3];
     __shared__ unsigned long long s_st[ST_COUNT];
     __shared__ unsigned long long s_time[MAX_WARPS][2];   // per warp: start, source seen exhausted
+    __shared__ unsigned long long s_wc[MAX_WARPS][3];     // per warp: iterations, photon / charged lane-steps
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     for (int i = threadIdx.x; i < ST_COUNT; i += blockDim.x) s_st[i] = 0ull;
     if (lane == 0) { s_top[wib][0] = 0; s_top[wib][1] = 0; s_top[wib][2] = 0; }
@@ -609,7 +610,11 @@ __global__ void __maxnreg__(NREG) k_transport(const __grid_constant__ TransportA
     bool active = false, just_switched = false;
     Lane p;
     unsigned n_fict = 0, n_hfict = 0;
-    unsigned long long iters = 0, lanes_ph = 0, lanes_ch = 0, hist = 0, e_in = 0, e_miss = 0, missed = 0;
+    // per-warp scheduler counters live in shared memory (iterations, photon and charged lane-steps),
+    // and per-history counts go straight to the block's statistics: none of them takes a register
+    // under the register cap
+    unsigned long long* wc = s_wc[wib];
+    if (lane == 0) { wc[0] = 0ull; wc[1] = 0ull; wc[2] = 0ull; }
 
     // modes (= stacks): 0 photons, 1 charged particles (at or above e_split when there are
     // three stacks), 2 charged particles below e_split
@@ -639,17 +644,17 @@ __global__ void __maxnreg__(NREG) k_transport(const __grid_constant__ TransportA
                 }
                 int r2 = rank - take;
                 if (!active && r2 >= 0 && r2 < want && base + r2 < a.count) {
-                    hist++;
+                    stat_add(c, ST_HISTORIES, 1);
                     bool in;
                     if constexpr (BL) in = init_beamlet(a, base + r2, p);
                     else if constexpr (ps_src) in = init_phase_space(a, a.first + base + r2, p);
                     else in = init_primary(a, a.first + base + r2, p);
                     float ecut = p.type == PHOTON ? a.pp.e_abs_g : a.pp.e_abs_e;
                     if (!in) {
-                        missed++;
-                        e_miss += fx(p.E);
+                        stat_add(c, ST_MISSED, 1);
+                        stat_add(c, ST_E_MISS, fx(p.E));
                     } else if constexpr (ps_src) {
-                        e_in += fx(p.E);
+                        stat_add(c, ST_E_IN, fx(p.E));
                         const bool charged = p.type != PHOTON;
                         if (p.E >= ecut && !(charged && (a.pp.flags & 8))) {
                             const int target = charged ? charged_stack(a, p.E) : 0;
@@ -661,7 +666,7 @@ __global__ void __maxnreg__(NREG) k_transport(const __grid_constant__ TransportA
                             deposit(c, p, p.ix, p.iy, p.iz, p.E);
                         }
                     } else {
-                        e_in += fx(p.E);
+                        stat_add(c, ST_E_IN, fx(p.E));
                         if (p.E >= ecut && !(p.type != PHOTON && (a.pp.flags & 8))) active = true;
                         else deposit(c, p, p.ix, p.iy, p.iz, p.E);
                     }
@@ -711,8 +716,8 @@ __global__ void __maxnreg__(NREG) k_transport(const __grid_constant__ TransportA
         }
         just_switched = false;
         if (lane == 0) {
-            iters++;
-            if (mode) lanes_ch += nact; else lanes_ph += nact;
+            wc[0] += 1ull;
+            wc[mode ? 2 : 1] += (unsigned long long)nact;
         }
         if (active) {
             if constexpr (XV) active = mode ? charged_step_cross(c, p, n_hfict) : photon_step(c, p, n_fict);
@@ -732,14 +737,10 @@ __global__ void __maxnreg__(NREG) k_transport(const __grid_constant__ TransportA
     // per-warp and per-lane statistics
     atomicAdd(s_st + ST_FICT, (unsigned long long)n_fict);
     atomicAdd(s_st + ST_HARD_FICT, (unsigned long long)n_hfict);
-    atomicAdd(s_st + ST_HISTORIES, hist);
-    atomicAdd(s_st + ST_E_IN, e_in);
-    atomicAdd(s_st + ST_E_MISS, e_miss);
-    atomicAdd(s_st + ST_MISSED, missed);
     if (lane == 0) {
-        atomicAdd(s_st + ST_WARP_ITERS, iters);
-        atomicAdd(s_st + ST_LANES_PHOTON, lanes_ph);
-        atomicAdd(s_st + ST_LANES_CHARGED, lanes_ch);
+        atomicAdd(s_st + ST_WARP_ITERS, wc[0]);
+        atomicAdd(s_st + ST_LANES_PHOTON, wc[1]);
+        atomicAdd(s_st + ST_LANES_CHARGED, wc[2]);
         // tail: how long this warp ran on its own stacks after the source ran dry
         const unsigned long long t_end = globaltimer_ns(), t0 = s_time[wib][0];
         const unsigned long long ts = s_time[wib][1] ? s_time[wib][1] : t0;
