@@ -32,13 +32,13 @@ import ocmc_inputs as I  # noqa: E402
 # launch of 2e7 histories of the default workload) and DRAM bytes of a full launch, from the ncu
 # captures summarised in profiles/k_transport_photon_slab_120.md (re-measured whenever the
 # kernel changes). Lanes that a branch switched off are not counted.
-INST_PER_LANE_STEP = 595.9
+INST_PER_LANE_STEP = 595.5
 # DRAM bytes of one transport launch measured by ncu on the full default workload
-DRAM_BYTES_PER_LAUNCH = {("photon_slab_120", 100_000_000): 20.947e9}
+DRAM_BYTES_PER_LAUNCH = {("photon_slab_120", 100_000_000): 20.235e9}
 # the same (predicated-on) for the beamlet-mode kernel (hash tallies) on the 512-beamlet CT
 # workload, measured by ncu on full runs of the same workload with every beamlet's histories
 # scaled by 0.2
-INST_PER_LANE_STEP_BEAMLETS = 644.4
+INST_PER_LANE_STEP_BEAMLETS = 612.0
 
 WORKLOADS = {
     "photon_slab_120": (I.photon_slab_120, 100_000_000,
