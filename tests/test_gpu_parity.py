@@ -362,3 +362,66 @@ def test_finalize_matches_the_batch_formula(ocmc, n):
     assert np.max(np.abs(D[m] / Dr[m] - 1)) < 1e-6
     # the FP32 difference of a batch mean and the whole carries ~1e-7 of the dose
     assert np.all(np.abs(S - Sr) <= 1e-4 * Sr + 1e-6 * Dr)
+
+
+def test_run_longer_than_one_launch_composes(ocmc):
+    """A run of 1.5e8 histories is transported in two launches (at most 1e8 histories each);
+    its tally equals that of the same history range split at another point, bit for bit."""
+    ph = I.homogeneous((16, 16, 16), (1.0, 1.0, 1.0))
+    beam = I.beam_on(ph, 0, I.spectrum_6mv(), (8, 8), 100.0)
+    n = 150_000_000
+    with ocmc.Engine(0, n_batches=4) as e:
+        e.create_phantom(ph)
+        e.set_source(beam)
+        e.run(n, seed=3)
+        st = e.stats()
+        whole = e.raw_tally()
+        e.reset()
+        e.run_range(0, 75_000_000, n, seed=3)
+        e.run_range(75_000_000, 75_000_000, n, seed=3)
+        split = e.raw_tally()
+    assert st["histories"] == n
+    check_conservation(st)
+    assert np.array_equal(whole, split)
+
+
+def test_largest_grid(ocmc):
+    """The largest grid the library takes: 1024 voxels along every axis (1.07e9 voxels; a stacked
+    particle's voxel indices are packed in 10 bits per axis, and voxel offsets are 32-bit). A 6 MV
+    beam over the whole entrance face runs with the invariants that hold at any size, deposits in
+    the last voxel layer of every axis, and a 1025-voxel axis is refused."""
+    import torch
+    n_side, n = 1024, 2_000_000
+    ph = I.homogeneous((n_side,) * 3, (0.05,) * 3)
+    beam = I.beam_on(ph, 0, I.spectrum_6mv(), (60.0, 60.0), 100.0)
+    with ocmc.Engine(0, n_batches=2) as e:
+        e.create_phantom(ph)
+        e.set_source(beam)
+        e.run(n, seed=1)
+        st = e.stats()
+        dose = torch.empty(ph.density.shape, dtype=torch.float32, device="cuda")
+        sig = torch.empty_like(dose)
+        e.dose(out=(dose, sig))
+        last = [float(dose[-1].sum()), float(dose[:, -1].sum()), float(dose[:, :, -1].sum()),
+                float(dose[0].sum()), float(dose[:, 0].sum()), float(dose[:, :, 0].sum())]
+        finite = bool(torch.isfinite(dose).all()) and bool(torch.isfinite(sig).all())
+        del dose, sig
+        assert st["histories"] == n
+        check_conservation(st)
+        assert finite and min(last) > 0.0, last
+        with pytest.raises(ocmc.OcmcError) as x:
+            e.create_phantom(I.homogeneous((n_side + 1, 2, 2), (1.0, 1.0, 1.0)))
+        assert x.value.status == ocmc.ERR_ARG
+
+
+@pytest.mark.parametrize("particle,E,n", [(0, 2.0, 400_000), (1, 10.0, 40_000)])
+def test_single_voxel_phantom(ocmc, particle, E, n):
+    """A 10 cm water cube as one voxel (every charged step ends on the cube's faces or its own
+    limits): the dose of the single voxel agrees with the oracle's on independent streams."""
+    ph = I.homogeneous((1, 1, 1), (10.0, 10.0, 10.0))
+    beam = I.beam_on(ph, particle, I.mono(E), (4, 4), 100.0)
+    D, S, Dr, Sr, st, tally, r = run_both(ocmc, ph, beam, n, B=20)
+    check_conservation(st)
+    assert D.shape == (1, 1, 1) and D[0, 0, 0] > 0
+    z = abs(float(D[0, 0, 0] - Dr[0, 0, 0])) / math.sqrt(float(S[0, 0, 0]) ** 2 + float(Sr[0, 0, 0]) ** 2)
+    assert z < 4.0, (D, Dr, S, Sr)
