@@ -140,7 +140,12 @@ ocmc_status read_overflow(ocmc_ctx* c, std::vector<unsigned int>& over)
 
 // Table sizes from two pilot runs: the distinct-voxel footprint at p2 and p1 = 4 p2
 // histories per beamlet, extrapolated to n as a power law (exponent clamped to
-// [0.2, 1]), with a 1.2 margin, a load factor of at most 0.7 and the global cap.
+// [0.2, 1]), with a 1.2 margin, a load factor of at most BL_LOAD and the global cap.
+// Target load factor of a beamlet's table at its estimated footprint: linear probing pays for
+// every occupied slot it passes, and on GB300 the 512-beamlet CT run took 219.8 ms at 0.7,
+// 183.9 ms at 0.35 and 180.7 ms at 0.175 (measured), at twice and four times the table memory.
+constexpr double BL_LOAD = 0.35;
+
 ocmc_status size_tables(ocmc_ctx* c, uint64_t seed, cudaStream_t s)
 {
     const int n = c->bl_n;
@@ -191,7 +196,7 @@ ocmc_status size_tables(ocmc_ctx* c, uint64_t seed, cudaStream_t s)
             a = std::log((double)nnz1[b] / nnz2[b]) / std::log((double)p1[b] / p2[b]);
         a = std::min(1.0, std::max(0.2, a));
         double est = std::min((double)c->nvox, std::max(1.0, (double)nnz1[b]) * std::pow(nb / p1[b], a)) * 1.2 * scale;
-        c->bl_cap[b] = std::min(cap_max, next_pow2(std::max<unsigned long long>(1024, (unsigned long long)(est / 0.7))));
+        c->bl_cap[b] = std::min(cap_max, next_pow2(std::max<unsigned long long>(1024, (unsigned long long)(est / BL_LOAD))));
     }
     c->bl_sized = true;
     c->bl_graph_valid = false;

@@ -69,18 +69,26 @@ struct Cfg {
     static constexpr int NS = NS_;                                       // halo stages
     static constexpr int G = CIN / 8;
     static constexpr int CHUNKS = CIN / 16;
+    // z-stacked taps for 16-channel slices: the three z-taps of one (dx, dy) are the N = 48
+    // columns of one MMA (see the kernel), so that each A window is read once instead of three
+    // times; an accumulator set then spans TZ + 4 slices (two spare slices at each end)
+    static constexpr bool ZS = NSL == 16;
+    static constexpr int ASLICES = ZS ? TZ + 4 : TZ;                     // slices per accumulator set
     static constexpr uint32_t W_BYTES = 27u * CIN * NSL * 2;             // one channel slice
     static constexpr uint32_t PLANE = (uint32_t)(TZ + 2) * HY * HX * 16;
     static constexpr uint32_t STAGE = 2 * PLANE;
     static constexpr uint32_t BAR_OFF = W_BYTES + NS * STAGE;
     static constexpr uint32_t BIAS_OFF = BAR_OFF + 256;
-    static constexpr uint32_t SMEM = BIAS_OFF + NSL * 4;
-    static constexpr uint32_t COLS = 2 * TZ * NSL;
+    static constexpr uint32_t ZERO_OFF = (BIAS_OFF + NSL * 4 + 127) / 128 * 128;
+    static constexpr uint32_t ZERO_BYTES = ZS ? 2u * ASLICES * NSL * 16 : 0u;   // zero B operand, both K halves
+    static constexpr uint32_t SMEM = ZERO_OFF + ZERO_BYTES;
+    static constexpr uint32_t COLS = 2 * ASLICES * NSL;
     static constexpr uint32_t NCOLS = COLS <= 32 ? 32 : COLS <= 64 ? 64 : COLS <= 128 ? 128 : COLS <= 256 ? 256 : 512;
     static_assert(COLS <= 512, "tensor memory holds 512 columns");
     static_assert(CIN % 16 == 0 && NSL % 16 == 0 && NSL <= 256, "MMA shape");
     static_assert(W_BYTES % 128 == 0 && PLANE % 128 == 0, "TMA destinations 128-byte aligned");
     static_assert(SMEM <= 232448, "shared memory per block");
+    static_assert(!ZS || ASLICES * NSL <= 256, "the zeroing MMA covers a whole accumulator set");
 };
 
 __device__ __forceinline__ bool wait_bounded(uint64_t* bar, uint32_t parity)
@@ -110,6 +118,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv3_tc(const __grid_constan
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int n0 = blockIdx.y * NSL;                  // this block's output channels n0 .. n0 + NSL - 1
     for (int i = threadIdx.x; i < NSL; i += TC_THREADS) sbias[i] = a.bias ? a.bias[n0 + i] : 0.f;
+    if constexpr (C::ZS)
+        for (uint32_t i = threadIdx.x; i < C::ZERO_BYTES / 16; i += TC_THREADS)
+            reinterpret_cast<uint4*>(smem + C::ZERO_OFF)[i] = make_uint4(0u, 0u, 0u, 0u);
 
     if (threadIdx.x == 0) {
         mbar_init(w_full, 1);
@@ -126,6 +137,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv3_tc(const __grid_constan
         fence_mbar_init();
     }
     if (warp == 1) tmem_alloc(tmem_slot, C::NCOLS);
+    if constexpr (C::ZS) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     fence_before_sync();
     __syncthreads();
     fence_after_sync();
@@ -178,7 +190,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv3_tc(const __grid_constan
                     }
                     if (!mbar_wait(&t_empty[acc], (ua & 1) ^ 1, abort, WAIT_NS)) break;
                     fence_after_sync();
-                    const uint32_t d0 = tmem + (uint32_t)(acc * TZ * NSL);
+                    const uint32_t d0 = tmem + (uint32_t)(acc * C::ASLICES * NSL);
                     for (int c = 0; c < C::CHUNKS; ++c, ++it) {
                         const int st = it % NS, u = it / NS;
                         if (!mbar_wait(&h_full[st], u & 1, abort, WAIT_NS)) break;
@@ -186,15 +198,37 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv3_tc(const __grid_constan
                         // descriptors are built once per chunk; a tap or slice only moves the start
                         // address, which is the descriptor's low field in 16-byte units
                         const uint64_t a0 = sdesc(sh_addr + (uint32_t)st * C::STAGE, C::PLANE, HX * 16);
-                        const uint64_t b0 = sdesc(sw_addr + (uint32_t)(2 * c) * NSL * 16, NSL * 16, 128);
+                        if constexpr (C::ZS) {
+                            // Input z-plane zi of the halo (0 .. TZ + 1) with shift (dx, dy) feeds output
+                            // slices zi - 2 + k through z-tap dz = 2 - k, k = 0, 1, 2: the weights hold the
+                            // z-taps of one (dx, dy) as N blocks k (dz = 2, 1, 0), and the MMA writes
+                            // accumulator slices zi .. zi + 2 of a set whose slice j is output slice j - 2.
+                            // Every MMA accumulates; the set is zeroed first by an MMA with a zero B.
+                            constexpr uint32_t idesc3 = idesc_bf16_f32(128, 3 * NSL);
+                            if (c == 0) {
+                                constexpr uint32_t idesc0 = idesc_bf16_f32(128, C::ASLICES * NSL);
+                                mma_f16(d0, a0, sdesc(saddr(smem + C::ZERO_OFF), C::ASLICES * NSL * 16, 128), idesc0, 0u);
+                            }
+                            const uint64_t b0 = sdesc(sw_addr + (uint32_t)(2 * c) * 3 * NSL * 16, 3 * NSL * 16, 128);
 #pragma unroll
-                        for (int t = 0; t < 27; ++t) {
-                            const int dx = t % 3, dy = (t / 3) % 3, dz = t / 9;
-                            const uint64_t bd = b0 + (uint64_t)(t * C::G * NSL);
+                            for (int zi = 0; zi < TZ + 2; ++zi)
 #pragma unroll
-                            for (int s = 0; s < TZ; ++s)
-                                mma_f16(d0 + (uint32_t)(s * NSL), a0 + (uint64_t)(((s + dz) * HY + dy) * HX + dx), bd,
-                                        idesc, (t != 0 || c != 0) ? 1u : 0u);
+                                for (int t9 = 0; t9 < 9; ++t9) {
+                                    const int dx = t9 % 3, dy = t9 / 3;
+                                    mma_f16(d0 + (uint32_t)(zi * NSL), a0 + (uint64_t)((zi * HY + dy) * HX + dx),
+                                            b0 + (uint64_t)(t9 * C::G * 3 * NSL), idesc3, 1u);
+                                }
+                        } else {
+                            const uint64_t b0 = sdesc(sw_addr + (uint32_t)(2 * c) * NSL * 16, NSL * 16, 128);
+#pragma unroll
+                            for (int t = 0; t < 27; ++t) {
+                                const int dx = t % 3, dy = (t / 3) % 3, dz = t / 9;
+                                const uint64_t bd = b0 + (uint64_t)(t * C::G * NSL);
+#pragma unroll
+                                for (int s = 0; s < TZ; ++s)
+                                    mma_f16(d0 + (uint32_t)(s * NSL), a0 + (uint64_t)(((s + dz) * HY + dy) * HX + dx),
+                                            bd, idesc, (t != 0 || c != 0) ? 1u : 0u);
+                            }
                         }
                         mma_commit(&h_empty[st]);
                         issued = true;
@@ -220,7 +254,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv3_tc(const __grid_constan
             fence_after_sync();
             const int tx = tile % a.tiles_x, r = tile / a.tiles_x;
             const int x = tx * TX + (row & 7), y = (r % a.tiles_y) * TY + (row >> 3), z0 = (r / a.tiles_y) * TZ;
-            const uint32_t tbase = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(acc * TZ * NSL);
+            // (with z-stacked taps output slice s is accumulator slice s + 2)
+            const uint32_t tbase = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(acc * C::ASLICES * NSL) +
+                                   (uint32_t)(C::ZS ? 2 * NSL : 0);
 #pragma unroll 1
             for (int s = 0; s < TZ; ++s) {
                 float v[NSL];
@@ -282,19 +318,31 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv3_tc(const __grid_constan
     if (threadIdx.x == 0 && *abort && a.err) atomicExch(a.err, 1);
 }
 
-// [taps][K][N] -> [N / NSL][taps][K/8][NSL][8]: one contiguous block per output-channel slice
-__global__ void k_pack_tc(const __nv_bfloat16* src, int taps, int K, int N, int nsl, __nv_bfloat16* dst)
+// [27][K][N] (tap t = dx + 3 dy + 9 dz) -> one contiguous block per output-channel slice:
+// [N / NSL][27][K/8][NSL][8], or with z-stacked taps (zs) [N / NSL][9 (dx + 3 dy)][K/8][3][NSL][8]
+// with the z-taps in the order dz = 2, 1, 0
+__global__ void k_pack_tc(const __nv_bfloat16* src, int K, int N, int nsl, int zs, __nv_bfloat16* dst)
 {
-    long long total = (long long)taps * K * N;
+    long long total = 27LL * K * N;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
         int kk = (int)(i & 7);
         long long q = i >> 3;
         int nn = (int)(q % nsl);
         q /= nsl;
-        int g = (int)(q % (K / 8));
-        q /= K / 8;
-        int t = (int)(q % taps);
-        int sl = (int)(q / taps);
+        int t, g, sl;
+        if (zs) {
+            const int k3 = (int)(q % 3);
+            q /= 3;
+            g = (int)(q % (K / 8));
+            q /= K / 8;
+            t = 9 * (2 - k3) + (int)(q % 9);
+            sl = (int)(q / 9);
+        } else {
+            g = (int)(q % (K / 8));
+            q /= K / 8;
+            t = (int)(q % 27);
+            sl = (int)(q / 27);
+        }
         dst[i] = src[((long long)t * K + 8 * g + kk) * N + sl * nsl + nn];
     }
 }
@@ -394,8 +442,9 @@ bool conv3_tc_supported(int cin, int cout)
 cudaError_t pack_conv3_tc(const __nv_bfloat16* w, int cin, int cout, __nv_bfloat16* wpack, cudaStream_t s)
 {
     long long n = 27LL * cin * cout;
-    k_pack_tc<<<(unsigned)std::min<long long>((n + 255) / 256, 4096), 256, 0, s>>>(w, 27, cin, cout,
-                                                                                  slice_width(cin, cout), wpack);
+    const int nsl = slice_width(cin, cout);
+    k_pack_tc<<<(unsigned)std::min<long long>((n + 255) / 256, 4096), 256, 0, s>>>(w, cin, cout, nsl, nsl == 16 ? 1 : 0,
+                                                                                  wpack);
     return cudaGetLastError();
 }
 
