@@ -18,6 +18,12 @@
 // accumulating in FP32 in tensor memory; two accumulator sets let the epilogue of one tile
 // overlap the MMAs of the next. Blocks of different channel slices read the same halo tiles,
 // which L2 serves.
+// With 16 or 32 output channels per slice the kernel stacks the z-taps instead: the window of
+// halo plane zi at shift (dx, dy) feeds output slices zi - 2, zi - 1 and zi through z-taps 2, 1
+// and 0, so one MMA of N = 3 NSL (weights packed [dx, dy][channel group][dz = 2, 1, 0][out
+// channel][8]) writes three consecutive slices of an accumulator set that carries two spare
+// slices at each end. The tensor core's operand reads from shared memory, which bound the
+// one-tap form at these widths, drop by 1.4-2x.
 //
 // Warp roles (192 threads): warp 0 issues the TMA copies, warp 1 owns tensor memory and one of
 // its lanes issues the MMAs, warps 2-5 read the accumulators (each warp its 32-lane quarter of
@@ -69,10 +75,11 @@ struct Cfg {
     static constexpr int NS = NS_;                                       // halo stages
     static constexpr int G = CIN / 8;
     static constexpr int CHUNKS = CIN / 16;
-    // z-stacked taps for 16-channel slices: the three z-taps of one (dx, dy) are the N = 48
-    // columns of one MMA (see the kernel), so that each A window is read once instead of three
-    // times; an accumulator set then spans TZ + 4 slices (two spare slices at each end)
-    static constexpr bool ZS = NSL == 16;
+    // z-stacked taps for 16- and 32-channel slices: the three z-taps of one (dx, dy) are the
+    // N = 3 NSL columns of one MMA (see the kernel), so that each A window is read once instead
+    // of three times; an accumulator set then spans TZ + 4 slices (two spare slices at each end),
+    // which for NSL = 32 fits tensor memory twice only with TZ <= 4
+    static constexpr bool ZS = NSL == 16 || (NSL == 32 && TZ <= 4);
     static constexpr int ASLICES = ZS ? TZ + 4 : TZ;                     // slices per accumulator set
     static constexpr uint32_t W_BYTES = 27u * CIN * NSL * 2;             // one channel slice
     static constexpr uint32_t PLANE = (uint32_t)(TZ + 2) * HY * HX * 16;
@@ -365,6 +372,7 @@ template <int CIN, int NSL, int TZ, int NS>
 cudaError_t launch_cfg(const ConvArgs& a, const __nv_bfloat16* wpack, int* err, cudaStream_t s)
 {
     using C = Cfg<CIN, NSL, TZ, NS>;
+    static_assert(C::ZS == (NSL <= 32), "pack_conv3_tc stacks the z-taps exactly for slices of up to 32 channels");
     static std::once_flag once;
     static cudaError_t attr = cudaSuccess;
     std::call_once(once, [] {
@@ -443,7 +451,7 @@ cudaError_t pack_conv3_tc(const __nv_bfloat16* w, int cin, int cout, __nv_bfloat
 {
     long long n = 27LL * cin * cout;
     const int nsl = slice_width(cin, cout);
-    k_pack_tc<<<(unsigned)std::min<long long>((n + 255) / 256, 4096), 256, 0, s>>>(w, cin, cout, nsl, nsl == 16 ? 1 : 0,
+    k_pack_tc<<<(unsigned)std::min<long long>((n + 255) / 256, 4096), 256, 0, s>>>(w, cin, cout, nsl, nsl <= 32 ? 1 : 0,
                                                                                   wpack);
     return cudaGetLastError();
 }
@@ -454,11 +462,11 @@ cudaError_t launch_conv3_tc(const ConvArgs& a, const __nv_bfloat16* wpack, int* 
         (a.mask && (a.mask_c0 % 8 || a.mask_stride % 8)) || !conv3_tc_supported(a.cin, a.cout))
         return cudaErrorInvalidValue;
     if (a.cin == 16 && a.cout == 16) return launch_cfg<16, 16, 8, 3>(a, wpack, err, s);
-    if (a.cin == 16 && a.cout == 32) return launch_cfg<16, 32, 8, 3>(a, wpack, err, s);
+    if (a.cin == 16 && a.cout == 32) return launch_cfg<16, 32, 4, 3>(a, wpack, err, s);
     if (a.cin == 32 && a.cout == 16) return launch_cfg<32, 16, 8, 3>(a, wpack, err, s);
-    if (a.cin == 32 && a.cout == 32) return launch_cfg<32, 32, 8, 3>(a, wpack, err, s);
+    if (a.cin == 32 && a.cout == 32) return launch_cfg<32, 32, 4, 3>(a, wpack, err, s);
     if (a.cin == 32 && a.cout == 64) return launch_cfg<32, 64, 4, 3>(a, wpack, err, s);
-    if (a.cin == 64 && a.cout == 32) return launch_cfg<64, 32, 8, 2>(a, wpack, err, s);
+    if (a.cin == 64 && a.cout == 32) return launch_cfg<64, 32, 4, 3>(a, wpack, err, s);
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);

@@ -18,8 +18,8 @@ void conv3_tc_test_stall(int tile, uint64_t ns);
 bool conv3_tc_supported(int cin, int cout);
 
 // Repack BF16 weights [27][cin][cout] into the kernel's layout [cout/nsl][27][cin/8][nsl][8],
-// nsl the kernel's output-channel slice for (cin, cout); for nsl = 16 the z-taps of each (dx, dy)
-// are stacked: [cout/16][9][cin/8][3 (dz = 2, 1, 0)][16][8].
+// nsl the kernel's output-channel slice for (cin, cout); for nsl <= 32 the z-taps of each (dx, dy)
+// are stacked: [cout/nsl][9][cin/8][3 (dz = 2, 1, 0)][nsl][8].
 cudaError_t pack_conv3_tc(const __nv_bfloat16* w, int cin, int cout, __nv_bfloat16* wpack, cudaStream_t s);
 
 // CONV3 convolution (forward, or data gradient with flipped transposed weights) with the same
