@@ -50,7 +50,7 @@ struct ConvArgs {
     int accumulate;              // out = out + result
     const __nv_bfloat16* mask;   // multiply by (mask(v, c) > 0), mask is a Slice-like buffer
     int mask_stride, mask_c0;
-    const __nv_bfloat16* wtc;    // CONV3: weights packed for the tensor-memory kernel, or null
+    const __nv_bfloat16* wtc;    // CONV3 / UP: weights packed for the tensor-memory kernel, or null
     int* err;                    // device error flag for the tensor-memory kernel (may be null)
 };
 

@@ -25,7 +25,7 @@
 // slices at each end. The tensor core's operand reads from shared memory, which bound the
 // one-tap form at these widths, drop by 1.4-2x.
 //
-// Warp roles (192 threads): warp 0 issues the TMA copies, warp 1 owns tensor memory and one of
+// Warp roles of the 3x3x3 kernel (192 threads): warp 0 issues the TMA copies, warp 1 owns tensor memory and one of
 // its lanes issues the MMAs, warps 2-5 read the accumulators (each warp its 32-lane quarter of
 // tensor memory), add bias / previous value, apply ReLU and mask, and store BF16. Every wait
 // gives up after two seconds, sets the error flag, lets its copies in flight land and frees
@@ -34,6 +34,7 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <cstring>
 #include <mutex>
 
 #include "ocmc_umma.cuh"
@@ -56,6 +57,7 @@ uint64_t g_stall_ns = 0;
 
 struct TcArgs {
     Grid3 g;
+    Grid3 gout;                  // UP: the fine output grid
     Slice out;
     const __nv_bfloat16* wpack;
     const float* bias;
@@ -354,6 +356,233 @@ __global__ void k_pack_tc(const __nv_bfloat16* src, int K, int N, int nsl, int z
     }
 }
 
+// ---- transposed 2x2x2 convolution (UP: coarse -> fine) on tcgen05 ----------------------------
+// Rows are coarse voxels: a tile is 8 (x) x 16 (y) voxels of one z-plane, the M = 128 rows of
+// an MMA (row m = x + 8 y), loaded by TMA as one plane of 8 channels per channel group (the same
+// 5-D view as the 3x3x3 kernel's, without a halo). Columns are the eight output parities times
+// the output channels, N = 8 COUT (j = p COUT + n), so one chain of CIN / 16 MMAs (two per K
+// step when N = 512) gives every output of the tile; the weights [p][cin][cout] stay in shared
+// memory packed [cin/8][N][8] (K-major B). Output voxel of row (x, y, z) and parity p =
+// (px, py, pz): (2x + px, 2y + py, 2z + pz). The data gradient of a DOWN layer is this same
+// operation with the transposed weights.
+constexpr int UP_THREADS = 320;   // producer warp, MMA warp, 8 epilogue warps (two per lane quarter)
+
+template <int CIN, int COUT>
+struct UpCfg {
+    static constexpr int G = CIN / 8;
+    static constexpr int N = 8 * COUT;
+    static constexpr int NMMA = N > 256 ? 2 : 1;                     // MMAs per K step (N <= 256 each)
+    static constexpr int NACC = 2 * N <= 512 ? 2 : 1;                // accumulator sets in tensor memory
+    static constexpr int NS = CIN * N * 2 > 65536 ? 2 : 4;           // input stages
+    static constexpr uint32_t W_BYTES = (uint32_t)N * CIN * 2;
+    static constexpr uint32_t PLANE = 128 * 16;                      // one channel group of a tile
+    static constexpr uint32_t STAGE = G * PLANE;
+    static constexpr uint32_t BAR_OFF = W_BYTES + NS * STAGE;
+    static constexpr uint32_t BIAS_OFF = BAR_OFF + 256;
+    static constexpr uint32_t SMEM = BIAS_OFF + COUT * 4;
+    static constexpr uint32_t COLS = NACC * N;
+    static constexpr uint32_t NCOLS = COLS <= 128 ? 128 : COLS <= 256 ? 256 : 512;
+    static_assert(CIN % 16 == 0 && COUT % 16 == 0 && COLS <= 512, "UP tile shape");
+    static_assert(W_BYTES % 128 == 0 && SMEM <= 232448, "shared memory per block");
+};
+
+template <int CIN, int COUT>
+__global__ void __launch_bounds__(UP_THREADS, 1) k_up_tc(const __grid_constant__ CUtensorMap tmap, const TcArgs a)
+{
+    using C = UpCfg<CIN, COUT>;
+    constexpr int NS = C::NS, N = C::N;
+    extern __shared__ __align__(1024) uint8_t smem[];
+    uint8_t* sw = smem;
+    uint8_t* sh = smem + C::W_BYTES;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + C::BAR_OFF);
+    uint64_t* w_full = bars;
+    uint64_t* h_full = bars + 1;
+    uint64_t* h_empty = bars + 1 + NS;
+    uint64_t* t_full = bars + 1 + 2 * NS;
+    uint64_t* t_empty = bars + 3 + 2 * NS;
+    uint64_t* drain = bars + 5 + 2 * NS;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 6 + 2 * NS);
+    volatile int* abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
+    float* sbias = reinterpret_cast<float*>(smem + C::BIAS_OFF);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int i = threadIdx.x; i < COUT; i += UP_THREADS) sbias[i] = a.bias ? a.bias[i] : 0.f;
+    if (threadIdx.x == 0) {
+        mbar_init(w_full, 1);
+        for (int i = 0; i < NS; ++i) {
+            mbar_init(&h_full[i], 1);
+            mbar_init(&h_empty[i], 1);
+        }
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&t_full[i], 1);
+            mbar_init(&t_empty[i], 8);
+        }
+        mbar_init(drain, 1);
+        *abort = 0;
+        fence_mbar_init();
+    }
+    if (warp == 1) tmem_alloc(tmem_slot, C::NCOLS);
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        // ---- producer: weights once, then every channel group of one tile per stage ----
+        if (lane == 0) {
+            mbar_expect_tx(w_full, C::W_BYTES);
+            const uint8_t* wsrc = reinterpret_cast<const uint8_t*>(a.wpack);
+            for (uint32_t off = 0; off < C::W_BYTES; off += 32768u)
+                bulk_load(sw + off, wsrc + off, min(32768u, C::W_BYTES - off), w_full);
+            int it = 0;
+            int last[NS];
+#pragma unroll
+            for (int i = 0; i < NS; ++i) last[i] = -1;
+            for (int tile = blockIdx.x; tile < a.ntiles && !*abort; tile += gridDim.x, ++it) {
+                const int tx = tile % a.tiles_x, r = tile / a.tiles_x;
+                const int x0 = tx * TX, y0 = (r % a.tiles_y) * TY, z = r / a.tiles_y;
+                const int st = it % NS, u = it / NS;
+                if (!mbar_wait(&h_empty[st], (u & 1) ^ 1, abort, WAIT_NS)) break;
+                uint8_t* dst = sh + st * C::STAGE;
+                mbar_expect_tx(&h_full[st], C::STAGE);
+                for (int g = 0; g < C::G; ++g) tma_load_5d(dst + g * C::PLANE, &tmap, 0, g, x0, y0, z, &h_full[st]);
+                last[st] = u;
+            }
+            if (*abort) {   // copies in flight must land before the block exits
+                wait_bounded(w_full, 0);
+                for (int i = 0; i < NS; ++i)
+                    if (last[i] >= 0) wait_bounded(&h_full[i], last[i] & 1);
+            }
+        }
+    } else if (warp == 1) {
+        // ---- MMA issue: D[128 x N] = A[128 x CIN] W[CIN x N] per tile ----
+        if (lane == 0) {
+            bool issued = false;
+            if (mbar_wait(w_full, 0, abort, WAIT_NS)) {
+                fence_after_sync();
+                constexpr uint32_t idesc = idesc_bf16_f32(128, N / C::NMMA);
+                const uint32_t sw_addr = saddr(sw), sh_addr = saddr(sh);
+                const uint64_t b0 = sdesc(sw_addr, N * 16, 128);
+                int it = 0;
+                for (int tile = blockIdx.x; tile < a.ntiles && !*abort; tile += gridDim.x, ++it) {
+                    const int acc = it % C::NACC, ua = it / C::NACC;
+                    if (!mbar_wait(&t_empty[acc], (ua & 1) ^ 1, abort, WAIT_NS)) break;
+                    fence_after_sync();
+                    const int st = it % NS, u = it / NS;
+                    if (!mbar_wait(&h_full[st], u & 1, abort, WAIT_NS)) break;
+                    fence_after_sync();
+                    const uint32_t d0 = tmem + (uint32_t)(acc * N);
+                    // rows 16 bytes apart, 8-row groups 128 bytes apart, channel groups one plane apart
+                    const uint64_t a0 = sdesc(sh_addr + (uint32_t)st * C::STAGE, C::PLANE, 128);
+#pragma unroll
+                    for (int k = 0; k < CIN / 16; ++k)
+#pragma unroll
+                        for (int h = 0; h < C::NMMA; ++h)
+                            mma_f16(d0 + (uint32_t)(h * 256), a0 + (uint64_t)(2 * k * C::PLANE / 16),
+                                    b0 + (uint64_t)((2 * k * N * 16 + h * 256 * 16) / 16), idesc, k ? 1u : 0u);
+                    mma_commit(&h_empty[st]);
+                    mma_commit(&t_full[acc]);
+                    issued = true;
+                }
+            }
+            if (*abort && issued) {   // MMAs in flight must finish before tensor memory is freed
+                mma_commit(drain);
+                wait_bounded(drain, 0);
+            }
+        }
+        __syncwarp();
+    } else {
+        // ---- epilogue: tensor memory -> bias / accumulate / ReLU / mask -> BF16 ----
+        // warps 2-9: two per tensor-memory lane quarter, each taking four of the eight parities
+        const int q = warp & 3;                       // the tensor-memory lane quarter of this warp
+        const int p0 = ((warp - 2) >> 2) * 4;
+        const int row = 32 * q + lane;
+        int it = 0;
+        for (int tile = blockIdx.x; tile < a.ntiles && !*abort; tile += gridDim.x, ++it) {
+            const int acc = it % C::NACC, ua = it / C::NACC;
+            if (!mbar_wait(&t_full[acc], ua & 1, abort, WAIT_NS)) break;
+            fence_after_sync();
+            const int tx = tile % a.tiles_x, r = tile / a.tiles_x;
+            const int x = tx * TX + (row & 7), y = (r % a.tiles_y) * TY + (row >> 3), z = r / a.tiles_y;
+            const bool inside = x < a.g.nx && y < a.g.ny;
+            const uint32_t tbase = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(acc * N);
+#pragma unroll 1
+            for (int p = p0; p < p0 + 4; ++p) {
+                const int ox = 2 * x + (p & 1), oy = 2 * y + ((p >> 1) & 1), oz = 2 * z + (p >> 2);
+                const bool ok = inside && ox < a.gout.nx && oy < a.gout.ny && oz < a.gout.nz;
+                const long long vox = ox + (long long)a.gout.nx * (oy + (long long)a.gout.ny * oz);
+#pragma unroll
+                for (int j = 0; j < COUT / 16; ++j) {
+                    float v[16];
+                    tmem_ld16(tbase + (uint32_t)(p * COUT + 16 * j), v);   // every lane: the load is warp-wide
+                    if (!ok) continue;
+                    __nv_bfloat16* o = a.out.ptr + vox * a.out.stride + a.out.c0 + 16 * j;
+                    const __nv_bfloat16* mk = a.mask ? a.mask + vox * a.mask_stride + a.mask_c0 + 16 * j : nullptr;
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        float f[8];
+#pragma unroll
+                        for (int e = 0; e < 8; ++e) f[e] = v[8 * h + e] + sbias[16 * j + 8 * h + e];
+                        if (a.accumulate) {
+                            uint4 old = *reinterpret_cast<const uint4*>(o + 8 * h);
+                            const __nv_bfloat162* ob = reinterpret_cast<const __nv_bfloat162*>(&old);
+#pragma unroll
+                            for (int e = 0; e < 4; ++e) {
+                                float2 t2 = __bfloat1622float2(ob[e]);
+                                f[2 * e] += t2.x;
+                                f[2 * e + 1] += t2.y;
+                            }
+                        }
+                        if (a.relu) {
+#pragma unroll
+                            for (int e = 0; e < 8; ++e) f[e] = fmaxf(f[e], 0.f);
+                        }
+                        if (mk) {
+                            uint4 mv = *reinterpret_cast<const uint4*>(mk + 8 * h);
+                            const __nv_bfloat162* mb = reinterpret_cast<const __nv_bfloat162*>(&mv);
+#pragma unroll
+                            for (int e = 0; e < 4; ++e) {
+                                float2 t2 = __bfloat1622float2(mb[e]);
+                                if (!(t2.x > 0.f)) f[2 * e] = 0.f;
+                                if (!(t2.y > 0.f)) f[2 * e + 1] = 0.f;
+                            }
+                        }
+                        uint4 w;
+                        __nv_bfloat162* wb2 = reinterpret_cast<__nv_bfloat162*>(&w);
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) wb2[e] = __floats2bfloat162_rn(f[2 * e], f[2 * e + 1]);
+                        *reinterpret_cast<uint4*>(o + 8 * h) = w;
+                    }
+                }
+            }
+            fence_before_sync();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&t_empty[acc]);
+        }
+    }
+    fence_before_sync();
+    __syncthreads();
+    if (warp == 1) {
+        fence_after_sync();
+        tmem_dealloc(tmem, C::NCOLS);
+    }
+    if (threadIdx.x == 0 && *abort && a.err) atomicExch(a.err, 1);
+}
+
+// [8][K][COUT] (parity p, input channel, output channel) -> [K/8][8 COUT][8]: K-major B with
+// column j = p COUT + n
+__global__ void k_pack_up_tc(const __nv_bfloat16* src, int K, int cout, __nv_bfloat16* dst)
+{
+    const int N = 8 * cout;
+    long long total = (long long)K * N;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+        const int kk = (int)(i & 7);
+        const long long q = i >> 3;
+        const int n = (int)(q % N), g = (int)(q / N);
+        const int p = n / cout, co = n - p * cout;
+        dst[i] = src[((long long)p * K + 8 * g + kk) * cout + co];
+    }
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
 {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
@@ -418,6 +647,53 @@ cudaError_t launch_cfg(const ConvArgs& a, const __nv_bfloat16* wpack, int* err, 
     return cudaGetLastError();
 }
 
+template <int CIN, int COUT>
+cudaError_t launch_up_cfg(const ConvArgs& a, const __nv_bfloat16* wpack, int* err, cudaStream_t s)
+{
+    using C = UpCfg<CIN, COUT>;
+    static std::once_flag once;
+    static cudaError_t attr = cudaSuccess;
+    std::call_once(once, [] {
+        attr = cudaFuncSetAttribute(k_up_tc<CIN, COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+    });
+    if (attr != cudaSuccess) return attr;
+    auto enc = encode_fn();
+    if (!enc) return cudaErrorNotSupported;
+    const Grid3 g = a.gin;
+    CUtensorMap m;
+    cuuint64_t dims[5] = {8, (cuuint64_t)(CIN / 8), (cuuint64_t)g.nx, (cuuint64_t)g.ny, (cuuint64_t)g.nz};
+    const cuuint64_t vb = (cuuint64_t)a.in.stride * 2;
+    cuuint64_t strides[4] = {16, vb, vb * g.nx, vb * g.nx * g.ny};
+    cuuint32_t box[5] = {8, 1, TX, TY, 1};
+    cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+    CUresult r = enc(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, (void*)(a.in.ptr + a.in.c0), dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+    TcArgs t;
+    std::memset(&t, 0, sizeof(t));
+    t.g = g;
+    t.gout = a.gout;
+    t.out = a.out;
+    t.wpack = wpack;
+    t.bias = a.bias;
+    t.relu = a.relu;
+    t.accumulate = a.accumulate;
+    t.mask = a.mask;
+    t.mask_stride = a.mask_stride;
+    t.mask_c0 = a.mask_c0;
+    t.tiles_x = (g.nx + TX - 1) / TX;
+    t.tiles_y = (g.ny + TY - 1) / TY;
+    t.ntiles = t.tiles_x * t.tiles_y * g.nz;
+    t.err = err;
+    t.stall_tile = -1;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    k_up_tc<CIN, COUT><<<(unsigned)std::max(1, std::min(t.ntiles, sms)), UP_THREADS, C::SMEM, s>>>(m, t);
+    return cudaGetLastError();
+}
+
 // Output channels per block: the whole layer where its weights fit next to the halo stages,
 // else slices of 32 (64 input channels) or 16 (128 input channels).
 int slice_width(int cin, int cout)
@@ -454,6 +730,29 @@ cudaError_t pack_conv3_tc(const __nv_bfloat16* w, int cin, int cout, __nv_bfloat
     k_pack_tc<<<(unsigned)std::min<long long>((n + 255) / 256, 4096), 256, 0, s>>>(w, cin, cout, nsl, nsl <= 32 ? 1 : 0,
                                                                                   wpack);
     return cudaGetLastError();
+}
+
+bool up_tc_supported(int cin, int cout)
+{
+    // (128, 64) runs on the 16^3 level: 32 tiles, each block would load 128 KB of weights for
+    // one tile, and the implicit-GEMM kernel is faster there (measured)
+    return (cin == 32 && cout == 16) || (cin == 64 && cout == 32);
+}
+
+cudaError_t pack_up_tc(const __nv_bfloat16* w, int cin, int cout, __nv_bfloat16* wpack, cudaStream_t s)
+{
+    long long n = 8LL * cin * cout;
+    k_pack_up_tc<<<(unsigned)std::min<long long>((n + 255) / 256, 4096), 256, 0, s>>>(w, cin, cout, wpack);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_up_tc(const ConvArgs& a, const __nv_bfloat16* wpack, int* err, cudaStream_t s)
+{
+    if (a.mode != UP || a.in.c0 % 8 || a.in.stride % 8 || a.out.c0 % 8 || a.out.stride % 8 ||
+        (a.mask && (a.mask_c0 % 8 || a.mask_stride % 8)) || !up_tc_supported(a.cin, a.cout))
+        return cudaErrorInvalidValue;
+    if (a.cin == 32) return launch_up_cfg<32, 16>(a, wpack, err, s);
+    return launch_up_cfg<64, 32>(a, wpack, err, s);
 }
 
 cudaError_t launch_conv3_tc(const ConvArgs& a, const __nv_bfloat16* wpack, int* err, cudaStream_t s)

@@ -27,5 +27,12 @@ cudaError_t pack_conv3_tc(const __nv_bfloat16* w, int cin, int cout, __nv_bfloat
 // null) is set to 1 if a wait inside the kernel timed out.
 cudaError_t launch_conv3_tc(const ConvArgs& a, const __nv_bfloat16* wpack, int* err, cudaStream_t s);
 
+// Transposed 2x2x2 convolution (UP, coarse -> fine; also the data gradient of a DOWN layer) on
+// the tensor-memory path, for (cin, cout) = (32, 16) and (64, 32). Weights [8][cin][cout]
+// are packed by pack_up_tc into [cin/8][8 cout][8]; same epilogue semantics as k_conv's UP mode.
+bool up_tc_supported(int cin, int cout);
+cudaError_t pack_up_tc(const __nv_bfloat16* w, int cin, int cout, __nv_bfloat16* wpack, cudaStream_t s);
+cudaError_t launch_up_tc(const ConvArgs& a, const __nv_bfloat16* wpack, int* err, cudaStream_t s);
+
 }  // namespace unet
 }  // namespace ocmc
