@@ -356,6 +356,21 @@ cudaError_t launch_conv_bk(const ConvArgs& a, cudaStream_t s)
     }
 }
 
+// The data gradient of a layer kind: 3x3x3 stays 3x3x3, DOWN and UP swap.
+Mode dgrad_mode(Mode m) { return m == DOWN ? UP : (m == UP ? DOWN : CONV3); }
+
+// Whether a convolution of kind m with (cin, cout) has a tensor-memory kernel, and its weight packing.
+bool tc_supported(Mode m, int cin, int cout)
+{
+    return m == CONV3 ? conv3_tc_supported(cin, cout) : (m == UP ? up_tc_supported(cin, cout) : down_tc_supported(cin, cout));
+}
+
+cudaError_t pack_tc(Mode m, const __nv_bfloat16* w, int cin, int cout, __nv_bfloat16* wpack, cudaStream_t s)
+{
+    return m == CONV3 ? pack_conv3_tc(w, cin, cout, wpack, s)
+                      : (m == UP ? pack_up_tc(w, cin, cout, wpack, s) : pack_down_tc(w, cin, cout, wpack, s));
+}
+
 cudaError_t launch_conv(const ConvArgs& a, cudaStream_t s)
 {
     // 16-byte copies and stores: channel offsets and strides in multiples of 8 (BF16)
@@ -364,6 +379,7 @@ cudaError_t launch_conv(const ConvArgs& a, cudaStream_t s)
         return cudaErrorInvalidValue;
     if (a.mode == CONV3 && a.wtc && conv3_tc_supported(a.cin, a.cout)) return launch_conv3_tc(a, a.wtc, a.err, s);
     if (a.mode == UP && a.wtc && up_tc_supported(a.cin, a.cout)) return launch_up_tc(a, a.wtc, a.err, s);
+    if (a.mode == DOWN && a.wtc && down_tc_supported(a.cin, a.cout)) return launch_down_tc(a, a.wtc, a.err, s);
     return a.cin % 32 == 0 ? launch_conv_bk<32>(a, s) : launch_conv_bk<16>(a, s);
 }
 
@@ -534,6 +550,8 @@ cudaError_t layer_bwd(ocmc_unet* u, const Layer& L, bool need_dx, cudaStream_t s
     a.gin = u->g[L.lout];
     a.gout = u->g[L.lin];
     a.w = L.wt;
+    a.wtc = u->tc ? L.wtc_t : nullptr;
+    a.err = u->kerr;
     return launch_conv(a, s);
 }
 
@@ -544,10 +562,8 @@ cudaError_t refresh_bf16(ocmc_unet* u, cudaStream_t s)
         k_weights_bf16<<<grid_for(m), 256, 0, s>>>(u->params + L.woff, L.taps, L.cin, L.cout, L.mode == CONV3,
                                                    L.wf, L.wt);
         cudaError_t e = cudaSuccess;
-        if (L.wtc_f)
-            e = L.mode == CONV3 ? pack_conv3_tc(L.wf, L.cin, L.cout, L.wtc_f, s) : pack_up_tc(L.wf, L.cin, L.cout, L.wtc_f, s);
-        if (e == cudaSuccess && L.wtc_t)
-            e = L.mode == CONV3 ? pack_conv3_tc(L.wt, L.cout, L.cin, L.wtc_t, s) : pack_up_tc(L.wt, L.cout, L.cin, L.wtc_t, s);
+        if (L.wtc_f) e = pack_tc(L.mode, L.wf, L.cin, L.cout, L.wtc_f, s);
+        if (e == cudaSuccess && L.wtc_t) e = pack_tc(dgrad_mode(L.mode), L.wt, L.cout, L.cin, L.wtc_t, s);
         if (e != cudaSuccess) return e;
     }
     return cudaGetLastError();
@@ -678,12 +694,13 @@ ocmc_status ocmc_unet_create(ocmc_unet** out, int device, int nx, int ny, int nz
         size_t m = (size_t)L.taps * L.cin * L.cout * sizeof(__nv_bfloat16);
         if (e == cudaSuccess) e = cudaMalloc(&L.wf, m);
         if (e == cudaSuccess) e = cudaMalloc(&L.wt, m);
-        // packed weights for the tensor-memory kernels: 3x3x3 layers both ways, UP layers forward,
-        // DOWN layers for their data gradient (a transposed convolution)
+        // packed weights for the tensor-memory kernels, forward and data gradient (the data
+        // gradient of a DOWN layer is an UP convolution and vice versa)
         if (L.mode == CONV3 && conv3_tc_supported(L.cin, L.cout) && e == cudaSuccess) e = cudaMalloc(&L.wtc_f, m);
         if (L.mode == CONV3 && conv3_tc_supported(L.cout, L.cin) && e == cudaSuccess) e = cudaMalloc(&L.wtc_t, m);
-        if (L.mode == UP && up_tc_supported(L.cin, L.cout) && e == cudaSuccess) e = cudaMalloc(&L.wtc_f, m);
-        if (L.mode == DOWN && up_tc_supported(L.cout, L.cin) && e == cudaSuccess) e = cudaMalloc(&L.wtc_t, m);
+        if (L.mode != CONV3 && tc_supported(L.mode, L.cin, L.cout) && e == cudaSuccess) e = cudaMalloc(&L.wtc_f, m);
+        if (L.mode != CONV3 && tc_supported(dgrad_mode(L.mode), L.cout, L.cin) && e == cudaSuccess)
+            e = cudaMalloc(&L.wtc_t, m);
     }
     if (e == cudaSuccess) e = cudaMalloc(&u->kerr, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(u->kerr, 0, sizeof(int));
@@ -909,8 +926,7 @@ ocmc_status ocmc_unet_test_layer(int device, int mode, int nx, int ny, int nz, i
     A((void**)&part, part_n * 4); A((void**)&dW, nw * 4); A((void**)&dW2, nw * 4);
     __nv_bfloat16 *pf = nullptr, *pt = nullptr;
     int* kerr = nullptr;
-    const bool tcf = (m == CONV3 && conv3_tc_supported(cin, cout)) || (m == UP && up_tc_supported(cin, cout));
-    const bool tct = (m == CONV3 && conv3_tc_supported(cout, cin)) || (m == DOWN && up_tc_supported(cout, cin));
+    const bool tcf = tc_supported(m, cin, cout), tct = tc_supported(dgrad_mode(m), cout, cin);
     if (tcf) A((void**)&pf, nw * 2);
     if (tct) A((void**)&pt, nw * 2);
     A((void**)&kerr, sizeof(int));
@@ -920,9 +936,8 @@ ocmc_status ocmc_unet_test_layer(int device, int mode, int nx, int ny, int nz, i
     if (e == cudaSuccess) e = cudaMemcpy(w32, w, nw * 4, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) {
         k_weights_bf16<<<grid_for(nw), 256>>>(w32, taps, cin, cout, m == CONV3, wf, wt);
-        if (tcf) e = m == CONV3 ? pack_conv3_tc(wf, cin, cout, pf, nullptr) : pack_up_tc(wf, cin, cout, pf, nullptr);
-        if (tct && e == cudaSuccess)
-            e = m == CONV3 ? pack_conv3_tc(wt, cout, cin, pt, nullptr) : pack_up_tc(wt, cout, cin, pt, nullptr);
+        if (tcf) e = pack_tc(m, wf, cin, cout, pf, nullptr);
+        if (tct && e == cudaSuccess) e = pack_tc(dgrad_mode(m), wt, cout, cin, pt, nullptr);
         ConvArgs a;
         std::memset(&a, 0, sizeof(a));
         a.mode = m; a.gin = gi; a.gout = go; a.in = Slice{dX, cin, 0}; a.out = Slice{dY, cout, 0};

@@ -57,7 +57,7 @@ uint64_t g_stall_ns = 0;
 
 struct TcArgs {
     Grid3 g;
-    Grid3 gout;                  // UP: the fine output grid
+    Grid3 gfine;                 // UP: the fine output grid; DOWN: the fine input grid
     Slice out;
     const __nv_bfloat16* wpack;
     const float* bias;
@@ -508,8 +508,8 @@ __global__ void __launch_bounds__(UP_THREADS, 1) k_up_tc(const __grid_constant__
 #pragma unroll 1
             for (int p = p0; p < p0 + 4; ++p) {
                 const int ox = 2 * x + (p & 1), oy = 2 * y + ((p >> 1) & 1), oz = 2 * z + (p >> 2);
-                const bool ok = inside && ox < a.gout.nx && oy < a.gout.ny && oz < a.gout.nz;
-                const long long vox = ox + (long long)a.gout.nx * (oy + (long long)a.gout.ny * oz);
+                const bool ok = inside && ox < a.gfine.nx && oy < a.gfine.ny && oz < a.gfine.nz;
+                const long long vox = ox + (long long)a.gfine.nx * (oy + (long long)a.gfine.ny * oz);
 #pragma unroll
                 for (int j = 0; j < COUT / 16; ++j) {
                     float v[16];
@@ -580,6 +580,238 @@ __global__ void k_pack_up_tc(const __nv_bfloat16* src, int K, int cout, __nv_bfl
         const int n = (int)(q % N), g = (int)(q / N);
         const int p = n / cout, co = n - p * cout;
         dst[i] = src[((long long)p * K + 8 * g + kk) * cout + co];
+    }
+}
+
+// ---- stride-2 2x2x2 convolution (DOWN: fine -> coarse) on tcgen05 -----------------------------
+// Rows are coarse output voxels, a tile of 8 (x) x 16 (y) voxels of one z-plane (row m = x + 8 y).
+// Input voxel of row (x, y, z) and parity p = (px, py, pz): (2x + px, 2y + py, 2z + pz) -- every
+// other voxel along each axis, which a TMA box cannot hand to a K-major descriptor, so eight
+// producer warps gather them: two threads per row m load the 16-byte channel runs of the row for
+// four parities each and every channel group and writes them to plane (p, g) of the stage, row m (16 bytes per
+// row, 2 KB per plane), then fences them for the tensor core and arrives on the stage's barrier.
+// One MMA chain of 8 CIN / 16 steps (K = parity x input channel, N = COUT) per tile; weights
+// [p][cin][cout] packed [p][cin/8][cout][8] stay in shared memory. The data gradient of an UP
+// layer is this same operation with the transposed weights.
+constexpr int DOWN_THREADS = 416;   // MMA warp, eight producer warps, four epilogue warps
+
+template <int CIN, int COUT>
+struct DownCfg {
+    static constexpr int G = CIN / 8;
+    static constexpr int NS = CIN <= 16 ? 4 : 2;                     // input stages (64 KB each for 32 channels)
+    static constexpr uint32_t W_BYTES = 8u * CIN * COUT * 2;
+    static constexpr uint32_t PLANE = 128 * 16;
+    static constexpr uint32_t STAGE = 8 * G * PLANE;                 // eight parities x channel groups
+    static constexpr uint32_t BAR_OFF = W_BYTES + NS * STAGE;
+    static constexpr uint32_t BIAS_OFF = BAR_OFF + 256;
+    static constexpr uint32_t SMEM = BIAS_OFF + COUT * 4;
+    static constexpr uint32_t COLS = 2 * COUT;
+    static constexpr uint32_t NCOLS = COLS <= 32 ? 32 : COLS <= 64 ? 64 : COLS <= 128 ? 128 : 256;
+    static_assert(CIN % 16 == 0 && COUT % 16 == 0 && COUT <= 128, "DOWN tile shape");
+    static_assert(W_BYTES % 128 == 0 && SMEM <= 232448, "shared memory per block");
+};
+
+template <int CIN, int COUT>
+__global__ void __launch_bounds__(DOWN_THREADS, 1) k_down_tc(const TcArgs a, const __nv_bfloat16* __restrict__ in,
+                                                             int in_stride)
+{
+    using C = DownCfg<CIN, COUT>;
+    constexpr int NS = C::NS, G = C::G;
+    extern __shared__ __align__(1024) uint8_t smem[];
+    uint8_t* sw = smem;
+    uint8_t* sh = smem + C::W_BYTES;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + C::BAR_OFF);
+    uint64_t* w_full = bars;
+    uint64_t* h_full = bars + 1;
+    uint64_t* h_empty = bars + 1 + NS;
+    uint64_t* t_full = bars + 1 + 2 * NS;
+    uint64_t* t_empty = bars + 3 + 2 * NS;
+    uint64_t* drain = bars + 5 + 2 * NS;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 6 + 2 * NS);
+    volatile int* abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
+    float* sbias = reinterpret_cast<float*>(smem + C::BIAS_OFF);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int i = threadIdx.x; i < COUT; i += DOWN_THREADS) sbias[i] = a.bias ? a.bias[i] : 0.f;
+    if (threadIdx.x == 0) {
+        mbar_init(w_full, 1);
+        for (int i = 0; i < NS; ++i) {
+            mbar_init(&h_full[i], 256);             // every producer thread arrives
+            mbar_init(&h_empty[i], 1);
+        }
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&t_full[i], 1);
+            mbar_init(&t_empty[i], 4);
+        }
+        mbar_init(drain, 1);
+        *abort = 0;
+        fence_mbar_init();
+    }
+    if (warp == 0) tmem_alloc(tmem_slot, C::NCOLS);
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        // ---- weights, then MMA issue: D[128 x COUT] = sum over parities of A_p[128 x CIN] W_p ----
+        if (lane == 0) {
+            mbar_expect_tx(w_full, C::W_BYTES);
+            const uint8_t* wsrc = reinterpret_cast<const uint8_t*>(a.wpack);
+            for (uint32_t off = 0; off < C::W_BYTES; off += 32768u)
+                bulk_load(sw + off, wsrc + off, min(32768u, C::W_BYTES - off), w_full);
+            bool issued = false, weights = mbar_wait(w_full, 0, abort, WAIT_NS);
+            if (weights) {
+                fence_after_sync();
+                constexpr uint32_t idesc = idesc_bf16_f32(128, COUT);
+                const uint32_t sw_addr = saddr(sw), sh_addr = saddr(sh);
+                int it = 0;
+                for (int tile = blockIdx.x; tile < a.ntiles && !*abort; tile += gridDim.x, ++it) {
+                    const int acc = it & 1, ua = it >> 1;
+                    if (!mbar_wait(&t_empty[acc], (ua & 1) ^ 1, abort, WAIT_NS)) break;
+                    fence_after_sync();
+                    const int st = it % NS, u = it / NS;
+                    if (!mbar_wait(&h_full[st], u & 1, abort, WAIT_NS)) break;
+                    fence_after_sync();
+                    const uint32_t d0 = tmem + (uint32_t)(acc * COUT);
+                    const uint32_t stage = sh_addr + (uint32_t)st * C::STAGE;
+#pragma unroll
+                    for (int p = 0; p < 8; ++p)
+#pragma unroll
+                        for (int k = 0; k < CIN / 16; ++k) {
+                            const uint32_t pg = (uint32_t)(p * G + 2 * k);
+                            mma_f16(d0, sdesc(stage + pg * C::PLANE, C::PLANE, 128),
+                                    sdesc(sw_addr + pg * COUT * 16, COUT * 16, 128), idesc, (p | k) ? 1u : 0u);
+                        }
+                    mma_commit(&h_empty[st]);
+                    mma_commit(&t_full[acc]);
+                    issued = true;
+                }
+            } else {
+                wait_bounded(w_full, 0);               // the weight copy must land before the block exits
+            }
+            if (*abort && issued) {   // MMAs in flight must finish before tensor memory is freed
+                mma_commit(drain);
+                wait_bounded(drain, 0);
+            }
+        }
+        __syncwarp();
+    } else if (warp <= 8) {
+        // ---- producers: threads m and m + 128 gather row m of the (parity, channel group) planes
+        // of parities 0-3 and 4-7 ----
+        const int m = (threadIdx.x - 32) & 127, p_lo = ((threadIdx.x - 32) >> 7) * 4;
+        constexpr int PB = G <= 2 ? 4 : 2;           // parities per batch of loads in flight
+        int it = 0;
+        for (int tile = blockIdx.x; tile < a.ntiles && !*abort; tile += gridDim.x, ++it) {
+            const int st = it % NS, u = it / NS;
+            if (!mbar_wait(&h_empty[st], (u & 1) ^ 1, abort, WAIT_NS)) break;
+            const int tx = tile % a.tiles_x, r = tile / a.tiles_x;
+            const int x = tx * TX + (m & 7), y = (r % a.tiles_y) * TY + (m >> 3), z = r / a.tiles_y;
+            const bool rowin = x < a.g.nx && y < a.g.ny;
+            uint8_t* dst = sh + st * C::STAGE + m * 16;
+#pragma unroll
+            for (int p0 = p_lo; p0 < p_lo + 4; p0 += PB) {
+                uint4 v[PB][G];
+#pragma unroll
+                for (int q = 0; q < PB; ++q) {
+                    const int p = p0 + q;
+                    const int ix = 2 * x + (p & 1), iy = 2 * y + ((p >> 1) & 1), iz = 2 * z + (p >> 2);
+                    const bool ok = rowin && ix < a.gfine.nx && iy < a.gfine.ny && iz < a.gfine.nz;
+                    const long long vox = ok ? ix + (long long)a.gfine.nx * (iy + (long long)a.gfine.ny * iz) : 0;
+                    const uint4* src = reinterpret_cast<const uint4*>(in + vox * in_stride);
+#pragma unroll
+                    for (int g = 0; g < G; ++g) v[q][g] = ok ? __ldg(src + g) : make_uint4(0u, 0u, 0u, 0u);
+                }
+#pragma unroll
+                for (int q = 0; q < PB; ++q)
+#pragma unroll
+                    for (int g = 0; g < G; ++g)
+                        *reinterpret_cast<uint4*>(dst + ((p0 + q) * G + g) * C::PLANE) = v[q][g];
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // visible to the tensor core
+            mbar_arrive(&h_full[st]);
+        }
+    } else {
+        // ---- epilogue (warps 9-12): tensor memory -> bias / accumulate / ReLU / mask -> BF16 ----
+        const int q = warp & 3;                       // the tensor-memory lane quarter of this warp
+        const int row = 32 * q + lane;
+        int it = 0;
+        for (int tile = blockIdx.x; tile < a.ntiles && !*abort; tile += gridDim.x, ++it) {
+            const int acc = it & 1, ua = it >> 1;
+            if (!mbar_wait(&t_full[acc], ua & 1, abort, WAIT_NS)) break;
+            fence_after_sync();
+            const int tx = tile % a.tiles_x, r = tile / a.tiles_x;
+            const int x = tx * TX + (row & 7), y = (r % a.tiles_y) * TY + (row >> 3), z = r / a.tiles_y;
+            const bool ok = x < a.g.nx && y < a.g.ny;
+            const long long vox = x + (long long)a.g.nx * (y + (long long)a.g.ny * z);
+            const uint32_t tbase = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(acc * COUT);
+#pragma unroll
+            for (int j = 0; j < COUT / 16; ++j) {
+                float v[16];
+                tmem_ld16(tbase + (uint32_t)(16 * j), v);   // every lane: the load is warp-wide
+                if (!ok) continue;
+                __nv_bfloat16* o = a.out.ptr + vox * a.out.stride + a.out.c0 + 16 * j;
+                const __nv_bfloat16* mk = a.mask ? a.mask + vox * a.mask_stride + a.mask_c0 + 16 * j : nullptr;
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    float f[8];
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) f[e] = v[8 * h + e] + sbias[16 * j + 8 * h + e];
+                    if (a.accumulate) {
+                        uint4 old = *reinterpret_cast<const uint4*>(o + 8 * h);
+                        const __nv_bfloat162* ob = reinterpret_cast<const __nv_bfloat162*>(&old);
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            float2 t2 = __bfloat1622float2(ob[e]);
+                            f[2 * e] += t2.x;
+                            f[2 * e + 1] += t2.y;
+                        }
+                    }
+                    if (a.relu) {
+#pragma unroll
+                        for (int e = 0; e < 8; ++e) f[e] = fmaxf(f[e], 0.f);
+                    }
+                    if (mk) {
+                        uint4 mv = *reinterpret_cast<const uint4*>(mk + 8 * h);
+                        const __nv_bfloat162* mb = reinterpret_cast<const __nv_bfloat162*>(&mv);
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            float2 t2 = __bfloat1622float2(mb[e]);
+                            if (!(t2.x > 0.f)) f[2 * e] = 0.f;
+                            if (!(t2.y > 0.f)) f[2 * e + 1] = 0.f;
+                        }
+                    }
+                    uint4 w;
+                    __nv_bfloat162* wb2 = reinterpret_cast<__nv_bfloat162*>(&w);
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) wb2[e] = __floats2bfloat162_rn(f[2 * e], f[2 * e + 1]);
+                    *reinterpret_cast<uint4*>(o + 8 * h) = w;
+                }
+            }
+            fence_before_sync();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&t_empty[acc]);
+        }
+    }
+    fence_before_sync();
+    __syncthreads();
+    if (warp == 0) {
+        fence_after_sync();
+        tmem_dealloc(tmem, C::NCOLS);
+    }
+    if (threadIdx.x == 0 && *abort && a.err) atomicExch(a.err, 1);
+}
+
+// [8][K][N] -> [8][K/8][N][8]: per parity a K-major B of N = cout rows
+__global__ void k_pack_down_tc(const __nv_bfloat16* src, int K, int N, __nv_bfloat16* dst)
+{
+    long long total = 8LL * K * N;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+        const int kk = (int)(i & 7);
+        long long q = i >> 3;
+        const int n = (int)(q % N);
+        q /= N;
+        const int g = (int)(q % (K / 8)), p = (int)(q / (K / 8));
+        dst[i] = src[((long long)p * K + 8 * g + kk) * N + n];
     }
 }
 
@@ -673,7 +905,7 @@ cudaError_t launch_up_cfg(const ConvArgs& a, const __nv_bfloat16* wpack, int* er
     TcArgs t;
     std::memset(&t, 0, sizeof(t));
     t.g = g;
-    t.gout = a.gout;
+    t.gfine = a.gout;
     t.out = a.out;
     t.wpack = wpack;
     t.bias = a.bias;
@@ -691,6 +923,41 @@ cudaError_t launch_up_cfg(const ConvArgs& a, const __nv_bfloat16* wpack, int* er
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     k_up_tc<CIN, COUT><<<(unsigned)std::max(1, std::min(t.ntiles, sms)), UP_THREADS, C::SMEM, s>>>(m, t);
+    return cudaGetLastError();
+}
+
+template <int CIN, int COUT>
+cudaError_t launch_down_cfg(const ConvArgs& a, const __nv_bfloat16* wpack, int* err, cudaStream_t s)
+{
+    using C = DownCfg<CIN, COUT>;
+    static std::once_flag once;
+    static cudaError_t attr = cudaSuccess;
+    std::call_once(once, [] {
+        attr = cudaFuncSetAttribute(k_down_tc<CIN, COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+    });
+    if (attr != cudaSuccess) return attr;
+    TcArgs t;
+    std::memset(&t, 0, sizeof(t));
+    t.g = a.gout;                    // tiles over the coarse output grid
+    t.gfine = a.gin;
+    t.out = a.out;
+    t.wpack = wpack;
+    t.bias = a.bias;
+    t.relu = a.relu;
+    t.accumulate = a.accumulate;
+    t.mask = a.mask;
+    t.mask_stride = a.mask_stride;
+    t.mask_c0 = a.mask_c0;
+    t.tiles_x = (t.g.nx + TX - 1) / TX;
+    t.tiles_y = (t.g.ny + TY - 1) / TY;
+    t.ntiles = t.tiles_x * t.tiles_y * t.g.nz;
+    t.err = err;
+    t.stall_tile = -1;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    k_down_tc<CIN, COUT><<<(unsigned)std::max(1, std::min(t.ntiles, sms)), DOWN_THREADS, C::SMEM, s>>>(
+        t, a.in.ptr + a.in.c0, a.in.stride);
     return cudaGetLastError();
 }
 
@@ -753,6 +1020,30 @@ cudaError_t launch_up_tc(const ConvArgs& a, const __nv_bfloat16* wpack, int* err
         return cudaErrorInvalidValue;
     if (a.cin == 32) return launch_up_cfg<32, 16>(a, wpack, err, s);
     return launch_up_cfg<64, 32>(a, wpack, err, s);
+}
+
+bool down_tc_supported(int cin, int cout)
+{
+    // measured against the implicit-GEMM kernel on GB300: (32, 64) over 64^3 -> 32^3 15.4 us
+    // instead of 19.0; (16, 32) over 128^3 -> 64^3 37.6 us instead of 36.0 (its 2 KB channel runs per
+    // voxel keep the gathering warps latency-bound), and (64, 128) on the 16^3 level has 32 tiles:
+    // those two stay on the implicit-GEMM kernel
+    return cin == 32 && cout == 64;
+}
+
+cudaError_t pack_down_tc(const __nv_bfloat16* w, int cin, int cout, __nv_bfloat16* wpack, cudaStream_t s)
+{
+    long long n = 8LL * cin * cout;
+    k_pack_down_tc<<<(unsigned)std::min<long long>((n + 255) / 256, 4096), 256, 0, s>>>(w, cin, cout, wpack);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_down_tc(const ConvArgs& a, const __nv_bfloat16* wpack, int* err, cudaStream_t s)
+{
+    if (a.mode != DOWN || a.in.c0 % 8 || a.in.stride % 8 || a.out.c0 % 8 || a.out.stride % 8 ||
+        (a.mask && (a.mask_c0 % 8 || a.mask_stride % 8)) || !down_tc_supported(a.cin, a.cout))
+        return cudaErrorInvalidValue;
+    return launch_down_cfg<32, 64>(a, wpack, err, s);
 }
 
 cudaError_t launch_conv3_tc(const ConvArgs& a, const __nv_bfloat16* wpack, int* err, cudaStream_t s)

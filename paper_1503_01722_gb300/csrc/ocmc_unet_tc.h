@@ -34,5 +34,12 @@ bool up_tc_supported(int cin, int cout);
 cudaError_t pack_up_tc(const __nv_bfloat16* w, int cin, int cout, __nv_bfloat16* wpack, cudaStream_t s);
 cudaError_t launch_up_tc(const ConvArgs& a, const __nv_bfloat16* wpack, int* err, cudaStream_t s);
 
+// Stride-2 2x2x2 convolution (DOWN, fine -> coarse; also the data gradient of an UP layer) on the
+// tensor-memory path, for (cin, cout) = (32, 64). Weights [8][cin][cout] are packed
+// by pack_down_tc into [8][cin/8][cout][8]; same epilogue semantics as k_conv's DOWN mode.
+bool down_tc_supported(int cin, int cout);
+cudaError_t pack_down_tc(const __nv_bfloat16* w, int cin, int cout, __nv_bfloat16* wpack, cudaStream_t s);
+cudaError_t launch_down_tc(const ConvArgs& a, const __nv_bfloat16* wpack, int* err, cudaStream_t s);
+
 }  // namespace unet
 }  // namespace ocmc

@@ -71,10 +71,11 @@ def test_conv3_large_grid(ocmc, cin, cout):
 
 @pytest.mark.parametrize("mode,cin,cout", [(2, 32, 16), (2, 64, 32), (2, 128, 64), (1, 16, 32), (1, 32, 64),
                                             (1, 64, 128)])
-def test_transposed_conv_large_grid(ocmc, mode, cin, cout):
-    """The transposed 2x2x2 convolution on the tensor-memory path -- an UP layer's forward, a DOWN
-    layer's data gradient -- over 288 to 576 tiles of 128 coarse voxels, so that every persistent
-    block runs several tiles through its accumulator sets and input stages."""
+def test_strided_conv_large_grid(ocmc, mode, cin, cout):
+    """The 2x2x2 convolutions on the tensor-memory path -- DOWN (stride 2) and UP (transposed),
+    forward and data gradient of each layer kind -- over 288 to 576 tiles of 128 coarse voxels,
+    so that every persistent block runs several tiles through its accumulator sets and input
+    stages."""
     rng = np.random.default_rng(mode * 100 + cin + cout)
     fine = (48, 96, 64) if max(cin, cout) >= 64 else (48, 80, 128)
     coarse = tuple(s // 2 for s in fine)
@@ -84,9 +85,13 @@ def test_transposed_conv_large_grid(ocmc, mode, cin, cout):
     W = U.bf16(rng.standard_normal((8, cin, cout)) / np.sqrt(8 * cin))
     dy = U.bf16(rng.standard_normal(gout + (cout,)))
     y, dx, _ = ocmc.unet_test_layer(mode, fine, cin, cout, x, W, dy)
-    got, ref = (y, U.up(x, W)) if mode == 2 else (dx, U.down_dx(dy, W, x.shape))
-    assert np.allclose(got, ref, rtol=8e-3, atol=1e-2 * np.abs(ref).max())
-    assert rel_l2(got, ref) < 4e-3
+    if mode == 2:
+        pairs = ((y, U.up(x, W)), (dx, U.up_dx(dy, W)))
+    else:
+        pairs = ((y, U.down(x, W)), (dx, U.down_dx(dy, W, x.shape)))
+    for got, ref in pairs:
+        assert np.allclose(got, ref, rtol=8e-3, atol=1e-2 * np.abs(ref).max())
+        assert rel_l2(got, ref) < 4e-3
 
 
 def test_tensor_memory_path_matches_mma_path(ocmc, monkeypatch):
