@@ -38,7 +38,7 @@ DRAM_BYTES_PER_LAUNCH = {("photon_slab_120", 100_000_000): 20.235e9}
 # the same (predicated-on) for the beamlet-mode kernel (hash tallies) on the 512-beamlet CT
 # workload, measured by ncu on full runs of the same workload with every beamlet's histories
 # scaled by 0.2
-INST_PER_LANE_STEP_BEAMLETS = 612.0
+INST_PER_LANE_STEP_BEAMLETS = 607.2
 # the library transports a run in launches of at most this many histories (plus one finalize)
 RUN_CHUNK = 100_000_000
 
