@@ -29,9 +29,9 @@ import ocmc_inputs as I  # noqa: E402
 
 # Predicated-on thread-instructions per lane-step of the transport kernel (ncu
 # smsp__thread_inst_executed_pred_on.sum divided by the kernel's own lane-step counter, one
-# launch of 2e7 histories of the default workload) and DRAM bytes of a full launch, from the ncu
-# captures summarised in profiles/k_transport_photon_slab_120.md (re-measured whenever the
-# kernel changes). Lanes that a branch switched off are not counted.
+# launch of 2e7 histories of the default workload) and DRAM bytes of a full launch, from ncu
+# captures of the current kernel on GB300 (re-measured whenever the kernel changes). Lanes that
+# a branch switched off are not counted.
 INST_PER_LANE_STEP = 595.5
 # DRAM bytes of one transport launch measured by ncu on the full default workload
 DRAM_BYTES_PER_LAUNCH = {("photon_slab_120", 100_000_000): 20.235e9}
