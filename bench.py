@@ -216,73 +216,94 @@ def cpu_baseline_beamlets(ph, spec, bl, target_s=12.0):
             "sample": f"the first min(n, 4000) histories of beamlets 0..{k - 1}: {done} histories, {t_total:.1f} s"}
 
 
-def run_beamlets_bench(args, make, desc):
-    """Batched beamlets: one step = one replay of the captured launch over all beamlets."""
+def beamlets_measure(bl_scale, steps, warmup, e2e_steps):
+    """Batched beamlets on the CT-like phantom: one step = one replay of the captured launch over
+    all beamlets, timed on the device with L2 flushed between steps; the end-to-end leg times
+    phantom upload, beamlet set-up (pilot sizing and graph capture), the run and every beamlet's
+    sparse dose read back to the host. Returns the phantom, spectrum and beamlets with the
+    measured record."""
     import torch
     from paper_1503_01722_gb300 import ocmc
-    ph, spec, bl = make()
-    if args.beamlet_scale != 1.0:
-        bl = [dict(b, n_histories=max(1, int(b["n_histories"] * args.beamlet_scale))) for b in bl]
+    ph, spec, bl = I.beamlets_ct()
+    if bl_scale != 1.0:
+        bl = [dict(b, n_histories=max(1, int(b["n_histories"] * bl_scale))) for b in bl]
     n_total = sum(b["n_histories"] for b in bl)
     eng = ocmc.Engine(0)
-    eng.create_phantom(ph)
-    eng.set_beamlets(0, spec[0], spec[1], bl)
-    eng.run_beamlets(seed=1)                      # sizes the tables (pilots) and captures the graph
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-    for _ in range(args.warmup):
-        eng.run_beamlets(seed=1)
-    ms = []
-    with ClockSampler(0) as clk:
-        for k in range(args.steps):
-            flush.fill_(float(k))
-            torch.cuda.synchronize()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record()
+    try:
+        eng.create_phantom(ph)
+        eng.set_beamlets(0, spec[0], spec[1], bl)
+        eng.run_beamlets(seed=1)                      # sizes the tables (pilots) and captures the graph
+        flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+        for _ in range(warmup):
             eng.run_beamlets(seed=1)
-            e1.record()
-            e1.synchronize()
-            ms.append(e0.elapsed_time(e1))
-    st = eng.stats()
-    # end to end: phantom upload, beamlet set-up (pilot sizing + capture), run, all sparse outputs to host
+        ms = []
+        with ClockSampler(0) as clk:
+            for k in range(steps):
+                flush.fill_(float(k))
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                eng.run_beamlets(seed=1)
+                e1.record()
+                e1.synchronize()
+                ms.append(e0.elapsed_time(e1))
+        st = eng.stats()
+    finally:
+        eng.close()
     e2e_ms, nnz_bytes = [], 0
-    for k in range(max(1, args.steps)):
+    for k in range(max(1, e2e_steps)):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         e2 = ocmc.Engine(0)
-        e2.create_phantom(ph)
-        e2.set_beamlets(0, spec[0], spec[1], bl)
-        e2.run_beamlets(seed=1)
-        nnz_bytes = sum(idx.nbytes + dose.nbytes for idx, dose in e2.beamlet_doses())
+        try:
+            e2.create_phantom(ph)
+            e2.set_beamlets(0, spec[0], spec[1], bl)
+            e2.run_beamlets(seed=1)
+            nnz_bytes = sum(idx.nbytes + dose.nbytes for idx, dose in e2.beamlet_doses())
+        finally:
+            e2.close()
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
-        e2.close()
     clocks = clk.summary()
-    kern = statistics.mean(ms)
-    line = {
-        "metric": "histories/s", "value": n_total * args.steps / (sum(ms) / 1e3), "unit": "histories/s",
-        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": kern, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": desc, "histories_per_step": n_total, "beamlets": len(bl),
-                   "l2": "flushed between steps (256 MB write)", "seed": 1},
-        "e2e": {"value": n_total / (statistics.mean(e2e_ms) / 1e3), "unit": "histories/s",
-                "h2d_bytes_per_step": int(ph.density.size * 5), "d2h_bytes_per_step": int(nnz_bytes)},
-        "gpu_launches": args.steps,
-        "clocks": clocks,
-        "kernel_stats_last_step": {k: v for k, v in st.items() if isinstance(v, (int, float))},
-    }
     peaks = measured_peaks()
     sm_mhz = clocks["sm_mhz"] or peaks.get("sm_max_mhz", 2070.0)
     peak = sm_peak_thread_inst(sm_mhz) / 1e12
     kern_ms = st["last_run_ms"]
     achieved = (None if INST_PER_LANE_STEP_BEAMLETS is None else
                 st["lane_steps"] * INST_PER_LANE_STEP_BEAMLETS / (kern_ms / 1e3) / 1e12)
-    line["roofline"] = {"bound": "alu", "kernel": "k_transport (beamlet mode)", "achieved": achieved, "peak": peak,
-                        "unit": "Tinst/s", "frac": None if achieved is None else achieved / peak,
-                        "peak_basis": f"152 SMs x 128 lanes x median SM clock under load ({sm_mhz:.0f} MHz)",
-                        "traffic": None, "kernel_ms": kern_ms, "lane_steps_per_launch": st["lane_steps"]}
+    rec = {
+        "metric": "histories/s", "value": n_total * steps / (sum(ms) / 1e3), "unit": "histories/s",
+        "steps": steps, "warmup": warmup, "ms_per_step": statistics.mean(ms), "histories_per_step": n_total,
+        "beamlets": len(bl),
+        "e2e": {"value": n_total / (statistics.mean(e2e_ms) / 1e3), "unit": "histories/s",
+                "h2d_bytes_per_step": int(ph.density.size * 5), "d2h_bytes_per_step": int(nnz_bytes)},
+        "roofline": {"bound": "alu", "kernel": "k_transport (beamlet mode)", "achieved": achieved, "peak": peak,
+                     "unit": "Tinst/s", "frac": None if achieved is None else achieved / peak,
+                     "peak_basis": f"152 SMs x 128 lanes x median SM clock under load ({sm_mhz:.0f} MHz)",
+                     "traffic": None, "kernel_ms": kern_ms, "lane_steps_per_launch": st["lane_steps"]},
+        "clocks": clocks,
+        "kernel_stats_last_step": {k: v for k, v in st.items() if isinstance(v, (int, float))},
+    }
+    return ph, spec, bl, rec
+
+
+def run_beamlets_bench(args, make, desc):
+    """Batched beamlets: one step = one replay of the captured launch over all beamlets."""
+    ph, spec, bl, r = beamlets_measure(args.beamlet_scale, args.steps, args.warmup, args.steps)
+    line = {
+        "metric": "histories/s", "value": r["value"], "unit": "histories/s",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms_per_step"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": desc, "histories_per_step": r["histories_per_step"], "beamlets": r["beamlets"],
+                   "l2": "flushed between steps (256 MB write)", "seed": 1},
+        "e2e": r["e2e"],
+        "gpu_launches": args.steps,
+        "clocks": r["clocks"],
+        "kernel_stats_last_step": r["kernel_stats_last_step"],
+        "roofline": r["roofline"],
+    }
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_beamlets(ph, spec, bl)
     print(json.dumps(line))
-    eng.close()
 
 
 def run_denoiser_bench(args, desc):
@@ -605,6 +626,8 @@ def main():
                     help="--impl reference: CPU seconds the oracle's timed and warm-up steps may take together")
     ap.add_argument("--no-throughput-run", action="store_true",
                     help="skip the half-slab throughput record (1e9 histories of each beam) of the default line")
+    ap.add_argument("--no-beamlets", action="store_true",
+                    help="default workload: leave out the batched-beamlet record")
     ap.add_argument("--no-denoiser", action="store_true",
                     help="default workload: skip the plain-vs-denoised time-to-1%% record")
     # held-out cases 1, 2, 6, 7 of the study: two photon and two electron beams whose judges reach an
@@ -794,6 +817,16 @@ def main():
                 "config": WORKLOADS["half_slab_throughput"][2], "clocks": r["clocks"]}
         except Exception as e:
             line["half_slab_throughput"] = {"error": f"{type(e).__name__}: {e}"}
+    if rank == 0 and world == 1 and args.workload == "photon_slab_120" and not args.no_beamlets and \
+            not args.histories:
+        # the batched-beamlet configuration (512 beamlets, one graph-captured launch), three
+        # timed replays after one warm-up, and one end-to-end pass
+        try:
+            _, _, _, r = beamlets_measure(1.0, 3, 1, 1)
+            r["config"] = WORKLOADS["beamlets_ct"][2]
+            line["beamlets"] = r
+        except Exception as e:
+            line["beamlets"] = {"error": f"{type(e).__name__}: {e}"}
     if rank == 0 and world == 1 and args.workload == "photon_slab_120" and not args.no_denoiser and not args.histories:
         eng.close()
         try:

@@ -395,10 +395,19 @@ __global__ void k_transpose_pnc(const float* src, int taps, int n, int c, float*
     }
 }
 
-// Weight gradient of a 3x3x3 convolution over grid g (input and output) into dW [27][cin][cout].
+// Weight gradient of a 3x3x3 convolution over grid g (input and output) into dW [27][cin][cout]:
+// on tcgen05 where that kernel covers the channel counts (tc), else on mma.sync.
 cudaError_t launch_wgrad3(Grid3 g, Slice x, Slice dy, int cin, int cout, float* part, size_t part_cap, float* dW,
-                          cudaStream_t s)
+                          bool tc, int* err, cudaStream_t s)
 {
+    if (tc && wgrad3_tc_fits(cin, cout, g.nx) && x.c0 % 8 == 0 && x.stride % 8 == 0 && dy.c0 % 8 == 0 &&
+        dy.stride % 8 == 0) {
+        int parts = 0;
+        cudaError_t e = launch_wgrad3_tc(g, x, dy, cin, cout, part, part_cap, err, s, &parts);
+        if (e != cudaSuccess) return e;
+        sum_rows(part, parts, 27LL * cin * cout, dW, s);
+        return cudaGetLastError();
+    }
     Wgrad3Args a;
     a.g = g;
     a.in = x;
@@ -431,7 +440,7 @@ cudaError_t launch_wgrad3(Grid3 g, Slice x, Slice dy, int cin, int cout, float* 
 
 // Weight gradient of one layer into dW (FP32, [taps][cin][cout]).
 cudaError_t launch_wgrad(Mode mode, Grid3 gin, Grid3 gout, Slice x, Slice dy, int cin, int cout, float* part,
-                         size_t part_cap, float* dW, cudaStream_t s)
+                         size_t part_cap, float* dW, bool tc, int* err, cudaStream_t s)
 {
     // UP layers are handled as DOWN over (dy, x) with the roles of the grids swapped:
     // dW[p][c][n] = sum_u x[u][c] dy[2u+p][n]  ==  sum_u (DOWN gather of dy)[u][n] x[u][c]
@@ -443,7 +452,7 @@ cudaError_t launch_wgrad(Mode mode, Grid3 gin, Grid3 gout, Slice x, Slice dy, in
     a.dy = dy;
     a.cin = cin;
     a.cout = cout;
-    if (mode == CONV3) return launch_wgrad3(gout, x, dy, cin, cout, part, part_cap, dW, s);
+    if (mode == CONV3) return launch_wgrad3(gout, x, dy, cin, cout, part, part_cap, dW, tc, err, s);
     const int taps = 8;
     long long rows = gout.n();
     int bc = std::min(cin, 64), bn = std::min(cout, 64);
@@ -502,13 +511,14 @@ cudaError_t layer_bwd(ocmc_unet* u, const Layer& L, bool need_dx, cudaStream_t s
     if (L.mode == UP) {
         // dW[p][c][n] = sum_u x[u][c] dy[2u+p][n]: a DOWN-gather weight gradient over the coarse
         // grid with operands (dy as gathered input, x as rows), computed into [p][n][c], then transposed
-        e = launch_wgrad(DOWN, u->g[L.lout], u->g[L.lin], dy, x, L.cout, L.cin, u->part, u->part_n, u->tmpw, s);
+        e = launch_wgrad(DOWN, u->g[L.lout], u->g[L.lin], dy, x, L.cout, L.cin, u->part, u->part_n, u->tmpw, u->tc,
+                         u->kerr, s);
         if (e != cudaSuccess) return e;
         long long m = 8LL * L.cin * L.cout;          // [p][n][c] -> grads [p][c][n]
         k_transpose_pnc<<<grid_for(m), 256, 0, s>>>(u->tmpw, 8, L.cout, L.cin, u->grads + L.woff);
     } else {
         e = launch_wgrad(L.mode, u->g[L.lin], u->g[L.lout], x, dy, L.cin, L.cout, u->part, u->part_n,
-                         u->grads + L.woff, s);
+                         u->grads + L.woff, u->tc, u->kerr, s);
         if (e != cudaSuccess) return e;
     }
     long long nout = u->g[L.lout].n();
@@ -958,13 +968,15 @@ ocmc_status ocmc_unet_test_layer(int device, int mode, int nx, int ny, int nz, i
     }
     if (e == cudaSuccess) {
         if (m == UP) {
-            e = launch_wgrad(DOWN, go, gi, Slice{dDY, cout, 0}, Slice{dX, cin, 0}, cout, cin, part, part_n, dW2, nullptr);
+            e = launch_wgrad(DOWN, go, gi, Slice{dDY, cout, 0}, Slice{dX, cin, 0}, cout, cin, part, part_n, dW2, true,
+                             kerr, nullptr);
             if (e == cudaSuccess) {
                 k_transpose_pnc<<<grid_for(nw), 256>>>(dW2, 8, cout, cin, dW);
                 e = cudaGetLastError();
             }
         } else {
-            e = launch_wgrad(m, gi, go, Slice{dX, cin, 0}, Slice{dDY, cout, 0}, cin, cout, part, part_n, dW, nullptr);
+            e = launch_wgrad(m, gi, go, Slice{dX, cin, 0}, Slice{dDY, cout, 0}, cin, cout, part, part_n, dW, true, kerr,
+                             nullptr);
         }
     }
     if (e == cudaSuccess) e = cudaDeviceSynchronize();

@@ -978,6 +978,8 @@ long long tc_blocks(Grid3 g, int tz, int slices)
 
 }  // namespace
 
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() { return encode_fn(); }
+
 void conv3_tc_test_stall(int tile, uint64_t ns)
 {
     g_stall_tile = tile;

@@ -1,5 +1,7 @@
 // ocmc_unet_tc.h -- host entry points of the tcgen05 3x3x3 convolution (ocmc_unet_tc.cu).
 #pragma once
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -40,6 +42,20 @@ cudaError_t launch_up_tc(const ConvArgs& a, const __nv_bfloat16* wpack, int* err
 bool down_tc_supported(int cin, int cout);
 cudaError_t pack_down_tc(const __nv_bfloat16* w, int cin, int cout, __nv_bfloat16* wpack, cudaStream_t s);
 cudaError_t launch_down_tc(const ConvArgs& a, const __nv_bfloat16* wpack, int* err, cudaStream_t s);
+
+// Weight gradient of a 3x3x3 convolution on the tensor-memory path (ocmc_unet_wgrad_tc.cu), for
+// (cin, cout) = (16, 16), (32, 16), (16, 32), (32, 32), (64, 32) on grids of at most 128 voxels
+// along x whose line stages fit shared memory (wgrad3_tc_fits): dW[t][c][n] = sum over voxels v
+// of grid g of x[v + d_t][c] dy[v][n]. Writes one partial [27][cin][cout] per block into part
+// (at most part_cap floats) and their count to *parts; the caller sums them in order. err (device
+// int, may be null) is set to 1 if a wait inside the kernel timed out.
+bool wgrad3_tc_supported(int cin, int cout);
+bool wgrad3_tc_fits(int cin, int cout, int nx);
+cudaError_t launch_wgrad3_tc(Grid3 g, Slice x, Slice dy, int cin, int cout, float* part, size_t part_cap, int* err,
+                             cudaStream_t s, int* parts);
+
+// The driver's cuTensorMapEncodeTiled (null if the driver does not provide it).
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder();
 
 }  // namespace unet
 }  // namespace ocmc

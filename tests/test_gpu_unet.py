@@ -51,11 +51,15 @@ def test_layer_matches_oracle(ocmc, mode, cin, cout):
     assert np.allclose(dw, dwr, rtol=1e-4, atol=1e-4 * np.abs(dwr).max())
 
 
-@pytest.mark.parametrize("cin,cout", [(16, 16), (32, 64), (64, 32), (64, 64), (128, 64), (128, 128)])
+@pytest.mark.parametrize("cin,cout", [(16, 16), (32, 16), (32, 32), (32, 64), (64, 32), (64, 64), (128, 64),
+                                      (128, 128)])
 def test_conv3_large_grid(ocmc, cin, cout):
     """A grid of 190+ output tiles per channel slice, so every block of the persistent
     tensor-memory kernel runs several tiles (both accumulator sets, every halo stage reused);
-    for 64 and 128 input channels the blocks also split the output channels into slices."""
+    for 64 and 128 input channels the blocks also split the output channels into slices. The
+    weight gradient of the 16- and 32-channel layers runs on tcgen05 too: every block then
+    accumulates over dozens of rows (all stages reused), with two or more row segments per x
+    line where the grid is 128 voxels wide."""
     rng = np.random.default_rng(cin * 7 + cout)
     fine = (48, 80, 128) if cin < 64 else (32, 48, 64)
     x = U.bf16(rng.standard_normal(fine + (cin,)))
