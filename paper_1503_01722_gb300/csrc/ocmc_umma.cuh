@@ -9,8 +9,12 @@
 //   bits 32-45  stride-dimension byte offset >> 4: distance between core matrices adjacent
 //               along M (or N)
 //   bits 46-47  descriptor version 1
-//   bits 61-63  layout: 0 = no swizzle
+//   bits 61-63  layout: 0 = no swizzle (6 = 32B, 4 = 64B, 2 = 128B swizzle)
 // A core matrix is 8 rows of 16 contiguous bytes (8 BF16 values along K), rows 16 bytes apart.
+// The weight-gradient kernel uses MN-major operands with 32B/64B/128B swizzling instead: a row
+// of one swizzle span holds consecutive M (or N) values, rows follow along K; the stride offset
+// is then the distance between groups of 8 rows along K and the leading offset the distance
+// between successive spans along M (or N).
 //
 // Instruction descriptor (32 bit) for kind::f16: D format F32 (bits 4-5 = 1), A and B BF16
 // (bits 7-9 = 1, bits 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 in bits 17-22,
@@ -89,6 +93,15 @@ __device__ __forceinline__ void tma_load_5d(void* dst, const void* tmap, int c0,
         "cp.async.bulk.tensor.5d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5, "
         "%6}], [%7];" ::"r"(saddr(dst)),
         "l"(reinterpret_cast<uint64_t>(tmap)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(saddr(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void tma_load_4d(void* dst, const void* tmap, int c0, int c1, int c2, int c3, uint64_t* bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+        "[%6];" ::"r"(saddr(dst)),
+        "l"(reinterpret_cast<uint64_t>(tmap)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(saddr(bar))
         : "memory");
 }
 

@@ -159,28 +159,72 @@ __global__ void __launch_bounds__(1024) k_sum_rows(const float* part, int parts,
     }
 }
 
+// The same sums for wide rows of at most 32 parts, four columns per thread (the block-per-32-
+// columns form above would launch m / 32 blocks of mostly idle threads): identical order of
+// additions (parts in 32 consecutive groups, each group summed from zero, the group sums added in
+// order from zero).
+__global__ void k_sum_rows4(const float4* part, int parts, long long m4, float4* out)
+{
+    const int L = (parts + 31) / 32;
+    for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < m4; j += (long long)gridDim.x * blockDim.x) {
+        float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int y = 0; y < 32; ++y) {
+            const int i0 = y * L, i1 = min(parts, i0 + L);
+            float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int i = i0; i < i1; ++i) {
+                const float4 v = part[(long long)i * m4 + j];
+                s.x += v.x; s.y += v.y; s.z += v.z; s.w += v.w;
+            }
+            t.x += s.x; t.y += s.y; t.z += s.z; t.w += s.w;
+        }
+        out[j] = t;
+    }
+}
+
+int sm_count();
+
 void sum_rows(const float* part, int parts, long long m, float* out, cudaStream_t s)
 {
+    if (m % 4 == 0 && m >= 8192 && parts <= 32) {   // wide rows, few parts (many parts: the block form)
+        const long long m4 = m / 4;
+        k_sum_rows4<<<(unsigned)std::min<long long>((m4 + 255) / 256, 8LL * sm_count()), 256, 0, s>>>(
+            reinterpret_cast<const float4*>(part), parts, m4, reinterpret_cast<float4*>(out));
+        return;
+    }
     k_sum_rows<<<(unsigned)((m + 31) / 32), dim3(32, 32), 0, s>>>(part, parts, (int)m, out);
 }
 
 // bias gradient partials: per block sums of dy[v][n] over its voxels, in a fixed order (thread
-// (r, c) of the block sums channel c over voxels r, r + R, ...; then the R partial sums of each
-// channel are added in order), so that gradients are bit-reproducible. cout divides blockDim.x.
+// (r, g) of the block sums channels 8 g .. 8 g + 7 over voxels r, r + R, ... with 16-byte loads;
+// then the R partial sums of each channel are added in order), so that gradients are
+// bit-reproducible. cout / 8 divides blockDim.x (at most 256 threads); stride and c0 are
+// multiples of 8.
 __global__ void k_bias_part(const __nv_bfloat16* dy, int stride, int c0, int cout, long long n, float* part)
 {
-    __shared__ float sh[256];
-    const int rpp = blockDim.x / cout;
-    const int c = threadIdx.x % cout, r = threadIdx.x / cout;
-    float acc = 0.f;
+    __shared__ float sh[256 * 8];
+    const int G = cout / 8, rpp = blockDim.x / G;
+    const int g = threadIdx.x % G, r = threadIdx.x / G;
+    float acc[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) acc[e] = 0.f;
     if (r < rpp)
-        for (long long v = (long long)blockIdx.x * rpp + r; v < n; v += (long long)gridDim.x * rpp)
-            acc += __bfloat162float(dy[v * stride + c0 + c]);
-    sh[threadIdx.x] = acc;
+        for (long long v = (long long)blockIdx.x * rpp + r; v < n; v += (long long)gridDim.x * rpp) {
+            const uint4 q = *reinterpret_cast<const uint4*>(dy + v * stride + c0 + 8 * g);
+            const __nv_bfloat162* b = reinterpret_cast<const __nv_bfloat162*>(&q);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const float2 f = __bfloat1622float2(b[e]);
+                acc[2 * e] += f.x;
+                acc[2 * e + 1] += f.y;
+            }
+        }
+#pragma unroll
+    for (int e = 0; e < 8; ++e) sh[threadIdx.x * 8 + e] = acc[e];
     __syncthreads();
     if (threadIdx.x < cout) {
+        const int gg = threadIdx.x / 8, e = threadIdx.x % 8;
         float sum = 0.f;
-        for (int i = 0; i < rpp; ++i) sum += sh[i * cout + threadIdx.x];
+        for (int i = 0; i < rpp; ++i) sum += sh[(i * G + gg) * 8 + e];
         part[blockIdx.x * cout + threadIdx.x] = sum;
     }
 }

@@ -8,21 +8,23 @@
 // A block walks lines of output voxels along x (the whole line, nx <= 128, at fixed (y, z)). With
 // P = L + 16 (L = nx rounded up to 16) it stages by TMA
 //   - the nine input lines j = dy + 3 dz at (y + dy - 1, z + dz - 1), voxels -1 .. P - 2: one plane
-//     per (j, channel group h of 8 channels), P voxels of 16 bytes each (plane position p holds
-//     input voxel p - 1), zero-filled outside the grid (the convolution's padding); planes in the
-//     order (j, h), PA = 16 P bytes apart;
-//   - the dy line three times, shifted: plane (dx, output channel group) holds at position p the
-//     dy of output voxel p - dx (zero outside the grid).
+//     per j of P voxels x CIN channels (position p holds input voxel p - 1), zero-filled outside
+//     the grid (the convolution's padding);
+//   - the dy line three times, shifted: plane dx holds at position p the dy of output voxel p - dx
+//     (zero outside the grid).
 // Then dW_dx = sum_p x_plane[p] dy_dx[p] over p in [0, P): every output voxel i meets its input
-// voxel i + dx - 1 exactly once, at p = i + dx, and every other product has a zero factor. In a
-// plane the 8 channels of a voxel are contiguous and successive voxels are 16 bytes apart, so both
-// operands are MN-major without swizzling: a core matrix is 8 voxels (K) by 8 channels (M or N),
-// K-groups of 8 voxels are 128 bytes apart and channel groups one plane apart. Row m = 8 g + c of
-// the M dimension, g = j H + h (H = CIN / 8), is input channel 8 h + c at line offset j; one MMA
-// (M = 128) covers a window of 16 consecutive planes. Its N = 3 COUT columns are (dx, output
-// channel), so each A window is read once for all three x-taps. With 9 H planes the windows start
-// at 0, 16, ..., and the last one at 9 H - 16, overlapping the one before it; its rows that the
-// earlier window covers are not written.
+// voxel i + dx - 1 exactly once, at p = i + dx, and every other product has a zero factor.
+// A plane row (one voxel, all its channels: 32, 64 or 128 bytes) is one TMA swizzle span (32B,
+// 64B or 128B swizzle), so TMA moves whole voxels and the plane is the canonical swizzled MN-major
+// layout of the MMA: M (or N) runs along a row's channels, K along the voxels; K-groups of 8 voxels
+// are 8 rows apart (the descriptor's stride offset) and rows of the next plane one plane apart (its
+// leading offset). Every operand starts at a plane or at a multiple of 16 voxels in it, i.e. on a
+// swizzle-pattern boundary. Row m = 8 g + c of the M dimension, g = j H + h (H = CIN / 8), is input
+// channel 8 h + c at line offset j; one MMA (M = 128) covers a window of 16 consecutive channel
+// groups (16 / H planes). Its N = 3 COUT columns are (dx, output channel), so each A window is read
+// once for all three x-taps. With 9 H groups the windows start at groups 0, 16, ..., and the last
+// one at 9 H - 16, overlapping the one before it; its rows that the earlier window covers are not
+// written.
 // Each window accumulates into its own FP32 accumulator of 3 COUT columns in tensor memory over
 // all lines of the block; at the end the block writes its partial dW [27][CIN][COUT], and the
 // caller sums the partials of all blocks in a fixed order.
@@ -58,7 +60,7 @@ struct WgArgs {
     Grid3 g;
     int P;                       // plane positions: nx rounded up to 16, plus 16
     long long rows;              // lines: ny * nz
-    uint32_t pa, stage;          // plane stride (16 P bytes), bytes per stage
+    uint32_t pa, pb, stage;      // input plane, dy plane (2 CIN P, 2 COUT P bytes rounded up to 1 KB), stage bytes
     int ns;                      // stages
     float* partial;              // [gridDim.x][27][CIN][COUT]
     int* err;
@@ -66,13 +68,18 @@ struct WgArgs {
 
 template <int CIN, int COUT>
 struct WgCfg {
-    static constexpr int H = CIN / 8, HC = COUT / 8, G = 9 * H;
+    static constexpr int H = CIN / 8, G = 9 * H;
     static constexpr int W = (G + 15) / 16;                   // windows of 16 input planes (M = 128)
     static constexpr uint32_t COLS = 3u * W * COUT;           // one accumulator of 3 COUT columns per window
     static constexpr uint32_t NCOLS = COLS <= 32 ? 32 : COLS <= 64 ? 64 : COLS <= 128 ? 128 : COLS <= 256 ? 256 : 512;
     static_assert(G >= 16 && COLS <= 512, "accumulators fit tensor memory");
     static_assert(COUT % 16 == 0 && 3 * COUT <= 256 && CIN % 8 == 0, "MMA shape");
     __host__ __device__ static constexpr int wstart(int w) { return w < W - 1 ? 16 * w : G - 16; }
+    // swizzle span = one voxel's channels; descriptor layout codes: 6 = 32B, 4 = 64B, 2 = 128B
+    static constexpr uint64_t swz(int bytes) { return bytes == 32 ? 6ull : bytes == 64 ? 4ull : 2ull; }
+    static constexpr uint64_t A_LAYOUT = swz(2 * CIN) << 61, B_LAYOUT = swz(2 * COUT) << 61;
+    static_assert(CIN == 16 || CIN == 32 || CIN == 64, "one voxel of input channels is one swizzle span");
+    static_assert(COUT == 16 || COUT == 32 || COUT == 64, "one voxel of output channels is one swizzle span");
 };
 
 __device__ __forceinline__ bool wg_wait_bounded(uint64_t* bar, uint32_t parity)
@@ -114,11 +121,11 @@ __global__ void __launch_bounds__(WG_THREADS, 1)
     __syncthreads();
     fence_after_sync();
     const uint32_t tmem = *tmem_slot;
-    const uint32_t in_bytes = (uint32_t)C::G * a.pa;
+    const uint32_t in_bytes = 9u * a.pa;
 
     if (warp == 0) {
         // ---- producer: the nine input lines and the three shifted dy lines of each line of the block ----
-        const uint32_t row_bytes = (uint32_t)(C::G + 3 * C::HC) * a.pa;
+        const uint32_t row_bytes = (uint32_t)a.P * 2u * (9u * CIN + 3u * COUT);   // what the twelve copies deliver
         int last[WG_MAX_STAGES];
 #pragma unroll
         for (int i = 0; i < WG_MAX_STAGES; ++i) last[i] = -1;
@@ -136,15 +143,10 @@ __global__ void __launch_bounds__(WG_THREADS, 1)
             const int y = (int)(r % a.g.ny), z = (int)(r / a.g.ny);
             uint8_t* sa = smem + (size_t)st * a.stage;
             uint8_t* sb = sa + in_bytes;
-            for (int k = lane; k < C::G + 3 * C::HC; k += 32) {
-                if (k < C::G) {
-                    const int j = k / C::H, h = k - (k / C::H) * C::H;
-                    tma_load_5d(sa + (size_t)k * a.pa, &xmap, 0, h, -1, y + j % 3 - 1, z + j / 3 - 1, &full[st]);
-                } else {
-                    const int kb = k - C::G, dx = kb / C::HC, hc = kb - dx * C::HC;
-                    tma_load_5d(sb + (size_t)kb * a.pa, &dymap, 0, hc, -dx, y, z, &full[st]);
-                }
-            }
+            if (lane < 9)
+                tma_load_4d(sa + (size_t)lane * a.pa, &xmap, 0, -1, y + lane % 3 - 1, z + lane / 3 - 1, &full[st]);
+            else if (lane < 12)
+                tma_load_4d(sb + (size_t)(lane - 9) * a.pb, &dymap, 0, 9 - lane, y, z, &full[st]);
             __syncwarp();
         }
         if (*abort && lane == 0) {   // copies in flight must land before the block exits
@@ -164,12 +166,16 @@ __global__ void __launch_bounds__(WG_THREADS, 1)
                 fence_after_sync();
                 const uint32_t sa = s0 + (uint32_t)st * a.stage, sb = sa + in_bytes;
                 for (int k = 0; k < a.P / 16; ++k) {
-                    // K step k: plane positions 16 k .. 16 k + 15 (K-groups 128 bytes apart)
-                    const uint64_t bd = sdesc(sb + (uint32_t)k * 256u, 128u, a.pa);
+                    // K step k: plane positions 16 k .. 16 k + 15; K-groups of 8 voxels are 8 rows apart
+                    // (stride offset), the next plane's rows one plane apart (leading offset)
+                    const uint64_t bd = sdesc(sb + (uint32_t)k * 32u * COUT, a.pb, 16u * COUT) | C::B_LAYOUT;
 #pragma unroll
-                    for (int w = 0; w < C::W; ++w)
-                        mma_f16(tmem + (uint32_t)(3 * w * COUT), sdesc(sa + (uint32_t)C::wstart(w) * a.pa + (uint32_t)k * 256u, 128u, a.pa),
-                                bd, idesc, (i > 0 || k > 0) ? 1u : 0u);
+                    for (int w = 0; w < C::W; ++w) {
+                        // window w starts at channel group wstart(w): plane wstart(w) / H
+                        const uint64_t ad = sdesc(sa + (uint32_t)(C::wstart(w) / C::H) * a.pa + (uint32_t)k * 32u * CIN,
+                                                  a.pa, 16u * CIN) | C::A_LAYOUT;
+                        mma_f16(tmem + (uint32_t)(3 * w * COUT), ad, bd, idesc, (i > 0 || k > 0) ? 1u : 0u);
+                    }
                 }
                 mma_commit(&empty[st]);
                 issued = true;
@@ -241,8 +247,11 @@ cudaError_t launch_wg_cfg(Grid3 g, Slice x, Slice dy, float* part, size_t part_c
     a.g = g;
     a.P = (g.nx + 15) / 16 * 16 + 16;
     a.rows = (long long)g.ny * g.nz;
-    a.pa = (uint32_t)a.P * 16u;
-    a.stage = (uint32_t)(C::G + 3 * C::HC) * a.pa;
+    // plane strides rounded up to 1024 bytes: every TMA destination and operand start sits on a
+    // boundary of the largest (128B) swizzle pattern
+    a.pa = (uint32_t)(a.P * 2 * CIN + 1023) / 1024u * 1024u;
+    a.pb = (uint32_t)(a.P * 2 * COUT + 1023) / 1024u * 1024u;
+    a.stage = 9u * a.pa + 3u * a.pb;
     a.ns = (int)std::min<uint32_t>(WG_MAX_STAGES, WG_STAGE_BUDGET / a.stage);
     a.err = err;
     a.partial = part;
@@ -255,24 +264,28 @@ cudaError_t launch_wg_cfg(Grid3 g, Slice x, Slice dy, float* part, size_t part_c
     if (blocks < 1) return cudaErrorMemoryAllocation;
 
     CUtensorMap mx, md;
-    cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+    cuuint32_t estr[4] = {1, 1, 1, 1};
+    auto swz = [](int bytes) {
+        return bytes == 32 ? CU_TENSOR_MAP_SWIZZLE_32B : bytes == 64 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B;
+    };
     {
-        cuuint64_t dims[5] = {8, (cuuint64_t)(CIN / 8), (cuuint64_t)g.nx, (cuuint64_t)g.ny, (cuuint64_t)g.nz};
+        // whole voxels (CIN channels, one swizzle span) along x, one line per copy
+        cuuint64_t dims[4] = {(cuuint64_t)CIN, (cuuint64_t)g.nx, (cuuint64_t)g.ny, (cuuint64_t)g.nz};
         const cuuint64_t vb = (cuuint64_t)x.stride * 2;
-        cuuint64_t strides[4] = {16, vb, vb * g.nx, vb * g.nx * g.ny};
-        cuuint32_t box[5] = {8, 1, (cuuint32_t)a.P, 1, 1};
-        if (enc(&mx, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, (void*)(x.ptr + x.c0), dims, strides, box, estr,
-                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+        cuuint64_t strides[3] = {vb, vb * g.nx, vb * g.nx * g.ny};
+        cuuint32_t box[4] = {(cuuint32_t)CIN, (cuuint32_t)a.P, 1, 1};
+        if (enc(&mx, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, (void*)(x.ptr + x.c0), dims, strides, box, estr,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, swz(2 * CIN), CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
             return cudaErrorInvalidValue;
     }
     {
-        cuuint64_t dims[5] = {8, (cuuint64_t)(COUT / 8), (cuuint64_t)g.nx, (cuuint64_t)g.ny, (cuuint64_t)g.nz};
+        cuuint64_t dims[4] = {(cuuint64_t)COUT, (cuuint64_t)g.nx, (cuuint64_t)g.ny, (cuuint64_t)g.nz};
         const cuuint64_t vb = (cuuint64_t)dy.stride * 2;
-        cuuint64_t strides[4] = {16, vb, vb * g.nx, vb * g.nx * g.ny};
-        cuuint32_t box[5] = {8, 1, (cuuint32_t)a.P, 1, 1};
-        if (enc(&md, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, (void*)(dy.ptr + dy.c0), dims, strides, box, estr,
-                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+        cuuint64_t strides[3] = {vb, vb * g.nx, vb * g.nx * g.ny};
+        cuuint32_t box[4] = {(cuuint32_t)COUT, (cuuint32_t)a.P, 1, 1};
+        if (enc(&md, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, (void*)(dy.ptr + dy.c0), dims, strides, box, estr,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, swz(2 * COUT), CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
             return cudaErrorInvalidValue;
     }
@@ -293,7 +306,8 @@ bool wgrad3_tc_fits(int cin, int cout, int nx)
 {
     if (!wgrad3_tc_supported(cin, cout) || nx < 1 || nx > 128) return false;
     const uint32_t P = (uint32_t)(nx + 15) / 16 * 16 + 16;
-    const uint32_t stage = (uint32_t)(9 * cin / 8 + 3 * cout / 8) * P * 16u;
+    const uint32_t pa = (P * 2u * cin + 1023u) / 1024u * 1024u, pb = (P * 2u * cout + 1023u) / 1024u * 1024u;
+    const uint32_t stage = 9u * pa + 3u * pb;
     return 2u * stage <= WG_STAGE_BUDGET;
 }
 
