@@ -54,7 +54,7 @@ bool wgrad3_tc_fits(int cin, int cout, int nx);
 cudaError_t launch_wgrad3_tc(Grid3 g, Slice x, Slice dy, int cin, int cout, float* part, size_t part_cap, int* err,
                              cudaStream_t s, int* parts);
 
-// The driver's cuTensorMapEncodeTiled (null if the driver does not provide it).
+// The CUDA driver's cuTensorMapEncodeTiled (null if the installed driver does not provide it).
 PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder();
 
 }  // namespace unet
