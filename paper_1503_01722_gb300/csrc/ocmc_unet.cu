@@ -159,10 +159,9 @@ __global__ void __launch_bounds__(1024) k_sum_rows(const float* part, int parts,
     }
 }
 
-// The same sums for wide rows of at most 32 parts, four columns per thread (the block-per-32-
-// columns form above would launch m / 32 blocks of mostly idle threads): identical order of
-// additions (parts in 32 consecutive groups, each group summed from zero, the group sums added in
-// order from zero).
+// The same sums for wide rows, four columns per thread (the block-per-32-columns form above would
+// launch m / 32 blocks of mostly idle threads): identical order of additions (parts in 32
+// consecutive groups, each group summed from zero, the group sums added in order from zero).
 __global__ void k_sum_rows4(const float4* part, int parts, long long m4, float4* out)
 {
     const int L = (parts + 31) / 32;
@@ -185,7 +184,9 @@ int sm_count();
 
 void sum_rows(const float* part, int parts, long long m, float* out, cudaStream_t s)
 {
-    if (m % 4 == 0 && m >= 8192 && parts <= 32) {   // wide rows, few parts (many parts: the block form)
+    // wide rows with few parts, or rows wide enough for a thread per four columns to keep the GPU
+    // busy; otherwise (narrow rows of many parts) the block form
+    if (m % 4 == 0 && m >= 8192 && (parts <= 32 || m >= 131072)) {
         const long long m4 = m / 4;
         k_sum_rows4<<<(unsigned)std::min<long long>((m4 + 255) / 256, 8LL * sm_count()), 256, 0, s>>>(
             reinterpret_cast<const float4*>(part), parts, m4, reinterpret_cast<float4*>(out));
